@@ -1,0 +1,256 @@
+"""FP64 CPU oracle of the direct-method XPCS/XSVS path -- TEST INFRASTRUCTURE.
+
+Only the tests, the smoke check and the bench's CPU-baseline leg may import
+this package.  It shares no code with the CUDA library: the intensity is the
+plain C direct sum in ``direct.c`` (built by :func:`build`), the correlation
+stages are written out below in numpy float64.
+
+What each function follows (arXiv 2204.13241):
+  amplitude / intensity   Sec. 2.2 Eqs. pe_ri, Iq_pq; Sec. 3.1 Eq.
+                          sq_cut_simple and Algorithm 1 (direct method).
+  g2                      Sec. 2.3 Eq. g2_def (XPCS autocorrelation).
+  ring_index, xsvs_contrast
+                          Sec. 2.3 Eqs. inte_Iq and bq_Iq (finite-exposure
+                          intensity as a sum of K frames, optical contrast
+                          over a |q| ring), averaged over exposures (Sec. 4.3).
+  grad_analytic           derivative of I = |S|^2 with respect to the atomic
+                          positions (the adjoint of Eq. pe_ri).
+  grad_fd                 central finite differences of a caller loss, with an
+                          exact incremental update of S per displaced atom.
+
+Readings taken where the paper leaves a choice (listed with the rest in the
+design notes): S uses exp(+i q.r) (the paper's p^e is its conjugate; I is
+the same); g2's numerator averages the T - tau available products and its
+denominator is the square of the mean over all T frames; a ring r holds the
+pixels with r - w/2 <= |q|/Delta < r + w/2, Delta = 2 pi / det(h)^(1/3);
+windows are the floor(T/K) non-overlapping blocks of K frames and beta is the
+population contrast averaged over windows.
+
+Every function here is pinned in tests/test_oracle_*.py against closed forms,
+invariants, brute force or hand-computed values; none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile direct.c into _build/liboracle.so with gcc (FP64, OpenMP, no fast-math)."""
+    src = os.path.join(_HERE, "direct.c")
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src)):
+        return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+           "-ffp-contract=off", src, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        I64 = ctypes.c_int64
+        lib.oracle_amplitude.argtypes = [P, I64, I64, P, P, P, I64, P, ctypes.c_int]
+        lib.oracle_amplitude.restype = ctypes.c_int
+        lib.oracle_qvectors.argtypes = [P, P, I64, P]
+        lib.oracle_qvectors.restype = ctypes.c_int
+        lib.oracle_inverse3.argtypes = [P, P]
+        lib.oracle_inverse3.restype = ctypes.c_int
+        lib.oracle_max_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+# ----------------------------------------------------------------------------
+# intensity (direct method)
+# ----------------------------------------------------------------------------
+
+def qvectors(box: np.ndarray, miller: np.ndarray) -> np.ndarray:
+    """q = 2 pi h^-T n for each Miller index, float64 [P][3]."""
+    h = np.ascontiguousarray(box, dtype=np.float64).reshape(9)
+    m = np.ascontiguousarray(miller, dtype=np.int32).reshape(-1, 3)
+    out = np.empty((m.shape[0], 3), dtype=np.float64)
+    if not _load().oracle_qvectors(_ptr(h), _ptr(m), m.shape[0], _ptr(out)):
+        raise ValueError("singular cell matrix")
+    return out
+
+
+def amplitude(pos: np.ndarray, f: np.ndarray, box: np.ndarray, miller: np.ndarray,
+              threads: int = 0) -> np.ndarray:
+    """S(q,t) = sum_j f_j exp(+i q.r_j(t)), complex128 [T][P].
+
+    `pos` float32 [T][N][3] (or [N][3] for one frame), `f` [N], `box` 3x3
+    (columns = cell edge vectors), `miller` int [P][3]."""
+    p = np.ascontiguousarray(pos, dtype=np.float32)
+    if p.ndim == 2:
+        p = p[None]
+    T, N, _ = p.shape
+    fd = np.ascontiguousarray(f, dtype=np.float64).reshape(N)
+    h = np.ascontiguousarray(box, dtype=np.float64).reshape(9)
+    m = np.ascontiguousarray(miller, dtype=np.int32).reshape(-1, 3)
+    out = np.empty((T, m.shape[0], 2), dtype=np.float64)
+    ok = _load().oracle_amplitude(_ptr(p), N, T, _ptr(fd), _ptr(h), _ptr(m), m.shape[0],
+                                  _ptr(out), int(threads))
+    if not ok:
+        raise ValueError("singular cell matrix")
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def intensity(pos, f, box, miller, threads: int = 0) -> np.ndarray:
+    """I(q,t) = |S(q,t)|^2, float64 [T][P]."""
+    s = amplitude(pos, f, box, miller, threads)
+    return s.real ** 2 + s.imag ** 2
+
+
+# ----------------------------------------------------------------------------
+# XPCS autocorrelation
+# ----------------------------------------------------------------------------
+
+def g2(I: np.ndarray, taus: Sequence[int]) -> tuple[np.ndarray, np.ndarray]:
+    """g2(q,tau) = <I(t) I(t+tau)>_t / <I(t)>_t^2 per pixel.
+
+    I [T][P]; the numerator averages the T - tau products with t in
+    [0, T - tau), the denominator squares the mean over all T frames.
+    Returns (g2 float64 [n_tau][P], mean float64 [P])."""
+    x = np.asarray(I, dtype=np.float64)
+    T = x.shape[0]
+    mean = x.sum(axis=0) / T
+    out = np.empty((len(taus),) + x.shape[1:], dtype=np.float64)
+    for k, tau in enumerate(taus):
+        tau = int(tau)
+        if tau < 0 or tau >= T:
+            raise ValueError("delay out of range")
+        num = (x[: T - tau] * x[tau:]).sum(axis=0) / (T - tau)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            out[k] = num / (mean * mean)
+    return out, mean
+
+
+# ----------------------------------------------------------------------------
+# XSVS contrast
+# ----------------------------------------------------------------------------
+
+def ring_index(box: np.ndarray, miller: np.ndarray, ring_width: float, n_rings: int) -> np.ndarray:
+    """Ring of each pixel (1..n_rings) or 0 when the pixel is in no ring.
+
+    Ring r collects r - w/2 <= |q|/Delta < r + w/2 with Delta = 2 pi /
+    det(h)^(1/3) (= 2 pi / L for a cubic box)."""
+    q = qvectors(box, miller)
+    det = float(np.linalg.det(np.asarray(box, dtype=np.float64)))
+    delta = 2.0 * math.pi / abs(det) ** (1.0 / 3.0)
+    x = np.sqrt((q * q).sum(axis=1)) / delta
+    r = np.floor(x + 0.5)
+    ok = (r >= 1) & (r <= n_rings) & (x >= r - ring_width / 2.0) & (x < r + ring_width / 2.0)
+    return np.where(ok, r, 0).astype(np.int32)
+
+
+def xsvs_contrast(I: np.ndarray, Ks: Sequence[int], rings: np.ndarray, n_rings: int
+                  ) -> tuple[np.ndarray, np.ndarray]:
+    """beta_K(r), float64 [n_K][n_rings], and pixels per ring.
+
+    For window length K the exposures are I_K(q,w) = sum_{t=wK}^{wK+K-1}
+    I(q,t), w = 0..floor(T/K)-1; per window and ring
+    beta = (<I_K^2>_ring - <I_K>_ring^2) / <I_K>_ring^2, then beta_K(r) is the
+    mean of beta over windows.  A ring with no pixel gives NaN."""
+    x = np.asarray(I, dtype=np.float64)
+    T = x.shape[0]
+    rings = np.asarray(rings).reshape(-1)
+    counts = np.array([(rings == r).sum() for r in range(1, n_rings + 1)], dtype=np.int64)
+    out = np.full((len(Ks), n_rings), np.nan, dtype=np.float64)
+    for ik, K in enumerate(Ks):
+        K = int(K)
+        if K < 1 or K > T:
+            raise ValueError("window length out of range")
+        W = T // K
+        sums = np.stack([x[w * K:(w + 1) * K].sum(axis=0) for w in range(W)])  # [W][P]
+        for r in range(1, n_rings + 1):
+            sel = rings == r
+            n = int(sel.sum())
+            if n == 0:
+                continue
+            v = sums[:, sel]
+            m1 = v.sum(axis=1) / n
+            m2 = (v * v).sum(axis=1) / n
+            with np.errstate(divide="ignore", invalid="ignore"):
+                beta_w = (m2 - m1 * m1) / (m1 * m1)
+            out[ik, r - 1] = beta_w.sum() / W
+    return out, counts
+
+
+# ----------------------------------------------------------------------------
+# gradients with respect to positions
+# ----------------------------------------------------------------------------
+
+def grad_analytic(pos: np.ndarray, f: np.ndarray, box: np.ndarray, miller: np.ndarray,
+                  dL_dI: np.ndarray, atoms: Optional[np.ndarray] = None,
+                  amp: Optional[np.ndarray] = None) -> np.ndarray:
+    """dL/dr_j = sum_q dL/dI_q * 2 Re[conj(S_q) * i q f_j exp(i q.r_j)].
+
+    One frame: pos [N][3].  `atoms` selects the rows returned (all by
+    default); `amp` may pass S for the full atom set (else it is computed)."""
+    p = np.asarray(pos, dtype=np.float32).reshape(-1, 3)
+    q = qvectors(box, miller)
+    if amp is None:
+        amp = amplitude(p, f, box, miller)[0]
+    H = np.asarray(dL_dI, dtype=np.float64).reshape(-1) * np.conj(amp)
+    sel = np.arange(p.shape[0]) if atoms is None else np.asarray(atoms)
+    fd = np.asarray(f, dtype=np.float64)
+    out = np.empty((sel.size, 3), dtype=np.float64)
+    for k0 in range(0, sel.size, 64):
+        idx = sel[k0:k0 + 64]
+        th = p[idx].astype(np.float64) @ q.T                    # [n][P]
+        e = np.cos(th) + 1j * np.sin(th)
+        val = 2.0 * fd[idx, None] * np.real(1j * H[None, :] * e)  # [n][P]
+        out[k0:k0 + idx.size] = val @ q
+    return out
+
+
+def grad_fd(pos: np.ndarray, f: np.ndarray, box: np.ndarray, miller: np.ndarray,
+            loss_of_I, atoms: Sequence[int], h: float = 1e-4,
+            amp: Optional[np.ndarray] = None) -> np.ndarray:
+    """Central differences (L(r + h e_a) - L(r - h e_a)) / 2h of loss_of_I(I).
+
+    The displaced amplitude is S + f_j (exp(i q.r'_j) - exp(i q.r_j)),
+    exact in FP64 and O(P) per displacement."""
+    p = np.asarray(pos, dtype=np.float32).reshape(-1, 3)
+    q = qvectors(box, miller)
+    S = amplitude(p, f, box, miller)[0] if amp is None else np.asarray(amp)
+    fd = np.asarray(f, dtype=np.float64)
+    out = np.empty((len(atoms), 3), dtype=np.float64)
+    for k, j in enumerate(atoms):
+        r0 = p[j].astype(np.float64)
+        e0 = np.exp(1j * (q @ r0))
+        for a in range(3):
+            vals = []
+            for sgn in (+1.0, -1.0):
+                r1 = r0.copy()
+                r1[a] += sgn * h
+                S1 = S + fd[j] * (np.exp(1j * (q @ r1)) - e0)
+                vals.append(loss_of_I(S1.real ** 2 + S1.imag ** 2))
+            out[k, a] = (vals[0] - vals[1]) / (2.0 * h)
+    return out
