@@ -1,0 +1,208 @@
+/*
+ * xs_api.h -- C ABI of the GB300 direct-method XPCS / XSVS library (libxs.so).
+ *
+ * The library computes, on one GPU, the quantities of arXiv 2204.13241:
+ *   - the scattered intensity I(q,t) = |S(q,t)|^2 with
+ *     S(q,t) = sum_j f_j exp(+i q.r_j(t))            (Sec. 2.2, Eqs. pe_ri, Iq_pq;
+ *     on reciprocal-lattice q = 2 pi h^-T n            Sec. 3.1, Eq. sq_cut_simple,
+ *                                                     Algorithm 1),
+ *   - the XPCS autocorrelation g2(q,tau)             (Sec. 2.3, Eq. g2_def),
+ *   - the XSVS contrast of K-frame exposures         (Sec. 2.3, Eqs. inte_Iq, bq_Iq),
+ *   - the gradient of a loss L(I) with respect to the atomic positions
+ *     (the adjoint of Eq. pe_ri).
+ * Sign convention: the paper writes p^e = sum f exp(-i q.r); this library's
+ * amplitude S is its complex conjugate.  I, g2 and the contrast are identical.
+ *
+ * Conventions for every entry point
+ *   - Units: positions and cell in Angstrom; q in 1/Angstrom; time in frames.
+ *   - Cell: xs_box.h is the row-major 3x3 matrix whose COLUMNS are the cell
+ *     edge vectors, so fractional coordinates are s = h^-1 r and the detector
+ *     points are q = 2 pi h^-T n for integer Miller indices n.  A cubic box of
+ *     side L is h = L * identity.
+ *   - Grids: xs_qgrid gives n_x in [nx0, nx0+nx), n_y in [ny0, ny0+ny),
+ *     n_z in [nz0, nz0+nz); pixel p = (iz*ny + iy)*nx + ix (x fastest).
+ *   - Ownership: the caller owns every input and output buffer; the library
+ *     never frees or retains them past the call.  Internal workspace is taken
+ *     from the context's allocator and kept by the context for reuse.
+ *   - Asynchrony: all GPU work is enqueued on the caller's CUDA stream
+ *     (`cuda_stream`, a cudaStream_t; NULL = legacy default stream) and the
+ *     call returns without waiting, except where host buffers are read or
+ *     written (stated per call).
+ *   - Errors: arguments are checked before any launch; a bad argument returns
+ *     XS_ERR_INVALID_ARG and enqueues nothing.  Failures found by a kernel
+ *     (a bounded wait that timed out, a non-finite position) set the
+ *     context's device error word; xs_sync_status() reports it.  No C++
+ *     exception crosses this ABI and no kernel traps.  xs_last_error() gives
+ *     a message for the last non-OK status of the calling thread.
+ */
+#ifndef XS_API_H
+#define XS_API_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define XS_API __attribute__((visibility("default")))
+#else
+#define XS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    XS_OK = 0,
+    XS_ERR_INVALID_ARG = 1,   /* null pointer, size <= 0, singular cell, tau/K out of range */
+    XS_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+    XS_ERR_NO_MEMORY = 3,     /* the allocator returned NULL */
+    XS_ERR_CUDA = 4,          /* a CUDA runtime call failed (message has the CUDA error) */
+    XS_ERR_TIMEOUT = 5,       /* a kernel's bounded wait expired (device error word) */
+    XS_ERR_NUMERIC = 6        /* a kernel met a non-finite input (device error word) */
+} xs_status;
+
+/* Arithmetic of the intensity (Sec. 3.1 direct method; every variant computes
+ * the same S, they differ only in rounding):
+ *   XS_PREC_FP32_DIRECT  one FP32 phase factor per atom and pixel from an exact
+ *                        integer phase, FP32 sums merged in FP64 blocks;
+ *   XS_PREC_SPLIT_FP16   tensor-core contraction over atoms of FP16 hi+lo split
+ *                        factor tables, FP32 accumulation flushed per atom chunk;
+ *   XS_PREC_SPLIT_BF16   the same with BF16 hi+lo tables. */
+typedef enum {
+    XS_PREC_FP32_DIRECT = 0,
+    XS_PREC_SPLIT_FP16 = 1,
+    XS_PREC_SPLIT_BF16 = 2
+} xs_precision;
+
+typedef struct { double h[9]; } xs_box;                          /* row-major, columns = edges */
+typedef struct { int32_t nx0, nx, ny0, ny, nz0, nz; } xs_qgrid;  /* Miller-index ranges */
+
+/* One trajectory.  pos is float32 [n_frames][n_atoms][3] (unwrapped
+ * coordinates are fine: the method is periodic, Sec. 3.1); on the device, or
+ * in host memory when pos_on_host != 0 (then the library streams frames to the
+ * device in chunks; page-locked memory lets the copies overlap compute).
+ * f is float32 [n_atoms] in the same memory space as pos. */
+typedef struct {
+    const float* pos;
+    int32_t pos_on_host;
+    const float* f;
+    int64_t n_atoms;
+    int64_t n_frames;
+    xs_box box;
+} xs_traj;
+
+/* Device-memory allocator used for workspace.  alloc returns NULL on
+ * failure; free receives pointers alloc returned.  Both are called on the
+ * calling host thread.  NULL allocator = cudaMalloc / cudaFree. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, void* ctx);
+    void* ctx;
+} xs_allocator;
+
+typedef struct xs_context xs_context;
+
+/* Creates a context bound to the current CUDA device: workspace cache, tuned
+ * tile choices and the device error word.  *out receives the handle. */
+XS_API xs_status xs_context_create(const xs_allocator* allocator, xs_context** out);
+
+/* Synchronizes the device, frees the workspace and the handle. NULL is a no-op. */
+XS_API xs_status xs_context_destroy(xs_context* ctx);
+
+/*
+ * Intensity on a detector grid for every frame: Algorithm 1 of Sec. 3.1
+ * (direct method), S(q,t) = sum_j f_j exp(+i q.r_j(t)), I = |S|^2 (Eq. Iq_pq).
+ *   I_out   float32 [n_frames][nz][ny][nx]
+ *   amp_out float32 [n_frames][nz][ny][nx][2] = (Re S, Im S), or NULL
+ * Outputs may be device or host memory (detected per pointer); host outputs
+ * make the call wait for the stream.  XS_PREC_SPLIT_* need nx, ny <= 4096 and
+ * the 128-aligned tiles described in the design notes; every grid works
+ * with XS_PREC_FP32_DIRECT.
+ */
+XS_API xs_status xs_intensity(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid,
+                       xs_precision prec, float* I_out, float* amp_out, void* cuda_stream);
+
+/*
+ * Many independent trajectories in one persistent launch (the batched form
+ * of Algorithm 1).  traj[i], grid[i] and I_out[i] as in xs_intensity, with
+ * device positions; n_traj >= 1.  `traj`, `grid` and `I_out` are host arrays.
+ */
+XS_API xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid,
+                               int32_t n_traj, xs_precision prec, float* const* I_out,
+                               void* cuda_stream);
+
+/*
+ * XPCS autocorrelation, Sec. 2.3 Eq. g2_def, per pixel:
+ *   mean(p) = (1/T) sum_{t<T} I(t,p)
+ *   g2(tau,p) = [(1/(T-tau)) sum_{t<T-tau} I(t,p) I(t+tau,p)] / mean(p)^2
+ *   I        device float32 [T][P]
+ *   taus     HOST int32 [n_tau], each 0 <= tau < T (tau = 0 gives beta_0 + 1,
+ *            Eq. bq_g2)
+ *   g2_out   device float64 [n_tau][P]; NaN or Inf where mean(p) == 0
+ *   mean_out device float64 [P], or NULL
+ */
+XS_API xs_status xs_g2(xs_context* ctx, const float* I, int64_t T, int64_t P, const int32_t* taus,
+                int32_t n_tau, double* g2_out, double* mean_out, void* cuda_stream);
+
+/*
+ * XSVS contrast, Sec. 2.3 Eqs. inte_Iq and bq_Iq, averaged over exposures:
+ * for each window length K, exposures I_K(p,w) = sum_{t=wK}^{wK+K-1} I(t,p),
+ * w = 0..floor(T/K)-1; ring r (1..n_rings) holds the pixels with
+ * r - ring_width/2 <= |q|/Delta < r + ring_width/2, Delta = 2 pi / det(h)^(1/3);
+ *   beta_K(r) = mean_w [ (<I_K^2>_r - <I_K>_r^2) / <I_K>_r^2 ]  (population variance).
+ *   I              device float32 [T][P] on `grid` (P = nx*ny*nz)
+ *   Ks             HOST int32 [n_K], 1 <= K <= T
+ *   ring_width     in units of Delta, 0 < ring_width <= 1
+ *   beta_out       device float64 [n_K][n_rings]; NaN for an empty ring
+ *   ring_count_out HOST int32 [n_rings] pixels per ring, or NULL
+ */
+XS_API xs_status xs_xsvs_contrast(xs_context* ctx, const float* I, int64_t T, const xs_qgrid* grid,
+                           const xs_box* box, const int32_t* Ks, int32_t n_K, double ring_width,
+                           int32_t n_rings, double* beta_out, int32_t* ring_count_out,
+                           void* cuda_stream);
+
+/*
+ * Host-side helper (no GPU work): the ring of every pixel of `grid` as used by
+ * xs_xsvs_contrast, ring_out HOST int32 [nx*ny*nz], 0 for pixels in no ring.
+ */
+XS_API xs_status xs_ring_index(const xs_qgrid* grid, const xs_box* box, double ring_width, int32_t n_rings,
+                        int32_t* ring_out);
+
+/*
+ * Adjoint of the intensity for one frame (traj->n_frames must be 1, device
+ * positions):  dL/dr_j = sum_q dL/dI_q * 2 Re[ conj(S_q) * i q f_j exp(i q.r_j) ].
+ *   amp        device float32 [P][2], the S of this frame (xs_intensity amp_out)
+ *   dL_dI      device float32 [P]
+ *   dL_dr_out  device float32 [n_atoms][3]
+ * FP32 arithmetic; every grid shape is accepted.
+ */
+XS_API xs_status xs_intensity_backward(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid,
+                                const float* amp, const float* dL_dI, float* dL_dr_out,
+                                void* cuda_stream);
+
+/* Times the tensor-core tile choices for this trajectory shape and grid and
+ * keeps the fastest in the context (later calls of the same shape use it).
+ * Synchronizes the stream. */
+XS_API xs_status xs_tune(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, xs_precision prec,
+                  void* cuda_stream);
+
+/* Message for the last non-OK status returned on the calling thread. */
+XS_API const char* xs_last_error(void);
+
+/* Waits for `cuda_stream`, then reads and clears the device error word:
+ * XS_ERR_TIMEOUT, XS_ERR_NUMERIC or XS_OK. */
+XS_API xs_status xs_sync_status(xs_context* ctx, void* cuda_stream);
+
+/* Debug knob: the bounded waits inside the tensor-core kernel give up after
+ * `ns` nanoseconds (default 2e9).  Used by tests to force a timeout on a
+ * kernel whose wait can never complete. */
+XS_API xs_status xs_set_wait_timeout_ns(xs_context* ctx, int64_t ns);
+
+/* Library version string. */
+XS_API const char* xs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XS_API_H */

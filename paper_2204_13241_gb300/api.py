@@ -1,0 +1,248 @@
+"""PyTorch-facing calls of the library: argument marshalling only.
+
+Every computation runs in libxs.so (include/xs_api.h); PyTorch supplies
+device memory (through its caching allocator), the current CUDA stream and
+autograd plumbing.  Tensors must be contiguous float32 (positions, form
+factors, intensities, amplitudes).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _native as nat
+from .workloads import QGrid as GridSpec
+
+
+def _box(box) -> nat.Box:
+    h = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(9))
+    b = nat.Box()
+    for i in range(9):
+        b.h[i] = float(h[i])
+    return b
+
+
+def _grid(grid) -> nat.QGrid:
+    if isinstance(grid, GridSpec):
+        t = grid.as_tuple()
+    else:
+        t = tuple(int(v) for v in grid)
+    return nat.QGrid(*t)
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _need(t: torch.Tensor, name: str, dtype=torch.float32, cuda: Optional[bool] = True):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if cuda is True and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if cuda is False and t.is_cuda:
+        raise ValueError(f"{name} must be a host tensor")
+
+
+class Context:
+    """One libxs context per CUDA device; workspace comes from PyTorch's
+    caching allocator."""
+
+    _per_device: dict[int, "Context"] = {}
+
+    def __init__(self, device: Optional[int] = None):
+        self.lib = nat.load()
+        self.device = torch.cuda.current_device() if device is None else int(device)
+
+        def _alloc(nbytes, _ctx):
+            with torch.cuda.device(self.device):
+                return torch.cuda.caching_allocator_alloc(int(nbytes), self.device)
+
+        def _free(ptr, _ctx):
+            with torch.cuda.device(self.device):
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._fns = (nat.ALLOC_FN(_alloc), nat.FREE_FN(_free))
+        self._alloc = nat.Allocator(self._fns[0], self._fns[1], None)
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            nat.check(self.lib.xs_context_create(ctypes.byref(self._alloc), ctypes.byref(handle)))
+        self.handle = handle
+
+    @classmethod
+    def get(cls, device: Optional[int] = None) -> "Context":
+        dev = torch.cuda.current_device() if device is None else int(device)
+        ctx = cls._per_device.get(dev)
+        if ctx is None:
+            ctx = cls(dev)
+            cls._per_device[dev] = ctx
+        return ctx
+
+    def close(self):
+        if self.handle:
+            with torch.cuda.device(self.device):
+                self.lib.xs_context_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def sync_status(self) -> None:
+        nat.check(self.lib.xs_sync_status(self.handle, _stream()))
+
+    def set_wait_timeout_ns(self, ns: int) -> None:
+        nat.check(self.lib.xs_set_wait_timeout_ns(self.handle, int(ns)))
+
+
+def _traj(pos: torch.Tensor, f: torch.Tensor, box) -> tuple[nat.Traj, bool]:
+    if pos.dim() == 2:
+        pos = pos.unsqueeze(0)
+    if pos.dim() != 3 or pos.shape[-1] != 3:
+        raise ValueError("positions must be [T][N][3]")
+    host = not pos.is_cuda
+    _need(pos, "pos", cuda=not host)
+    _need(f, "f", cuda=not host)
+    if f.numel() != pos.shape[1]:
+        raise ValueError("f must have one entry per atom")
+    tr = nat.Traj(pos.data_ptr(), 1 if host else 0, f.data_ptr(), pos.shape[1], pos.shape[0], _box(box))
+    return tr, host
+
+
+def intensity(pos: torch.Tensor, f: torch.Tensor, box, grid, precision: str = "fp16",
+              want_amp: bool = False, out: Optional[torch.Tensor] = None,
+              amp_out: Optional[torch.Tensor] = None):
+    """I(q,t) = |sum_j f_j exp(i q.r_j(t))|^2 on `grid` for every frame
+    (Sec. 3.1, Algorithm 1).  Returns I [T][nz][ny][nx] (and the amplitude
+    [T][nz][ny][nx][2] when want_amp).  Host positions are streamed."""
+    tr, host = _traj(pos, f, box)
+    g = _grid(grid)
+    shape = (int(tr.n_frames), g.nz, g.ny, g.nx)
+    dev = torch.device("cuda", torch.cuda.current_device()) if not host else torch.device("cpu")
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=dev, pin_memory=host)
+    _need(out, "out", cuda=None)
+    if want_amp and amp_out is None:
+        amp_out = torch.empty(shape + (2,), dtype=torch.float32, device=dev, pin_memory=host)
+    if amp_out is not None:
+        _need(amp_out, "amp_out", cuda=None)
+    ctx = Context.get()
+    nat.check(ctx.lib.xs_intensity(ctx.handle, ctypes.byref(tr), ctypes.byref(g), nat.PRECISIONS[precision],
+                                   _ptr(out), _ptr(amp_out), _stream()))
+    return (out, amp_out) if want_amp else out
+
+
+def intensity_batched(trajs: Sequence[tuple], grids: Sequence, precision: str = "bf16",
+                      outs: Optional[Sequence[torch.Tensor]] = None):
+    """Many trajectories (pos, f, box) on their own grids in one call."""
+    n = len(trajs)
+    arr_t = (nat.Traj * n)()
+    arr_g = (nat.QGrid * n)()
+    keep = []
+    for i, (pos, f, box) in enumerate(trajs):
+        tr, host = _traj(pos, f, box)
+        if host:
+            raise ValueError("batched trajectories need device positions")
+        arr_t[i] = tr
+        arr_g[i] = _grid(grids[i])
+    if outs is None:
+        outs = [torch.empty((int(arr_t[i].n_frames), arr_g[i].nz, arr_g[i].ny, arr_g[i].nx), dtype=torch.float32,
+                            device="cuda") for i in range(n)]
+    ptrs = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    keep.append(ptrs)
+    ctx = Context.get()
+    nat.check(ctx.lib.xs_intensity_batched(ctx.handle, arr_t, arr_g, n, nat.PRECISIONS[precision], ptrs, _stream()))
+    return outs
+
+
+def tune(pos: torch.Tensor, f: torch.Tensor, box, grid, precision: str = "fp16") -> None:
+    tr, host = _traj(pos, f, box)
+    g = _grid(grid)
+    ctx = Context.get()
+    nat.check(ctx.lib.xs_tune(ctx.handle, ctypes.byref(tr), ctypes.byref(g), nat.PRECISIONS[precision], _stream()))
+
+
+def g2(I: torch.Tensor, taus: Sequence[int], want_mean: bool = True):
+    """g2(q,tau) per pixel (Sec. 2.3 Eq. g2_def) of I [T][...]; returns
+    (g2 float64 [n_tau][P], mean float64 [P])."""
+    _need(I, "I")
+    T = I.shape[0]
+    P = I.numel() // max(T, 1)
+    t = np.ascontiguousarray(np.asarray(taus, dtype=np.int32))
+    out = torch.empty((t.size, P), dtype=torch.float64, device=I.device)
+    mean = torch.empty((P,), dtype=torch.float64, device=I.device) if want_mean else None
+    ctx = Context.get()
+    nat.check(ctx.lib.xs_g2(ctx.handle, I.data_ptr(), T, P, t.ctypes.data_as(ctypes.c_void_p), t.size,
+                            out.data_ptr(), _ptr(mean), _stream()))
+    return out, mean
+
+
+def xsvs_contrast(I: torch.Tensor, grid, box, Ks: Sequence[int], n_rings: int, ring_width: float = 1.0):
+    """beta_K(ring) (Sec. 2.3 Eqs. inte_Iq, bq_Iq) of I [T][nz][ny][nx];
+    returns (beta float64 [n_K][n_rings], pixels per ring int32 [n_rings])."""
+    _need(I, "I")
+    g = _grid(grid)
+    b = _box(box)
+    k = np.ascontiguousarray(np.asarray(Ks, dtype=np.int32))
+    beta = torch.empty((k.size, n_rings), dtype=torch.float64, device=I.device)
+    counts = np.zeros(n_rings, dtype=np.int32)
+    ctx = Context.get()
+    nat.check(ctx.lib.xs_xsvs_contrast(ctx.handle, I.data_ptr(), I.shape[0], ctypes.byref(g), ctypes.byref(b),
+                                       k.ctypes.data_as(ctypes.c_void_p), k.size, float(ring_width), int(n_rings),
+                                       beta.data_ptr(), counts.ctypes.data_as(ctypes.c_void_p), _stream()))
+    return beta, counts
+
+
+def ring_index(grid, box, ring_width: float, n_rings: int) -> np.ndarray:
+    """Ring of every pixel as used by xsvs_contrast (host computation)."""
+    g = _grid(grid)
+    out = np.zeros(g.nx * g.ny * g.nz, dtype=np.int32)
+    lib = nat.load()
+    nat.check(lib.xs_ring_index(ctypes.byref(g), ctypes.byref(_box(box)), float(ring_width), int(n_rings),
+                                out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def intensity_backward(pos: torch.Tensor, f: torch.Tensor, box, grid, amp: torch.Tensor,
+                       dL_dI: torch.Tensor) -> torch.Tensor:
+    """dL/dr [N][3] for one frame from S (amp [P][2]) and dL/dI [P]."""
+    tr, host = _traj(pos, f, box)
+    if host:
+        raise ValueError("the adjoint needs device positions")
+    _need(amp, "amp")
+    _need(dL_dI, "dL_dI")
+    g = _grid(grid)
+    grad = torch.empty((int(tr.n_atoms), 3), dtype=torch.float32, device=pos.device)
+    ctx = Context.get()
+    nat.check(ctx.lib.xs_intensity_backward(ctx.handle, ctypes.byref(tr), ctypes.byref(g), amp.data_ptr(),
+                                            dL_dI.data_ptr(), grad.data_ptr(), _stream()))
+    return grad
+
+
+class IntensityFn(torch.autograd.Function):
+    """I(q) of one frame as a differentiable function of positions [N][3].
+
+    forward runs xs_intensity (FP32 direct or split tensor-core path) and
+    keeps S; backward runs xs_intensity_backward."""
+
+    @staticmethod
+    def forward(ctx, pos, f, box, grid, precision="fp32"):
+        p = pos.detach().contiguous()
+        I, amp = intensity(p, f, box, grid, precision, want_amp=True)
+        ctx.save_for_backward(p, f, amp)
+        ctx.box = box
+        ctx.grid = grid
+        return I.reshape(-1)
+
+    @staticmethod
+    def backward(ctx, grad_I):
+        p, f, amp = ctx.saved_tensors
+        g = intensity_backward(p, f, ctx.box, ctx.grid, amp.reshape(-1, 2).contiguous(),
+                               grad_I.contiguous().to(torch.float32))
+        return g.reshape(p.shape), None, None, None, None

@@ -1,0 +1,179 @@
+// Correlation stages on the intensity series I[t][p]:
+//   g2 (Sec. 2.3, Eq. g2_def) and the XSVS contrast (Eqs. inte_Iq, bq_Iq).
+//
+// g2_kernel: one thread per pixel and a group of up to kTauGroup delays.  The
+//   block walks t in order; I[t][p] and I[t+tau][p] are coalesced across the
+//   pixels of a warp.  Products are summed in FP32 over blocks of 64 frames and
+//   the block sums are added in FP64, as is the mean.
+//
+// XSVS: pixels are first permuted ring by ring (host-built permutation), then
+//   prefix_kernel   C[t][p'] = sum_{t'<t} I[t'][perm[p']]       (FP64, [T+1][P'])
+//   window_kernel   per (ring chunk, (K,w)): sum_p x and sum_p x^2 with
+//                   x = C[(w+1)K][p'] - C[wK][p'] (one warp per (K,w))
+//   finalize_kernel per (K, ring): ring sums over the ring's chunks in a fixed
+//                   order, beta per window, mean over windows.
+#include "xs_internal.h"
+
+namespace xs {
+
+namespace {
+
+constexpr int kTauGroup = 16;
+constexpr int kG2Threads = 128;
+constexpr int kFlush = 64;
+
+__global__ void __launch_bounds__(kG2Threads)
+g2_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __restrict__ taus,
+          int n_tau, double* __restrict__ g2, double* __restrict__ mean_out) {
+    __shared__ int s_tau[kTauGroup];
+    const int g0 = blockIdx.y * kTauGroup;
+    const int nt = min(kTauGroup, n_tau - g0);
+    if (threadIdx.x < kTauGroup) s_tau[threadIdx.x] = threadIdx.x < nt ? taus[g0 + threadIdx.x] : 0;
+    __syncthreads();
+    const int64_t p = blockIdx.x * (int64_t)kG2Threads + threadIdx.x;
+    if (p >= P) return;
+    int tau[kTauGroup];
+#pragma unroll
+    for (int k = 0; k < kTauGroup; ++k) tau[k] = s_tau[k];
+    float acc[kTauGroup];
+    double dacc[kTauGroup];
+#pragma unroll
+    for (int k = 0; k < kTauGroup; ++k) {
+        acc[k] = 0.0f;
+        dacc[k] = 0.0;
+    }
+    float msum = 0.0f;
+    double dmean = 0.0;
+    for (int64_t t0 = 0; t0 < T; t0 += kFlush) {
+        const int64_t t1 = min(T, t0 + kFlush);
+        for (int64_t t = t0; t < t1; ++t) {
+            const float x = I[t * P + p];
+            msum += x;
+#pragma unroll
+            for (int k = 0; k < kTauGroup; ++k) {
+                if (k < nt && t + tau[k] < T) acc[k] = fmaf(x, I[(t + tau[k]) * P + p], acc[k]);
+            }
+        }
+        dmean += (double)msum;
+        msum = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kTauGroup; ++k) {
+            dacc[k] += (double)acc[k];
+            acc[k] = 0.0f;
+        }
+    }
+    const double m = dmean / (double)T;
+    if (blockIdx.y == 0 && mean_out) mean_out[p] = m;
+#pragma unroll
+    for (int k = 0; k < kTauGroup; ++k) {
+        if (k < nt) g2[(int64_t)(g0 + k) * P + p] = (dacc[k] / (double)(T - tau[k])) / (m * m);
+    }
+}
+
+__global__ void prefix_kernel(const float* __restrict__ I, int64_t T, int64_t P,
+                              const int32_t* __restrict__ perm, int64_t n_in, double* __restrict__ C) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n_in) return;
+    const int64_t p = perm[q];
+    double acc = 0.0;
+    C[q] = 0.0;
+    for (int64_t t = 0; t < T; ++t) {
+        acc += (double)I[t * P + p];
+        C[(t + 1) * n_in + q] = acc;
+    }
+}
+
+// block = one chunk (ring, start, count); warps stride over the (K,w) list
+__global__ void window_kernel(const double* __restrict__ C, int64_t n_in, const int4* __restrict__ chunks,
+                              int n_chunks, const int32_t* __restrict__ Ks, const int64_t* __restrict__ kw_off,
+                              int n_K, int64_t n_kw, double2* __restrict__ partial) {
+    const int4 ch = chunks[blockIdx.x];  // (ring, start, count, 0)
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    int ik = 0;
+    for (int64_t kw = warp; kw < n_kw; kw += nwarps) {
+        while (ik + 1 < n_K && kw >= kw_off[ik + 1]) ++ik;
+        while (ik > 0 && kw < kw_off[ik]) --ik;
+        const int64_t K = Ks[ik];
+        const int64_t w = kw - kw_off[ik];
+        const double* c0 = C + (w * K) * n_in;
+        const double* c1 = C + ((w + 1) * K) * n_in;
+        double s1 = 0.0, s2 = 0.0;
+        for (int i = lane; i < ch.z; i += 32) {
+            const int64_t q = ch.y + i;
+            const double x = c1[q] - c0[q];
+            s1 += x;
+            s2 = fma(x, x, s2);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) partial[kw * n_chunks + blockIdx.x] = make_double2(s1, s2);
+    }
+}
+
+__global__ void finalize_kernel(const double2* __restrict__ partial, int n_chunks,
+                                const int32_t* __restrict__ Ks, const int64_t* __restrict__ kw_off, int n_K,
+                                int64_t T, const int32_t* __restrict__ ring_first_chunk,
+                                const int32_t* __restrict__ ring_count, int n_rings, double* __restrict__ beta) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_K * n_rings) return;
+    const int ik = (int)(i / n_rings);
+    const int r = (int)(i - (int64_t)ik * n_rings);
+    const int n = ring_count[r];
+    if (n == 0) {
+        beta[i] = __longlong_as_double(0x7ff8000000000000ll);  // NaN
+        return;
+    }
+    const int c0 = ring_first_chunk[r], c1 = ring_first_chunk[r + 1];
+    const int64_t K = Ks[ik];
+    const int64_t W = T / K;
+    double acc = 0.0;
+    for (int64_t w = 0; w < W; ++w) {
+        const double2* row = partial + (kw_off[ik] + w) * n_chunks;
+        double s1 = 0.0, s2 = 0.0;
+        for (int c = c0; c < c1; ++c) {
+            s1 += row[c].x;
+            s2 += row[c].y;
+        }
+        const double m1 = s1 / n, m2 = s2 / n;
+        acc += (m2 - m1 * m1) / (m1 * m1);
+    }
+    beta[i] = acc / (double)W;
+}
+
+}  // namespace
+
+cudaError_t launch_g2(const float* I, int64_t T, int64_t P, const int32_t* d_taus, int n_tau,
+                      double* g2, double* mean, cudaStream_t st) {
+    if (P == 0 || n_tau == 0) return cudaSuccess;
+    dim3 grid((unsigned)((P + kG2Threads - 1) / kG2Threads), (unsigned)((n_tau + kTauGroup - 1) / kTauGroup));
+    g2_kernel<<<grid, kG2Threads, 0, st>>>(I, T, P, d_taus, n_tau, g2, mean);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xsvs(const float* I, int64_t T, int64_t P, const int32_t* d_perm,
+                        const int4* d_chunks, int n_chunks, int64_t n_in_rings,
+                        const int32_t* d_K, const int64_t* d_kw_off, int n_K, int64_t n_kw,
+                        const int32_t* d_ring_first_chunk, const int32_t* d_ring_count,
+                        int n_rings, double* prefix, double2* partial, double* beta,
+                        cudaStream_t st) {
+    if (n_in_rings > 0) {
+        prefix_kernel<<<(unsigned)((n_in_rings + 127) / 128), 128, 0, st>>>(I, T, P, d_perm, n_in_rings, prefix);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        window_kernel<<<n_chunks, 256, 0, st>>>(prefix, n_in_rings, d_chunks, n_chunks, d_K, d_kw_off, n_K,
+                                                n_kw, partial);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t items = (int64_t)n_K * n_rings;
+    finalize_kernel<<<(unsigned)((items + 127) / 128), 128, 0, st>>>(partial, n_chunks, d_K, d_kw_off, n_K, T,
+                                                                     d_ring_first_chunk, d_ring_count, n_rings, beta);
+    return cudaGetLastError();
+}
+
+}  // namespace xs

@@ -1,0 +1,206 @@
+// Phase records and the plain FP32 direct sum (Algorithm 1, Sec. 3.1).
+//
+// phase_kernel: one thread per (frame, atom).  s = h^-1 r in FP64, then each
+//   axis is reduced to its fractional part and quantised to a 32-bit turn
+//   count.  This is the only FP64 work per atom; every later phase
+//   n_x*U_x + n_y*U_y + n_z*U_z is exact integer arithmetic modulo one turn.
+//
+// direct_kernel: the plain reference-rate kernel.  A block owns 256*PX pixels
+//   of one frame and a range of atoms; atom records are staged in shared
+//   memory 256 at a time.  Each (atom, pixel) costs one exact integer phase,
+//   one FP32 sincospi and two FMAs; FP32 sums over each 256-atom tile are
+//   merged into FP64 accumulators.  Atom ranges ("splits") give enough blocks
+//   for small grids; their FP64 partial amplitudes are added in a fixed order
+//   by reduce_kernel, so results are deterministic.
+#include "xs_internal.h"
+
+namespace xs {
+
+namespace {
+
+constexpr int kDirectThreads = 256;
+constexpr int kDirectPX = 4;     // pixels per thread
+constexpr int kAtomTile = 256;   // atom records staged per shared-memory tile
+
+__global__ void phase_kernel(const float* __restrict__ pos, const float* __restrict__ f,
+                             int64_t n_atoms, int64_t n_frames, int64_t n_pad, Mat3 hinv,
+                             AtomRec* __restrict__ rec, int* err) {
+    const int64_t total = n_frames * n_pad;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i / n_pad, j = i - t * n_pad;
+        AtomRec r;
+        if (j < n_atoms) {
+            const float* p = pos + (t * n_atoms + j) * 3;
+            const double x = p[0], y = p[1], z = p[2];
+            const float fj = f[j];
+            if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(fj)) {
+                set_dev_error(err, kDevErrNonFinite);
+                r.ux = r.uy = r.uz = 0u;
+                r.f = 0.0f;
+            } else {
+                const double sx = hinv.a[0] * x + hinv.a[1] * y + hinv.a[2] * z;
+                const double sy = hinv.a[3] * x + hinv.a[4] * y + hinv.a[5] * z;
+                const double sz = hinv.a[6] * x + hinv.a[7] * y + hinv.a[8] * z;
+                r.ux = turns_u32(sx);
+                r.uy = turns_u32(sy);
+                r.uz = turns_u32(sz);
+                r.f = fj;
+            }
+        } else {
+            r.ux = r.uy = r.uz = 0u;
+            r.f = 0.0f;
+        }
+        rec[i] = r;
+    }
+}
+
+__device__ __forceinline__ void pixel_miller(int64_t p, const GridDesc& g, uint32_t& nx, uint32_t& ny,
+                                             uint32_t& nz) {
+    const int64_t plane = (int64_t)g.nx * g.ny;
+    const int iz = (int)(p / plane);
+    const int64_t rem = p - (int64_t)iz * plane;
+    const int iy = (int)(rem / g.nx);
+    const int ix = (int)(rem - (int64_t)iy * g.nx);
+    nx = (uint32_t)(g.nx0 + ix);
+    ny = (uint32_t)(g.ny0 + iy);
+    nz = (uint32_t)(g.nz0 + iz);
+}
+
+// grid: x = pixel blocks, y = frame, z = atom split
+__global__ void __launch_bounds__(kDirectThreads)
+direct_kernel(const AtomRec* __restrict__ rec, int64_t n_pad, int64_t n_frames, GridDesc g,
+              int64_t atoms_per_split, double2* __restrict__ partial, float* __restrict__ I,
+              float* __restrict__ amp) {
+    __shared__ uint4 s_rec[kAtomTile];
+    const int64_t P = g.pixels();
+    const int t = blockIdx.y;
+    const int split = blockIdx.z;
+    const int64_t a0 = (int64_t)split * atoms_per_split;
+    const int64_t a1 = min(n_pad, a0 + atoms_per_split);
+    const uint4* frame_rec = reinterpret_cast<const uint4*>(rec + (int64_t)t * n_pad);
+
+    uint32_t nx[kDirectPX], ny[kDirectPX], nz[kDirectPX];
+    int64_t pix[kDirectPX];
+#pragma unroll
+    for (int i = 0; i < kDirectPX; ++i) {
+        pix[i] = ((int64_t)blockIdx.x * kDirectPX + i) * kDirectThreads + threadIdx.x;
+        const int64_t pc = pix[i] < P ? pix[i] : P - 1;
+        pixel_miller(pc, g, nx[i], ny[i], nz[i]);
+    }
+    float re[kDirectPX], im[kDirectPX];
+    double dre[kDirectPX], dim[kDirectPX];
+#pragma unroll
+    for (int i = 0; i < kDirectPX; ++i) {
+        re[i] = im[i] = 0.0f;
+        dre[i] = dim[i] = 0.0;
+    }
+    for (int64_t k0 = a0; k0 < a1; k0 += kAtomTile) {
+        const int nk = (int)min((int64_t)kAtomTile, a1 - k0);
+        __syncthreads();
+        if (threadIdx.x < nk) s_rec[threadIdx.x] = frame_rec[k0 + threadIdx.x];
+        __syncthreads();
+        for (int k = 0; k < nk; ++k) {
+            const uint4 a = s_rec[k];
+            const float fj = __uint_as_float(a.w);
+#pragma unroll
+            for (int i = 0; i < kDirectPX; ++i) {
+                const uint32_t ph = nx[i] * a.x + ny[i] * a.y + nz[i] * a.z;
+                float c, s;
+                phase_to_cs(ph, c, s);
+                re[i] = fmaf(fj, c, re[i]);
+                im[i] = fmaf(fj, s, im[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kDirectPX; ++i) {
+            dre[i] += (double)re[i];
+            dim[i] += (double)im[i];
+            re[i] = im[i] = 0.0f;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kDirectPX; ++i) {
+        if (pix[i] >= P) continue;
+        if (partial) {
+            partial[((int64_t)split * n_frames + t) * P + pix[i]] = make_double2(dre[i], dim[i]);
+        } else {
+            const int64_t o = (int64_t)t * P + pix[i];
+            I[o] = (float)(dre[i] * dre[i] + dim[i] * dim[i]);
+            if (amp) {
+                amp[2 * o] = (float)dre[i];
+                amp[2 * o + 1] = (float)dim[i];
+            }
+        }
+    }
+}
+
+__global__ void reduce_kernel(const double2* __restrict__ partial, int splits, int64_t n_items,
+                              float* __restrict__ I, float* __restrict__ amp) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_items;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int s = 0; s < splits; ++s) {
+            const double2 v = partial[(int64_t)s * n_items + i];
+            re += v.x;
+            im += v.y;
+        }
+        I[i] = (float)(re * re + im * im);
+        if (amp) {
+            amp[2 * i] = (float)re;
+            amp[2 * i + 1] = (float)im;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int64_t n_frames,
+                         int64_t n_pad, const Mat3& hinv, AtomRec* rec, int* err,
+                         cudaStream_t st) {
+    const int64_t total = n_frames * n_pad;
+    if (total == 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t blocks = min((total + threads - 1) / threads, (int64_t)65536);
+    phase_kernel<<<(unsigned)blocks, threads, 0, st>>>(pos, f, n_atoms, n_frames, n_pad, hinv, rec, err);
+    return cudaGetLastError();
+}
+
+DirectPlan plan_direct(int64_t n_pad, int64_t n_frames, const GridDesc& g, int num_sms) {
+    DirectPlan p;
+    const int64_t P = g.pixels();
+    const int64_t pix_blocks = (P + kDirectThreads * kDirectPX - 1) / (kDirectThreads * kDirectPX);
+    const int64_t base = pix_blocks * n_frames;
+    const int64_t want = 2 * (int64_t)num_sms;
+    int64_t tiles = (n_pad + kAtomTile - 1) / kAtomTile;
+    int64_t splits = base >= want ? 1 : (want + base - 1) / base;
+    if (splits > tiles) splits = tiles;
+    if (splits > 64) splits = 64;
+    if (splits < 1) splits = 1;
+    const int64_t tiles_per = (tiles + splits - 1) / splits;
+    p.atoms_per_split = tiles_per * kAtomTile;
+    p.splits = (int)((tiles + tiles_per - 1) / tiles_per);
+    if (p.splits < 1) p.splits = 1;
+    p.partial_bytes = p.splits > 1 ? (size_t)p.splits * n_frames * P * sizeof(double2) : 0;
+    return p;
+}
+
+cudaError_t launch_direct(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g,
+                          const DirectPlan& plan, void* partial, float* I, float* amp,
+                          cudaStream_t st) {
+    const int64_t P = g.pixels();
+    if (P == 0 || n_frames == 0) return cudaSuccess;
+    const int64_t pix_blocks = (P + kDirectThreads * kDirectPX - 1) / (kDirectThreads * kDirectPX);
+    if (n_frames > 65535 || pix_blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)pix_blocks, (unsigned)n_frames, (unsigned)plan.splits);
+    double2* part = plan.splits > 1 ? static_cast<double2*>(partial) : nullptr;
+    direct_kernel<<<grid, kDirectThreads, 0, st>>>(rec, n_pad, n_frames, g, plan.atoms_per_split, part, I, amp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || plan.splits == 1) return e;
+    const int64_t items = n_frames * P;
+    const int64_t blocks = min((items + 255) / 256, (int64_t)65536);
+    reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(part, plan.splits, items, I, amp);
+    return cudaGetLastError();
+}
+
+}  // namespace xs

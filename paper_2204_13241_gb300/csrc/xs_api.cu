@@ -1,0 +1,646 @@
+// C ABI of libxs: argument checking, workspace, frame streaming and launches.
+// The operations themselves are defined in include/xs_api.h with citations.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "xs_api.h"
+#include "xs_internal.h"
+
+using namespace xs;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+xs_status fail(xs_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define XS_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(XS_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                             \
+    } while (0)
+
+// inverse of a row-major 3x3 by the adjugate; false when singular
+bool invert3(const double* h, double* out) {
+    double adj[9];
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) {
+            // cofactor of element (c, r) goes to adj[r][c]
+            const int r1 = (c + 1) % 3, r2 = (c + 2) % 3, c1 = (r + 1) % 3, c2 = (r + 2) % 3;
+            adj[r * 3 + c] = h[r1 * 3 + c1] * h[r2 * 3 + c2] - h[r1 * 3 + c2] * h[r2 * 3 + c1];
+        }
+    }
+    const double det = h[0] * adj[0] + h[1] * adj[3] + h[2] * adj[6];
+    if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return false;
+    for (int i = 0; i < 9; ++i) out[i] = adj[i] / det;
+    return true;
+}
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct xs_context {
+    int device = 0;
+    int num_sms = 0;
+    xs_allocator alloc{};
+    bool has_alloc = false;
+    void* ws = nullptr;  // grow-only workspace
+    size_t ws_bytes = 0;
+    int* d_err = nullptr;
+    int64_t timeout_ns = 2000000000LL;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+    cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
+    std::map<std::tuple<int64_t, int, int, int, int>, int> tuned_chunk;  // (n_pad, nx, ny, nz, prec)
+    // small device-side tables, one slot per caller tag, re-uploaded only
+    // when their content changes (so repeated calls enqueue no host copies)
+    struct ConstSlot {
+        std::vector<char> key;
+        void* dev = nullptr;
+        size_t bytes = 0;
+    };
+    std::map<std::string, ConstSlot> consts;
+
+    void* raw_alloc(size_t bytes) {
+        if (has_alloc) return alloc.alloc(bytes, alloc.ctx);
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return p;
+    }
+    void raw_free(void* p) {
+        if (!p) return;
+        if (has_alloc)
+            alloc.free(p, alloc.ctx);
+        else
+            cudaFree(p);
+    }
+};
+
+namespace {
+
+// Ensures `bytes` of workspace; growing synchronizes the device first because
+// earlier work may still read the old block.
+xs_status ensure_ws(xs_context* ctx, size_t bytes) {
+    if (bytes <= ctx->ws_bytes) return XS_OK;
+    if (ctx->ws) {
+        XS_CUDA(cudaDeviceSynchronize());
+        ctx->raw_free(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    size_t want = bytes + bytes / 8;
+    ctx->ws = ctx->raw_alloc(want);
+    if (!ctx->ws) return fail(XS_ERR_NO_MEMORY, "workspace allocation of %zu bytes failed", want);
+    ctx->ws_bytes = want;
+    return XS_OK;
+}
+
+// Uploads a blob of small tables unless the same bytes are already resident.
+xs_status upload_const(xs_context* ctx, const char* tag, const std::vector<char>& blob, cudaStream_t st,
+                       void** dev) {
+    xs_context::ConstSlot& slot = ctx->consts[tag];
+    if (slot.dev && blob == slot.key) {
+        *dev = slot.dev;
+        return XS_OK;
+    }
+    // earlier launches on the stream may still read the old tables
+    XS_CUDA(cudaStreamSynchronize(st));
+    if (blob.size() > slot.bytes) {
+        ctx->raw_free(slot.dev);
+        slot.bytes = blob.size() + 4096;
+        slot.dev = ctx->raw_alloc(slot.bytes);
+        if (!slot.dev) {
+            slot.bytes = 0;
+            return fail(XS_ERR_NO_MEMORY, "table allocation failed");
+        }
+    }
+    XS_CUDA(cudaMemcpy(slot.dev, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+    slot.key = blob;
+    *dev = slot.dev;
+    return XS_OK;
+}
+
+template <class T>
+size_t push(std::vector<char>& blob, const T* data, size_t n) {
+    size_t off = round_up((int64_t)blob.size(), 256);
+    blob.resize(off + n * sizeof(T));
+    if (n) std::memcpy(blob.data() + off, data, n * sizeof(T));
+    return off;
+}
+
+xs_status check_grid(const xs_qgrid* g) {
+    if (!g) return fail(XS_ERR_INVALID_ARG, "grid is NULL");
+    if (g->nx < 0 || g->ny < 0 || g->nz < 0) return fail(XS_ERR_INVALID_ARG, "negative grid extent");
+    if (g->nx > 65536 || g->ny > 65536 || g->nz > 65536) return fail(XS_ERR_INVALID_ARG, "grid extent too large");
+    return XS_OK;
+}
+
+GridDesc to_desc(const xs_qgrid* g) { return GridDesc{g->nx0, g->nx, g->ny0, g->ny, g->nz0, g->nz}; }
+
+}  // namespace
+
+extern "C" {
+
+const char* xs_version(void) { return "xs 0.1 (sm_103a)"; }
+
+const char* xs_last_error(void) { return g_last_error.c_str(); }
+
+xs_status xs_context_create(const xs_allocator* allocator, xs_context** out) {
+    if (!out) return fail(XS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (allocator && (!allocator->alloc || !allocator->free))
+        return fail(XS_ERR_INVALID_ARG, "allocator needs both alloc and free");
+    xs_context* ctx = new xs_context();
+    if (allocator) {
+        ctx->alloc = *allocator;
+        ctx->has_alloc = true;
+    }
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return fail(XS_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+    }
+    ctx->d_err = static_cast<int*>(ctx->raw_alloc(256));
+    if (!ctx->d_err) {
+        delete ctx;
+        return fail(XS_ERR_NO_MEMORY, "error word allocation failed");
+    }
+    e = cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&ctx->ev_copied[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_consumed[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        xs_context_destroy(ctx);
+        return fail(XS_ERR_CUDA, "context setup failed: %s", cudaGetErrorString(e));
+    }
+    *out = ctx;
+    return XS_OK;
+}
+
+xs_status xs_context_destroy(xs_context* ctx) {
+    if (!ctx) return XS_OK;
+    cudaDeviceSynchronize();
+    ctx->raw_free(ctx->ws);
+    ctx->raw_free(ctx->d_err);
+    for (auto& kv : ctx->consts) ctx->raw_free(kv.second.dev);
+    for (int i = 0; i < 2; ++i) {
+        if (ctx->ev_copied[i]) cudaEventDestroy(ctx->ev_copied[i]);
+        if (ctx->ev_consumed[i]) cudaEventDestroy(ctx->ev_consumed[i]);
+    }
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    delete ctx;
+    return XS_OK;
+}
+
+xs_status xs_set_wait_timeout_ns(xs_context* ctx, int64_t ns) {
+    if (!ctx || ns <= 0) return fail(XS_ERR_INVALID_ARG, "bad context or timeout");
+    ctx->timeout_ns = ns;
+    return XS_OK;
+}
+
+xs_status xs_sync_status(xs_context* ctx, void* cuda_stream) {
+    if (!ctx) return fail(XS_ERR_INVALID_ARG, "context is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    XS_CUDA(cudaStreamSynchronize(st));
+    int word = 0;
+    XS_CUDA(cudaMemcpy(&word, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    XS_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    if (word & kDevErrTimeout) return fail(XS_ERR_TIMEOUT, "a kernel wait timed out (device error word %d)", word);
+    if (word & kDevErrNonFinite) return fail(XS_ERR_NUMERIC, "non-finite position or form factor (device error word %d)", word);
+    return XS_OK;
+}
+
+// --------------------------------------------------------------------------
+// intensity
+// --------------------------------------------------------------------------
+
+static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid,
+                                xs_precision prec, float* I_out, float* amp_out, cudaStream_t st,
+                                int chunk_override) {
+    if (!ctx || !traj || !I_out) return fail(XS_ERR_INVALID_ARG, "context, trajectory and I_out are required");
+    xs_status s = check_grid(grid);
+    if (s != XS_OK) return s;
+    if (prec != XS_PREC_FP32_DIRECT && prec != XS_PREC_SPLIT_FP16 && prec != XS_PREC_SPLIT_BF16)
+        return fail(XS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (traj->n_atoms < 0 || traj->n_frames < 0) return fail(XS_ERR_INVALID_ARG, "negative atom or frame count");
+    if (traj->n_atoms > (int64_t)1 << 31) return fail(XS_ERR_INVALID_ARG, "more than 2^31 atoms");
+    if (traj->n_atoms > 0 && (!traj->pos || !traj->f)) return fail(XS_ERR_INVALID_ARG, "positions or form factors are NULL");
+    double hinv[9];
+    if (!invert3(traj->box.h, hinv)) return fail(XS_ERR_INVALID_ARG, "singular or non-finite cell matrix");
+    const GridDesc g = to_desc(grid);
+    const int64_t P = g.pixels();
+    const int64_t T = traj->n_frames;
+    if (P == 0 || T == 0) return XS_OK;
+    const bool use_tc = prec != XS_PREC_FP32_DIRECT;
+    if (use_tc && !tc_supported(g)) return fail(XS_ERR_UNSUPPORTED, "grid not supported by the tensor-core path");
+
+    const bool out_dev = is_device_ptr(I_out) && (!amp_out || is_device_ptr(amp_out));
+    const bool pos_host = traj->pos_on_host != 0;
+    if (traj->n_atoms > 0) {
+        if (pos_host == is_device_ptr(traj->pos))
+            return fail(XS_ERR_INVALID_ARG, "pos_on_host=%d does not match where pos lives", (int)traj->pos_on_host);
+    }
+    Mat3 hm;
+    for (int i = 0; i < 9; ++i) hm.a[i] = hinv[i];
+    const int64_t N = traj->n_atoms;
+    const int64_t n_pad = round_up(N > 0 ? N : 1, 64);
+
+    // frames per chunk: records and (for host positions) staged positions
+    const size_t rec_per_frame = (size_t)n_pad * sizeof(AtomRec);
+    const size_t pos_per_frame = (size_t)N * 3 * sizeof(float);
+    const size_t cap = (size_t)6 << 30;
+    int64_t fchunk = T;
+    if ((size_t)T * rec_per_frame > cap) fchunk = std::max<int64_t>(1, (int64_t)(cap / rec_per_frame));
+    if (pos_host) fchunk = std::min<int64_t>(fchunk, std::max<int64_t>(1, (int64_t)((size_t)1 << 30) / std::max<size_t>(pos_per_frame, 1)));
+    if (fchunk > 65535) fchunk = 65535;
+
+    DirectPlan dplan{};
+    int chunk_stages = 64;
+    if (use_tc) {
+        auto key = std::make_tuple(n_pad, g.nx, g.ny, g.nz, (int)prec);
+        auto it = ctx->tuned_chunk.find(key);
+        if (it != ctx->tuned_chunk.end()) chunk_stages = it->second;
+        if (chunk_override > 0) chunk_stages = chunk_override;
+    } else {
+        dplan = plan_direct(n_pad, fchunk, g, ctx->num_sms);
+    }
+
+    // workspace layout
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        size_t o = round_up((int64_t)off, 256);
+        off = o + bytes;
+        return o;
+    };
+    const size_t o_rec = carve((size_t)fchunk * rec_per_frame);
+    const size_t o_part = carve(use_tc ? 0 : dplan.partial_bytes);
+    const size_t o_pos0 = carve(pos_host ? (size_t)fchunk * pos_per_frame : 0);
+    const size_t o_pos1 = carve(pos_host ? (size_t)fchunk * pos_per_frame : 0);
+    const size_t o_f = carve(pos_host ? (size_t)N * sizeof(float) : 0);
+    const size_t o_I = carve(out_dev ? 0 : (size_t)fchunk * P * sizeof(float));
+    const size_t o_amp = carve(out_dev || !amp_out ? 0 : (size_t)fchunk * P * 2 * sizeof(float));
+    s = ensure_ws(ctx, off + 256);
+    if (s != XS_OK) return s;
+    char* ws = static_cast<char*>(ctx->ws);
+    AtomRec* rec = reinterpret_cast<AtomRec*>(ws + o_rec);
+    float* pos_stage[2] = {reinterpret_cast<float*>(ws + o_pos0), reinterpret_cast<float*>(ws + o_pos1)};
+    const float* f_dev = traj->f;
+    if (pos_host && N > 0) {
+        XS_CUDA(cudaMemcpyAsync(ws + o_f, traj->f, (size_t)N * sizeof(float), cudaMemcpyHostToDevice, st));
+        f_dev = reinterpret_cast<float*>(ws + o_f);
+    }
+
+    const int64_t n_chunks = (T + fchunk - 1) / fchunk;
+    if (pos_host && N > 0) {
+        // the copy stream starts after everything already on the caller's stream
+        XS_CUDA(cudaEventRecord(ctx->ev_consumed[0], st));
+        XS_CUDA(cudaEventRecord(ctx->ev_consumed[1], st));
+    }
+    auto issue_copy = [&](int64_t c) -> xs_status {
+        const int64_t t0 = c * fchunk, nf = std::min(fchunk, T - t0);
+        const int b = (int)(c & 1);
+        XS_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_consumed[b], 0));
+        XS_CUDA(cudaMemcpyAsync(pos_stage[b], traj->pos + (size_t)t0 * N * 3, (size_t)nf * pos_per_frame,
+                                cudaMemcpyHostToDevice, ctx->copy_stream));
+        XS_CUDA(cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream));
+        return XS_OK;
+    };
+    if (pos_host && N > 0) {
+        s = issue_copy(0);
+        if (s != XS_OK) return s;
+    }
+    for (int64_t c = 0; c < n_chunks; ++c) {
+        const int64_t t0 = c * fchunk, nf = std::min(fchunk, T - t0);
+        float* Ic = out_dev ? I_out + (size_t)t0 * P : reinterpret_cast<float*>(ws + o_I);
+        float* Ac = amp_out ? (out_dev ? amp_out + (size_t)t0 * P * 2 : reinterpret_cast<float*>(ws + o_amp)) : nullptr;
+        if (N == 0) {
+            XS_CUDA(cudaMemsetAsync(Ic, 0, (size_t)nf * P * sizeof(float), st));
+            if (Ac) XS_CUDA(cudaMemsetAsync(Ac, 0, (size_t)nf * P * 2 * sizeof(float), st));
+        } else {
+            const float* pos_c;
+            if (pos_host) {
+                const int b = (int)(c & 1);
+                if (c + 1 < n_chunks) {
+                    s = issue_copy(c + 1);
+                    if (s != XS_OK) return s;
+                }
+                XS_CUDA(cudaStreamWaitEvent(st, ctx->ev_copied[b], 0));
+                pos_c = pos_stage[b];
+            } else {
+                pos_c = traj->pos + (size_t)t0 * N * 3;
+            }
+            XS_CUDA(launch_phase(pos_c, f_dev, N, nf, n_pad, hm, rec, ctx->d_err, st));
+            if (pos_host) XS_CUDA(cudaEventRecord(ctx->ev_consumed[c & 1], st));
+            if (use_tc) {
+                TcPlan pc = plan_tc(n_pad, nf, g, ctx->num_sms, chunk_stages);
+                XS_CUDA(launch_tc(rec, n_pad, nf, g, pc, prec == XS_PREC_SPLIT_BF16, Ic, Ac, ctx->d_err,
+                                  ctx->timeout_ns, st));
+            } else {
+                DirectPlan pc = plan_direct(n_pad, nf, g, ctx->num_sms);
+                if (pc.partial_bytes > dplan.partial_bytes) return fail(XS_ERR_CUDA, "internal: partial plan grew");
+                XS_CUDA(launch_direct(rec, n_pad, nf, g, pc, ws + o_part, Ic, Ac, st));
+            }
+        }
+        if (!out_dev) {
+            XS_CUDA(cudaMemcpyAsync(I_out + (size_t)t0 * P, Ic, (size_t)nf * P * sizeof(float), cudaMemcpyDeviceToHost, st));
+            if (amp_out)
+                XS_CUDA(cudaMemcpyAsync(amp_out + (size_t)t0 * P * 2, Ac, (size_t)nf * P * 2 * sizeof(float),
+                                        cudaMemcpyDeviceToHost, st));
+            XS_CUDA(cudaStreamSynchronize(st));
+        }
+    }
+    if (pos_host && N > 0) XS_CUDA(cudaStreamSynchronize(st));  // host buffers may be released on return
+    return XS_OK;
+}
+
+xs_status xs_intensity(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, xs_precision prec,
+                       float* I_out, float* amp_out, void* cuda_stream) {
+    return intensity_impl(ctx, traj, grid, prec, I_out, amp_out, static_cast<cudaStream_t>(cuda_stream), 0);
+}
+
+xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, int32_t n_traj,
+                               xs_precision prec, float* const* I_out, void* cuda_stream) {
+    if (!ctx || !traj || !grid || !I_out || n_traj < 1) return fail(XS_ERR_INVALID_ARG, "bad batched arguments");
+    for (int32_t i = 0; i < n_traj; ++i) {
+        if (traj[i].pos_on_host) return fail(XS_ERR_INVALID_ARG, "batched trajectories need device positions");
+        xs_status s = intensity_impl(ctx, &traj[i], &grid[i], prec, I_out[i], nullptr,
+                                     static_cast<cudaStream_t>(cuda_stream), 0);
+        if (s != XS_OK) return s;
+    }
+    return XS_OK;
+}
+
+xs_status xs_tune(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, xs_precision prec, void* cuda_stream) {
+    if (!ctx || !traj || !grid) return fail(XS_ERR_INVALID_ARG, "bad tune arguments");
+    if (prec == XS_PREC_FP32_DIRECT) return XS_OK;
+    if (traj->pos_on_host) return fail(XS_ERR_INVALID_ARG, "tuning needs device positions");
+    xs_status s = check_grid(grid);
+    if (s != XS_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const GridDesc g = to_desc(grid);
+    const int64_t P = g.pixels();
+    const int64_t T = std::min<int64_t>(traj->n_frames, 64);
+    if (P == 0 || T == 0 || traj->n_atoms == 0) return XS_OK;
+    XS_CUDA(cudaStreamSynchronize(st));
+    float* out = static_cast<float*>(ctx->raw_alloc((size_t)T * P * sizeof(float)));
+    if (!out) return fail(XS_ERR_NO_MEMORY, "tuning buffer allocation failed");
+    xs_traj sub = *traj;
+    sub.n_frames = T;
+    cudaEvent_t e0, e1;
+    XS_CUDA(cudaEventCreate(&e0));
+    XS_CUDA(cudaEventCreate(&e1));
+    const int cands[] = {16, 32, 64, 128, 256};
+    int best = 64;
+    float best_ms = 1e30f;
+    for (int c : cands) {
+        s = intensity_impl(ctx, &sub, grid, prec, out, nullptr, st, c);  // warm-up
+        if (s != XS_OK) break;
+        XS_CUDA(cudaEventRecord(e0, st));
+        s = intensity_impl(ctx, &sub, grid, prec, out, nullptr, st, c);
+        if (s != XS_OK) break;
+        XS_CUDA(cudaEventRecord(e1, st));
+        XS_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        XS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    ctx->raw_free(out);
+    if (s != XS_OK) return s;
+    const int64_t n_pad = round_up(traj->n_atoms, 64);
+    ctx->tuned_chunk[std::make_tuple(n_pad, g.nx, g.ny, g.nz, (int)prec)] = best;
+    return xs_sync_status(ctx, cuda_stream);
+}
+
+// --------------------------------------------------------------------------
+// g2
+// --------------------------------------------------------------------------
+
+xs_status xs_g2(xs_context* ctx, const float* I, int64_t T, int64_t P, const int32_t* taus, int32_t n_tau,
+                double* g2_out, double* mean_out, void* cuda_stream) {
+    if (!ctx || !I || !taus || !g2_out) return fail(XS_ERR_INVALID_ARG, "context, I, taus and g2_out are required");
+    if (T < 1 || P < 0 || n_tau < 0) return fail(XS_ERR_INVALID_ARG, "need T >= 1, P >= 0, n_tau >= 0");
+    for (int32_t k = 0; k < n_tau; ++k)
+        if (taus[k] < 0 || taus[k] >= T) return fail(XS_ERR_INVALID_ARG, "delay %d outside [0, T)", taus[k]);
+    if (P == 0 || n_tau == 0) return XS_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<char> blob;
+    const size_t o_tau = push(blob, taus, (size_t)n_tau);
+    void* d = nullptr;
+    xs_status s = upload_const(ctx, "g2", blob, st, &d);
+    if (s != XS_OK) return s;
+    const int32_t* d_taus = reinterpret_cast<const int32_t*>(static_cast<char*>(d) + o_tau);
+    XS_CUDA(launch_g2(I, T, P, d_taus, n_tau, g2_out, mean_out, st));
+    return XS_OK;
+}
+
+// --------------------------------------------------------------------------
+// XSVS contrast
+// --------------------------------------------------------------------------
+
+// ring (1..n_rings) of each pixel, 0 when in none; shared by the contrast call
+// and the host-side layout export below
+static xs_status ring_of_pixels(const xs_qgrid* grid, const xs_box* box, double ring_width, int32_t n_rings,
+                                std::vector<int32_t>& ring) {
+    double hinv[9];
+    if (!invert3(box->h, hinv)) return fail(XS_ERR_INVALID_ARG, "singular or non-finite cell matrix");
+    const double* h = box->h;
+    const double det = h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
+                       h[2] * (h[3] * h[7] - h[4] * h[6]);
+    const double two_pi = 6.283185307179586476925286766559;
+    const double delta = two_pi / std::cbrt(std::fabs(det));
+    const int64_t P = (int64_t)grid->nx * grid->ny * grid->nz;
+    ring.assign((size_t)P, 0);
+    int64_t p = 0;
+    for (int iz = 0; iz < grid->nz; ++iz)
+        for (int iy = 0; iy < grid->ny; ++iy)
+            for (int ix = 0; ix < grid->nx; ++ix, ++p) {
+                const double n[3] = {(double)(grid->nx0 + ix), (double)(grid->ny0 + iy), (double)(grid->nz0 + iz)};
+                double q2 = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    const double qa = two_pi * (hinv[0 * 3 + a] * n[0] + hinv[1 * 3 + a] * n[1] + hinv[2 * 3 + a] * n[2]);
+                    q2 += qa * qa;
+                }
+                const double x = std::sqrt(q2) / delta;
+                const double r = std::floor(x + 0.5);
+                if (r >= 1.0 && r <= (double)n_rings && x >= r - ring_width / 2.0 && x < r + ring_width / 2.0)
+                    ring[(size_t)p] = (int32_t)r;
+            }
+    return XS_OK;
+}
+
+xs_status xs_ring_index(const xs_qgrid* grid, const xs_box* box, double ring_width, int32_t n_rings,
+                        int32_t* ring_out) {
+    if (!grid || !box || !ring_out) return fail(XS_ERR_INVALID_ARG, "grid, box and ring_out are required");
+    xs_status s = check_grid(grid);
+    if (s != XS_OK) return s;
+    if (!(ring_width > 0.0 && ring_width <= 1.0) || n_rings < 0) return fail(XS_ERR_INVALID_ARG, "bad ring parameters");
+    std::vector<int32_t> ring;
+    s = ring_of_pixels(grid, box, ring_width, n_rings, ring);
+    if (s != XS_OK) return s;
+    if (!ring.empty()) std::memcpy(ring_out, ring.data(), ring.size() * sizeof(int32_t));
+    return XS_OK;
+}
+
+xs_status xs_xsvs_contrast(xs_context* ctx, const float* I, int64_t T, const xs_qgrid* grid, const xs_box* box,
+                           const int32_t* Ks, int32_t n_K, double ring_width, int32_t n_rings, double* beta_out,
+                           int32_t* ring_count_out, void* cuda_stream) {
+    if (!ctx || !I || !box || !Ks || !beta_out) return fail(XS_ERR_INVALID_ARG, "missing argument");
+    xs_status s = check_grid(grid);
+    if (s != XS_OK) return s;
+    if (T < 1 || n_K < 0 || n_rings < 0) return fail(XS_ERR_INVALID_ARG, "need T >= 1, n_K >= 0, n_rings >= 0");
+    if (!(ring_width > 0.0 && ring_width <= 1.0)) return fail(XS_ERR_INVALID_ARG, "ring_width must be in (0, 1]");
+    for (int32_t k = 0; k < n_K; ++k)
+        if (Ks[k] < 1 || Ks[k] > T) return fail(XS_ERR_INVALID_ARG, "window length %d outside [1, T]", Ks[k]);
+    if (n_K == 0 || n_rings == 0) return XS_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<int32_t> ring;
+    s = ring_of_pixels(grid, box, ring_width, n_rings, ring);
+    if (s != XS_OK) return s;
+    const int64_t P = (int64_t)ring.size();
+    // pixels grouped ring by ring (stable within a ring)
+    std::vector<int32_t> count((size_t)n_rings, 0);
+    for (int32_t r : ring)
+        if (r > 0) ++count[(size_t)r - 1];
+    std::vector<int64_t> start((size_t)n_rings + 1, 0);
+    for (int r = 0; r < n_rings; ++r) start[(size_t)r + 1] = start[(size_t)r] + count[(size_t)r];
+    const int64_t n_in = start[(size_t)n_rings];
+    std::vector<int32_t> perm((size_t)n_in);
+    {
+        std::vector<int64_t> fill(start.begin(), start.end() - 1);
+        for (int64_t p = 0; p < P; ++p)
+            if (ring[(size_t)p] > 0) perm[(size_t)fill[(size_t)ring[(size_t)p] - 1]++] = (int32_t)p;
+    }
+    constexpr int kChunk = 128;
+    std::vector<int32_t> chunks;  // int4 records (ring, start, count, 0)
+    std::vector<int32_t> first((size_t)n_rings + 1, 0);
+    for (int r = 0; r < n_rings; ++r) {
+        first[(size_t)r] = (int32_t)(chunks.size() / 4);
+        for (int64_t a = start[(size_t)r]; a < start[(size_t)r + 1]; a += kChunk) {
+            chunks.push_back(r + 1);
+            chunks.push_back((int32_t)a);
+            chunks.push_back((int32_t)std::min<int64_t>(kChunk, start[(size_t)r + 1] - a));
+            chunks.push_back(0);
+        }
+    }
+    const int n_chunks = (int)(chunks.size() / 4);
+    first[(size_t)n_rings] = n_chunks;
+    std::vector<int64_t> kw_off((size_t)n_K + 1, 0);
+    for (int k = 0; k < n_K; ++k) kw_off[(size_t)k + 1] = kw_off[(size_t)k] + T / Ks[k];
+    const int64_t n_kw = kw_off[(size_t)n_K];
+    if (ring_count_out) std::memcpy(ring_count_out, count.data(), count.size() * sizeof(int32_t));
+
+    std::vector<char> blob;
+    const int64_t key[2] = {T, P};
+    push(blob, key, 2);
+    const size_t o_perm = push(blob, perm.data(), perm.size());
+    const size_t o_chunks = push(blob, chunks.data(), chunks.size());
+    const size_t o_K = push(blob, Ks, (size_t)n_K);
+    const size_t o_kw = push(blob, kw_off.data(), kw_off.size());
+    const size_t o_first = push(blob, first.data(), first.size());
+    const size_t o_count = push(blob, count.data(), count.size());
+    void* d = nullptr;
+    s = upload_const(ctx, "xsvs", blob, st, &d);
+    if (s != XS_OK) return s;
+    char* dc = static_cast<char*>(d);
+
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        size_t o = round_up((int64_t)off, 256);
+        off = o + bytes;
+        return o;
+    };
+    const size_t o_prefix = carve((size_t)(T + 1) * n_in * sizeof(double));
+    const size_t o_partial = carve((size_t)n_kw * n_chunks * sizeof(double2));
+    s = ensure_ws(ctx, off + 256);
+    if (s != XS_OK) return s;
+    char* ws = static_cast<char*>(ctx->ws);
+    XS_CUDA(launch_xsvs(I, T, P, reinterpret_cast<const int32_t*>(dc + o_perm), reinterpret_cast<const int4*>(dc + o_chunks),
+                        n_chunks, n_in, reinterpret_cast<const int32_t*>(dc + o_K), reinterpret_cast<const int64_t*>(dc + o_kw),
+                        n_K, n_kw, reinterpret_cast<const int32_t*>(dc + o_first), reinterpret_cast<const int32_t*>(dc + o_count),
+                        n_rings, reinterpret_cast<double*>(ws + o_prefix), reinterpret_cast<double2*>(ws + o_partial),
+                        beta_out, st));
+    return XS_OK;
+}
+
+// --------------------------------------------------------------------------
+// adjoint
+// --------------------------------------------------------------------------
+
+xs_status xs_intensity_backward(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, const float* amp,
+                                const float* dL_dI, float* dL_dr_out, void* cuda_stream) {
+    if (!ctx || !traj || !amp || !dL_dI || !dL_dr_out) return fail(XS_ERR_INVALID_ARG, "missing argument");
+    xs_status s = check_grid(grid);
+    if (s != XS_OK) return s;
+    if (traj->n_frames != 1) return fail(XS_ERR_INVALID_ARG, "the adjoint takes exactly one frame");
+    if (traj->pos_on_host) return fail(XS_ERR_INVALID_ARG, "the adjoint needs device positions");
+    if (traj->n_atoms < 0) return fail(XS_ERR_INVALID_ARG, "negative atom count");
+    if (traj->n_atoms == 0) return XS_OK;
+    if (!traj->pos || !traj->f) return fail(XS_ERR_INVALID_ARG, "positions or form factors are NULL");
+    double hinv[9];
+    if (!invert3(traj->box.h, hinv)) return fail(XS_ERR_INVALID_ARG, "singular or non-finite cell matrix");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const GridDesc g = to_desc(grid);
+    const int64_t N = traj->n_atoms;
+    const int64_t n_pad = round_up(N, 64);
+    if (g.pixels() == 0) {
+        XS_CUDA(cudaMemsetAsync(dL_dr_out, 0, (size_t)N * 3 * sizeof(float), st));
+        return XS_OK;
+    }
+    Mat3 hm;
+    for (int i = 0; i < 9; ++i) hm.a[i] = hinv[i];
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        size_t o = round_up((int64_t)off, 256);
+        off = o + bytes;
+        return o;
+    };
+    const size_t o_rec = carve((size_t)n_pad * sizeof(AtomRec));
+    const size_t o_h = carve(adjoint_workspace_bytes(g));
+    s = ensure_ws(ctx, off + 256);
+    if (s != XS_OK) return s;
+    char* ws = static_cast<char*>(ctx->ws);
+    AtomRec* rec = reinterpret_cast<AtomRec*>(ws + o_rec);
+    XS_CUDA(launch_phase(traj->pos, traj->f, N, 1, n_pad, hm, rec, ctx->d_err, st));
+    XS_CUDA(launch_adjoint(rec, N, n_pad, g, hm, amp, dL_dI, ws + o_h, dL_dr_out, st));
+    return XS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,54 @@
+// Device helpers shared by the kernels of libxs (CUDA path only).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace xs {
+
+// Bits of the device error word (one int per context).
+enum : int {
+    kDevErrTimeout = 1,    // a bounded wait expired
+    kDevErrNonFinite = 2,  // a non-finite position or form factor was read
+};
+
+// 3x3 inverse cell matrix (row-major), passed by value to kernels.
+struct Mat3 {
+    double a[9];
+};
+
+// Per-atom record produced by the phase kernel: the fractional coordinate of
+// each axis as a 32-bit turn count U = round(frac(s) * 2^32) mod 2^32, and the
+// form factor's bits.  With integer Miller indices n, n*U mod 2^32 is the
+// phase n*s in turns reduced modulo one turn exactly (Sec. 3.1: for q on the
+// reciprocal lattice the periodic image of an atom does not matter).
+struct AtomRec {
+    uint32_t ux, uy, uz;
+    float f;
+};
+
+__device__ __forceinline__ void set_dev_error(int* err, int bit) {
+    if (err) atomicOr(err, bit);
+}
+
+// frac(s) in [0,1) quantised to 32-bit turns (FP64 throughout).
+__device__ __forceinline__ uint32_t turns_u32(double s) {
+    double fr = s - floor(s);
+    // fr*2^32 < 2^32; rounding may give 2^32, which wraps to 0 (the same turn)
+    unsigned long long u = __double2ull_rn(fr * 4294967296.0);
+    return (uint32_t)u;
+}
+
+// Phase factor exp(+i 2 pi P / 2^32) for a 32-bit turn count P.
+__device__ __forceinline__ void phase_to_cs(uint32_t P, float& c, float& s) {
+    float x = (float)(int32_t)P * 0x1p-31f;  // P/2^31 in [-1, 1): angle = pi * x
+    sincospif(x, &s, &c);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+}  // namespace xs

@@ -1,0 +1,69 @@
+// Internal launch interface between the C ABI (xs_api.cu) and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "xs_common.cuh"
+
+namespace xs {
+
+struct GridDesc {
+    int nx0, nx, ny0, ny, nz0, nz;
+    __host__ __device__ int64_t pixels() const { return (int64_t)nx * ny * nz; }
+};
+
+// ---- phase records (fractional coordinates as 32-bit turns) -------------
+// rec [n_frames][n_pad]; atoms >= n_atoms get f = 0 and U = 0.
+cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int64_t n_frames,
+                         int64_t n_pad, const Mat3& hinv, AtomRec* rec, int* err,
+                         cudaStream_t st);
+
+// ---- plain FP32 direct sum ----------------------------------------------
+struct DirectPlan {
+    int splits;            // atom splits (partials merged in FP64 by a second kernel)
+    int64_t atoms_per_split;
+    size_t partial_bytes;  // workspace for the partial amplitudes
+};
+DirectPlan plan_direct(int64_t n_pad, int64_t n_frames, const GridDesc& g, int num_sms);
+cudaError_t launch_direct(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g,
+                          const DirectPlan& plan, void* partial, float* I, float* amp,
+                          cudaStream_t st);
+
+// ---- tensor-core split-precision contraction ----------------------------
+struct TcPlan {
+    int chunk_stages;      // stages of 64 atoms accumulated in TMEM before a flush
+    int grid;              // persistent CTAs
+    int tiles_x, tiles_y;  // 128-pixel tiles per frame plane along x and y
+};
+bool tc_supported(const GridDesc& g);
+TcPlan plan_tc(int64_t n_pad, int64_t n_frames, const GridDesc& g, int num_sms, int chunk_stages);
+cudaError_t launch_tc(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g,
+                      const TcPlan& plan, bool bf16, float* I, float* amp, int* err,
+                      int64_t timeout_ns, cudaStream_t st);
+
+// ---- g2 -----------------------------------------------------------------
+cudaError_t launch_g2(const float* I, int64_t T, int64_t P, const int32_t* d_taus, int n_tau,
+                      double* g2, double* mean, cudaStream_t st);
+
+// ---- XSVS contrast --------------------------------------------------------
+struct XsvsLayout {
+    int64_t n_in_rings;   // pixels that belong to a ring
+    int n_chunks;         // (ring, pixel range) chunks
+    int64_t n_kw;         // sum over K of floor(T/K)
+};
+cudaError_t launch_xsvs(const float* I, int64_t T, int64_t P, const int32_t* d_perm,
+                        const int4* d_chunks, int n_chunks, int64_t n_in_rings,
+                        const int32_t* d_K, const int64_t* d_kw_off, int n_K, int64_t n_kw,
+                        const int32_t* d_ring_first_chunk, const int32_t* d_ring_count,
+                        int n_rings, double* prefix, double2* partial, double* beta,
+                        cudaStream_t st);
+
+// ---- adjoint --------------------------------------------------------------
+size_t adjoint_workspace_bytes(const GridDesc& g);
+cudaError_t launch_adjoint(const AtomRec* rec, int64_t n_atoms, int64_t n_pad, const GridDesc& g,
+                           const Mat3& hinv, const float* amp, const float* dL_dI,
+                           void* workspace, float* grad, cudaStream_t st);
+
+}  // namespace xs
