@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Throughput of the direct-method XPCS/XSVS hot path on GB300.
+
+One step = the whole path over one batch: the intensity I(q,t) of every
+frame on the detector plane (split-FP16 tensor-core contraction over atoms,
+Sec. 3.1 Algorithm 1), its g2 on 64 log-spaced delays (Sec. 2.3) and its
+XSVS contrast on 1-2-5 window lengths over unit |q| rings (Sec. 2.3).
+Workload: 256,000-atom FCC crystal (a = 4 A, L = 160 A, thermal 0.15 A,
+f in {1.0, 0.6}), 1,000 Brownian frames (0.05 A), 128 x 128 plane at n_z = 0.
+
+Metric: atom*pixel*frames per second (N * P * T / step time), whole job.
+With --gpus N (torchrun), every rank runs its own replica of the workload
+(independent problems, no collective on the data path): weak scaling.
+
+--impl reference times the FP64 CPU oracle on bounded samples of the same
+workload on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "atom*pixel*frames/s"
+FALLBACK_PEAK = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=1000, help="frames of the workload (default: all 1,000)")
+    ap.add_argument("--precision", choices=["fp16", "bf16"], default="fp16")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except (OSError, ValueError):
+        return dict(FALLBACK_PEAK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.fh = None
+
+    def start(self):
+        self.fh = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu_id], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.flush()
+        self.fh.seek(0)
+        rows = [ln.strip().split(",") for ln in self.fh.read().splitlines() if ln.strip()]
+        os.unlink(self.fh.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 8:
+                continue
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2204_13241_gb300 import workloads as wl
+
+    oracle.build()
+    traj, grid = wl.config1(keep=[0])
+    m = grid.miller()
+    n_pix = 1024
+    rng = np.random.default_rng(7)
+    cores = oracle.max_threads()
+    per_step = traj.n_atoms * n_pix
+    for _ in range(args.warmup):
+        sel = rng.choice(m.shape[0], n_pix, replace=False)
+        oracle.intensity(traj.pos[:1], traj.f, traj.box, m[sel])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sel = rng.choice(m.shape[0], n_pix, replace=False)
+        oracle.intensity(traj.pos[:1], traj.f, traj.box, m[sel])
+    dt = (time.perf_counter() - t0) / args.steps
+    value = per_step / dt
+    sample = f"frame 0, {n_pix} random pixels of the 128^2 plane, {traj.n_atoms} atoms, per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "fcc256k_T1000_plane128", "n_atoms": traj.n_atoms, "n_frames": 1000,
+                   "grid": "128x128 (n_z=0)", "sample_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_2204_13241_gb300 import build as xbuild
+    from paper_2204_13241_gb300 import workloads as wl
+
+    if rank == 0 or not xbuild.up_to_date():
+        xbuild.build()
+    from paper_2204_13241_gb300 import api as xs
+
+    traj, grid = wl.config1(n_frames=args.frames)
+    T, N, P = traj.pos.shape[0], traj.n_atoms, grid.n_pixels
+    taus = [int(t) for t in wl.log_delays(T, 64)]
+    Ks = [int(k) for k in wl.window_list_125(T)]
+    R = wl.rings_for_plane(grid)
+    box = traj.box
+    pos_d = torch.from_numpy(traj.pos).to(f"cuda:{dev}")
+    f_d = torch.from_numpy(traj.f).to(f"cuda:{dev}")
+    I = torch.empty((T, 1, grid.ny, grid.nx), dtype=torch.float32, device="cuda")
+    ctx = xs.Context.get()
+
+    def step(pos, f):
+        xs.intensity(pos, f, box, grid, args.precision, out=I)
+        g, mean = xs.g2(I.view(T, -1), taus)
+        beta, counts = xs.xsvs_contrast(I, grid, box, Ks, R)
+        return g, mean, beta
+
+    for _ in range(max(args.warmup, 1)):
+        step(pos_d, f_d)
+    ctx.sync_status()
+
+    # ---- timed region: inputs resident in HBM (7 GB of positions and phase
+    # records per step, far above the 129 MB L2) -------------------------------
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid else str(dev))
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
+    ctx.profile_read("")
+    launches0 = ctx.launch_count()
+    barrier()
+    sampler.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(pos_d, f_d)
+    ev1.record(stream)
+    ev1.synchronize()
+    clocks = sampler.stop()
+    barrier()
+    launches = ctx.launch_count() - launches0
+    tc_ms, tc_n = ctx.profile_read("tc")
+    all_ms, all_n = ctx.profile_read("")
+    ctx.profile(False)
+    ctx.sync_status()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ms)
+    units = float(N) * P * T
+    value = units * world / (ms * 1e-3)
+
+    peaks, peak_src = _peaks()
+    tc_launch_ms = tc_ms / max(tc_n, 1)
+    alg_flops = 8.0 * units           # one complex multiply-add per atom*pixel*frame
+    exe_flops = 24.0 * units          # 4 real products x 3 split passes x 2 flops
+    peak = float(peaks.get("bf16_tflops_sustained", FALLBACK_PEAK["bf16_tflops_sustained"]))
+    achieved = alg_flops / (tc_launch_ms * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "tc_kernel (split-FP16 contraction)", "kernel_ms_per_launch": tc_launch_ms,
+                "peak_source": f"{peak_src} bf16 sustained (fp16 dense rate = bf16)",
+                "executed_tflops": exe_flops / (tc_launch_ms * 1e-3) / 1e12,
+                "executed_frac": exe_flops / (tc_launch_ms * 1e-3) / 1e12 / peak,
+                "share_of_step": tc_ms / max(tc_ms + all_ms, 1e-9)}
+
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16-split (hi+lo), f32 accumulate", "data": "synthetic",
+            "config": {"workload": "fcc256k_T1000_plane128", "n_atoms": N, "n_frames": T,
+                       "grid": f"{grid.nx}x{grid.ny} (n_z=0)", "precision": f"split_{args.precision}",
+                       "n_tau": len(taus), "window_lengths": Ks, "rings": R,
+                       "l2": "inputs larger than L2 (3.1 GB positions + 4.1 GB phase records read per step)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "gpu_launches": launches, "clocks": clocks}
+
+    # ---- end to end through the public API with host buffers ------------------
+    if not args.no_e2e:
+        pos_h = torch.from_numpy(traj.pos).pin_memory()
+        f_h = torch.from_numpy(traj.f).pin_memory()
+        I_h = torch.empty(I.shape, dtype=torch.float32).pin_memory()
+        g_h = torch.empty((len(taus), P), dtype=torch.float64).pin_memory()
+        b_h = torch.empty((len(Ks), R), dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            g, mean, beta = step(pos_h, f_h)
+            I_h.copy_(I, non_blocking=True)
+            g_h.copy_(g, non_blocking=True)
+            b_h.copy_(beta, non_blocking=True)
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        barrier()
+        e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
+        ctx.sync_status()
+        h2d = traj.pos.nbytes + traj.f.nbytes
+        d2h = I_h.numel() * 4 + g_h.numel() * 8 + b_h.numel() * 8
+        line["e2e"] = {"value": units * world / (e_ms * 1e-3), "unit": METRIC, "ms_per_step": e_ms,
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        del pos_h
+
+    # ---- plain FP32 direct-sum kernel on the same workload (first 32 frames) ---
+    if not args.no_fp32 and rank == 0:
+        nf = min(32, T)
+        sub = pos_d[:nf].contiguous()
+        I32 = torch.empty((nf, 1, grid.ny, grid.nx), dtype=torch.float32, device="cuda")
+        xs.intensity(sub, f_d, box, grid, "fp32", out=I32)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xs.intensity(sub, f_d, box, grid, "fp32", out=I32)
+        e1.record(stream)
+        e1.synchronize()
+        ctx.sync_status()
+        rate32 = float(N) * P * nf / (e0.elapsed_time(e1) * 1e-3)
+        ours_rate = units / (tc_launch_ms * 1e-3)
+        line["fp32_direct"] = {"value": rate32, "unit": METRIC, "frames": nf,
+                               "tc_kernel_rate": ours_rate, "speedup_tc_vs_fp32": ours_rate / rate32}
+
+    # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N = 1) ----
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        import oracle
+
+        oracle.build()
+        m = grid.miller()
+        sel = np.arange(0, m.shape[0], 2)
+        t0 = time.perf_counter()
+        ref = oracle.intensity(traj.pos[:1], traj.f, traj.box, m[sel])
+        dt = time.perf_counter() - t0
+        got = I.view(T, -1)[0].cpu().numpy().astype(np.float64)[sel]
+        nz = np.any(m[sel] != 0, axis=1)
+        e_I = float(np.linalg.norm(got[nz] - ref[0, nz]) / np.linalg.norm(ref[0, nz]))
+        line["cpu_baseline"] = {"value": traj.n_atoms * sel.size / dt, "unit": METRIC,
+                                "cores": oracle.max_threads(), "kind": "oracle",
+                                "sample": f"frame 0, {sel.size} of {m.shape[0]} pixels (every 2nd), "
+                                          f"{traj.n_atoms} atoms, {dt:.1f} s"}
+        line["accuracy"] = {"e_I_frame0": e_I, "against": "oracle on the cpu_baseline sample"}
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

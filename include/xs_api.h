@@ -198,6 +198,19 @@ XS_API xs_status xs_sync_status(xs_context* ctx, void* cuda_stream);
  * kernel whose wait can never complete. */
 XS_API xs_status xs_set_wait_timeout_ns(xs_context* ctx, int64_t ns);
 
+/* Tracing.  When enabled, every kernel launch of the context is bracketed by
+ * CUDA events recorded on the launching stream.  xs_profile_read waits for
+ * those events and returns, for launch groups whose name starts with `prefix`
+ * ("" = all), the summed device time in milliseconds and the number of
+ * kernels since the last read, and forgets those records (others stay).  Launch groups: "phase"
+ * (phase records, 1 kernel), "direct" (FP32 direct sum, 1-2), "tc"
+ * (tensor-core contraction, 1), "g2" (1), "xsvs" (prefix, windows,
+ * finalize: 1-3), "adjoint" (2).  xs_launch_count returns the number of kernels the
+ * context has launched since it was created (tracing on or off). */
+XS_API xs_status xs_profile_enable(xs_context* ctx, int32_t on);
+XS_API xs_status xs_profile_read(xs_context* ctx, const char* prefix, double* total_ms, int64_t* launches);
+XS_API xs_status xs_launch_count(xs_context* ctx, int64_t* count);
+
 /* Library version string. */
 XS_API const char* xs_version(void);
 

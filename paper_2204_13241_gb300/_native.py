@@ -18,7 +18,8 @@ PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
 
 EXPORTS = ["xs_context_create", "xs_context_destroy", "xs_intensity", "xs_intensity_batched", "xs_g2",
            "xs_xsvs_contrast", "xs_ring_index", "xs_intensity_backward", "xs_tune", "xs_last_error",
-           "xs_sync_status", "xs_set_wait_timeout_ns", "xs_version"]
+           "xs_sync_status", "xs_set_wait_timeout_ns", "xs_version", "xs_profile_enable", "xs_profile_read",
+           "xs_launch_count"]
 
 
 class XsError(RuntimeError):
@@ -80,6 +81,9 @@ def load() -> ctypes.CDLL:
         "xs_sync_status": ([P, P], st),
         "xs_set_wait_timeout_ns": ([P, I64], st),
         "xs_version": ([], ctypes.c_char_p),
+        "xs_profile_enable": ([P, I32], st),
+        "xs_profile_read": ([P, ctypes.c_char_p, ctypes.POINTER(D), ctypes.POINTER(I64)], st),
+        "xs_launch_count": ([P, ctypes.POINTER(I64)], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -100,6 +100,22 @@ class Context:
     def set_wait_timeout_ns(self, ns: int) -> None:
         nat.check(self.lib.xs_set_wait_timeout_ns(self.handle, int(ns)))
 
+    def profile(self, on: bool) -> None:
+        """Bracket every launch group with CUDA events on its stream."""
+        nat.check(self.lib.xs_profile_enable(self.handle, 1 if on else 0))
+
+    def profile_read(self, prefix: str = "") -> tuple[float, int]:
+        """(device milliseconds, kernels) of launch groups named `prefix`* since the last read."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        nat.check(self.lib.xs_profile_read(self.handle, prefix.encode(), ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def launch_count(self) -> int:
+        n = ctypes.c_int64()
+        nat.check(self.lib.xs_launch_count(self.handle, ctypes.byref(n)))
+        return n.value
+
 
 def _traj(pos: torch.Tensor, f: torch.Tensor, box) -> tuple[nat.Traj, bool]:
     if pos.dim() == 2:

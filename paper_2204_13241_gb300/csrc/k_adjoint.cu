@@ -157,6 +157,7 @@ cudaError_t launch_adjoint(const AtomRec* rec, int64_t n_atoms, int64_t n_pad, c
     const int64_t P = g.pixels();
     float2* H = static_cast<float2*>(workspace);
     const int64_t hb = min((P + 255) / 256, (int64_t)4096);
+    ++tl_kernel_launches;
     h_kernel<<<(unsigned)hb, 256, 0, st>>>(amp, dL_dI, P, H);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -164,6 +165,7 @@ cudaError_t launch_adjoint(const AtomRec* rec, int64_t n_atoms, int64_t n_pad, c
     e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = n_pad / kAdjAtoms;
+    ++tl_kernel_launches;
     adjoint_kernel<<<(unsigned)blocks, kAdjThreads, smem, st>>>(rec, n_atoms, g, hinv, H, grad);
     return cudaGetLastError();
 }

@@ -3,8 +3,9 @@
 //
 // g2_kernel: one thread per pixel and a group of up to kTauGroup delays.  The
 //   block walks t in order; I[t][p] and I[t+tau][p] are coalesced across the
-//   pixels of a warp.  Products are summed in FP32 over blocks of 64 frames and
-//   the block sums are added in FP64, as is the mean.
+//   pixels of a warp.  Products are summed with compensated (Kahan) FP32
+//   updates over blocks of 64 frames, the block sums are added in FP64; the
+//   mean is summed in FP64 directly.
 //
 // XSVS: pixels are first permuted ring by ring (host-built permutation), then
 //   prefix_kernel   C[t][p'] = sum_{t'<t} I[t'][perm[p']]       (FP64, [T+1][P'])
@@ -35,31 +36,33 @@ g2_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __re
     int tau[kTauGroup];
 #pragma unroll
     for (int k = 0; k < kTauGroup; ++k) tau[k] = s_tau[k];
-    float acc[kTauGroup];
+    float acc[kTauGroup], comp[kTauGroup];
     double dacc[kTauGroup];
 #pragma unroll
     for (int k = 0; k < kTauGroup; ++k) {
-        acc[k] = 0.0f;
+        acc[k] = comp[k] = 0.0f;
         dacc[k] = 0.0;
     }
-    float msum = 0.0f;
     double dmean = 0.0;
     for (int64_t t0 = 0; t0 < T; t0 += kFlush) {
         const int64_t t1 = min(T, t0 + kFlush);
         for (int64_t t = t0; t < t1; ++t) {
             const float x = I[t * P + p];
-            msum += x;
+            dmean += (double)x;
 #pragma unroll
             for (int k = 0; k < kTauGroup; ++k) {
-                if (k < nt && t + tau[k] < T) acc[k] = fmaf(x, I[(t + tau[k]) * P + p], acc[k]);
+                if (k < nt && t + tau[k] < T) {
+                    const float y = fmaf(x, I[(t + tau[k]) * P + p], -comp[k]);
+                    const float s = acc[k] + y;
+                    comp[k] = (s - acc[k]) - y;
+                    acc[k] = s;
+                }
             }
         }
-        dmean += (double)msum;
-        msum = 0.0f;
 #pragma unroll
         for (int k = 0; k < kTauGroup; ++k) {
-            dacc[k] += (double)acc[k];
-            acc[k] = 0.0f;
+            dacc[k] += (double)acc[k] - (double)comp[k];
+            acc[k] = comp[k] = 0.0f;
         }
     }
     const double m = dmean / (double)T;
@@ -151,6 +154,7 @@ cudaError_t launch_g2(const float* I, int64_t T, int64_t P, const int32_t* d_tau
                       double* g2, double* mean, cudaStream_t st) {
     if (P == 0 || n_tau == 0) return cudaSuccess;
     dim3 grid((unsigned)((P + kG2Threads - 1) / kG2Threads), (unsigned)((n_tau + kTauGroup - 1) / kTauGroup));
+    ++tl_kernel_launches;
     g2_kernel<<<grid, kG2Threads, 0, st>>>(I, T, P, d_taus, n_tau, g2, mean);
     return cudaGetLastError();
 }
@@ -162,15 +166,18 @@ cudaError_t launch_xsvs(const float* I, int64_t T, int64_t P, const int32_t* d_p
                         int n_rings, double* prefix, double2* partial, double* beta,
                         cudaStream_t st) {
     if (n_in_rings > 0) {
+        ++tl_kernel_launches;
         prefix_kernel<<<(unsigned)((n_in_rings + 127) / 128), 128, 0, st>>>(I, T, P, d_perm, n_in_rings, prefix);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        ++tl_kernel_launches;
         window_kernel<<<n_chunks, 256, 0, st>>>(prefix, n_in_rings, d_chunks, n_chunks, d_K, d_kw_off, n_K,
                                                 n_kw, partial);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     const int64_t items = (int64_t)n_K * n_rings;
+    ++tl_kernel_launches;
     finalize_kernel<<<(unsigned)((items + 127) / 128), 128, 0, st>>>(partial, n_chunks, d_K, d_kw_off, n_K, T,
                                                                      d_ring_first_chunk, d_ring_count, n_rings, beta);
     return cudaGetLastError();

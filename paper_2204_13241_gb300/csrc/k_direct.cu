@@ -1,15 +1,20 @@
 // Phase records and the plain FP32 direct sum (Algorithm 1, Sec. 3.1).
 //
-// phase_kernel: one thread per (frame, atom).  s = h^-1 r in FP64, then each
-//   axis is reduced to its fractional part and quantised to a 32-bit turn
-//   count.  This is the only FP64 work per atom; every later phase
-//   n_x*U_x + n_y*U_y + n_z*U_z is exact integer arithmetic modulo one turn.
+// phase_kernel: one thread per (frame, atom slot).  s = h^-1 r in FP64, then
+//   each axis is reduced to its fractional part and quantised to a 32-bit
+//   turn count.  This is the only FP64 work per atom (one multiply per axis
+//   for an orthorhombic cell); every later phase n_x*U_x + n_y*U_y + n_z*U_z
+//   is exact integer arithmetic modulo one turn.  Slots may hold the atoms in
+//   a coprime-stride order (k -> k*a mod n_pad): summing in that order turns
+//   the coherent partial sums of an ordered crystal into random walks.
 //
 // direct_kernel: the plain reference-rate kernel.  A block owns 256*PX pixels
 //   of one frame and a range of atoms; atom records are staged in shared
 //   memory 256 at a time.  Each (atom, pixel) costs one exact integer phase,
-//   one FP32 sincospi and two FMAs; FP32 sums over each 256-atom tile are
-//   merged into FP64 accumulators.  Atom ranges ("splits") give enough blocks
+//   one FP32 sincospi and a compensated (Kahan) FP32 update of Re and Im; the
+//   compensated sums of each 256-atom tile are merged into FP64 accumulators.
+//   Plain FP32 sums would drift by ~n*eps on coherent sums (q = 0, Bragg
+//   peaks), where every term has the same sign and size.  Atom ranges ("splits") give enough blocks
 //   for small grids; their FP64 partial amplitudes are added in a fixed order
 //   by reduce_kernel, so results are deterministic.
 #include "xs_internal.h"
@@ -23,33 +28,38 @@ constexpr int kDirectPX = 4;     // pixels per thread
 constexpr int kAtomTile = 256;   // atom records staged per shared-memory tile
 
 __global__ void phase_kernel(const float* __restrict__ pos, const float* __restrict__ f,
-                             int64_t n_atoms, int64_t n_frames, int64_t n_pad, Mat3 hinv,
+                             int64_t n_atoms, int64_t n_frames, int64_t n_pad, Mat3 hinv, PhaseOpts opt,
                              AtomRec* __restrict__ rec, int* err) {
     const int64_t total = n_frames * n_pad;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = i / n_pad, j = i - t * n_pad;
+        const int64_t t = i / n_pad, k = i - t * n_pad;
+        const int64_t j = opt.perm_mul == 1 ? k : (int64_t)(((uint64_t)k * (uint64_t)opt.perm_mul) % (uint64_t)n_pad);
         AtomRec r;
+        r.ux = r.uy = r.uz = 0u;
+        r.f = 0.0f;
         if (j < n_atoms) {
             const float* p = pos + (t * n_atoms + j) * 3;
-            const double x = p[0], y = p[1], z = p[2];
+            const float x = p[0], y = p[1], z = p[2];
             const float fj = f[j];
             if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(fj)) {
                 set_dev_error(err, kDevErrNonFinite);
-                r.ux = r.uy = r.uz = 0u;
-                r.f = 0.0f;
             } else {
-                const double sx = hinv.a[0] * x + hinv.a[1] * y + hinv.a[2] * z;
-                const double sy = hinv.a[3] * x + hinv.a[4] * y + hinv.a[5] * z;
-                const double sz = hinv.a[6] * x + hinv.a[7] * y + hinv.a[8] * z;
+                double sx, sy, sz = 0.0;
+                if (opt.ortho) {
+                    sx = (double)x * hinv.a[0];
+                    sy = (double)y * hinv.a[4];
+                    if (opt.need_z) sz = (double)z * hinv.a[8];
+                } else {
+                    sx = hinv.a[0] * x + hinv.a[1] * y + hinv.a[2] * z;
+                    sy = hinv.a[3] * x + hinv.a[4] * y + hinv.a[5] * z;
+                    if (opt.need_z) sz = hinv.a[6] * x + hinv.a[7] * y + hinv.a[8] * z;
+                }
                 r.ux = turns_u32(sx);
                 r.uy = turns_u32(sy);
-                r.uz = turns_u32(sz);
+                if (opt.need_z) r.uz = turns_u32(sz);
                 r.f = fj;
             }
-        } else {
-            r.ux = r.uy = r.uz = 0u;
-            r.f = 0.0f;
         }
         rec[i] = r;
     }
@@ -88,11 +98,11 @@ direct_kernel(const AtomRec* __restrict__ rec, int64_t n_pad, int64_t n_frames, 
         const int64_t pc = pix[i] < P ? pix[i] : P - 1;
         pixel_miller(pc, g, nx[i], ny[i], nz[i]);
     }
-    float re[kDirectPX], im[kDirectPX];
+    float re[kDirectPX], im[kDirectPX], cre[kDirectPX], cim[kDirectPX];
     double dre[kDirectPX], dim[kDirectPX];
 #pragma unroll
     for (int i = 0; i < kDirectPX; ++i) {
-        re[i] = im[i] = 0.0f;
+        re[i] = im[i] = cre[i] = cim[i] = 0.0f;
         dre[i] = dim[i] = 0.0;
     }
     for (int64_t k0 = a0; k0 < a1; k0 += kAtomTile) {
@@ -108,15 +118,23 @@ direct_kernel(const AtomRec* __restrict__ rec, int64_t n_pad, int64_t n_frames, 
                 const uint32_t ph = nx[i] * a.x + ny[i] * a.y + nz[i] * a.z;
                 float c, s;
                 phase_to_cs(ph, c, s);
-                re[i] = fmaf(fj, c, re[i]);
-                im[i] = fmaf(fj, s, im[i]);
+                // Kahan: y = term - carried error; the rounding of re + y is
+                // recovered exactly as (t - re) - y
+                const float yr = fmaf(fj, c, -cre[i]);
+                const float tr = re[i] + yr;
+                cre[i] = (tr - re[i]) - yr;
+                re[i] = tr;
+                const float yi = fmaf(fj, s, -cim[i]);
+                const float ti = im[i] + yi;
+                cim[i] = (ti - im[i]) - yi;
+                im[i] = ti;
             }
         }
 #pragma unroll
         for (int i = 0; i < kDirectPX; ++i) {
-            dre[i] += (double)re[i];
-            dim[i] += (double)im[i];
-            re[i] = im[i] = 0.0f;
+            dre[i] += (double)re[i] - (double)cre[i];
+            dim[i] += (double)im[i] - (double)cim[i];
+            re[i] = im[i] = cre[i] = cim[i] = 0.0f;
         }
     }
 #pragma unroll
@@ -156,13 +174,14 @@ __global__ void reduce_kernel(const double2* __restrict__ partial, int splits, i
 }  // namespace
 
 cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int64_t n_frames,
-                         int64_t n_pad, const Mat3& hinv, AtomRec* rec, int* err,
+                         int64_t n_pad, const Mat3& hinv, const PhaseOpts& opt, AtomRec* rec, int* err,
                          cudaStream_t st) {
     const int64_t total = n_frames * n_pad;
     if (total == 0) return cudaSuccess;
     const int threads = 256;
     const int64_t blocks = min((total + threads - 1) / threads, (int64_t)65536);
-    phase_kernel<<<(unsigned)blocks, threads, 0, st>>>(pos, f, n_atoms, n_frames, n_pad, hinv, rec, err);
+    ++tl_kernel_launches;
+    phase_kernel<<<(unsigned)blocks, threads, 0, st>>>(pos, f, n_atoms, n_frames, n_pad, hinv, opt, rec, err);
     return cudaGetLastError();
 }
 
@@ -194,11 +213,13 @@ cudaError_t launch_direct(const AtomRec* rec, int64_t n_pad, int64_t n_frames, c
     if (n_frames > 65535 || pix_blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)pix_blocks, (unsigned)n_frames, (unsigned)plan.splits);
     double2* part = plan.splits > 1 ? static_cast<double2*>(partial) : nullptr;
+    ++tl_kernel_launches;
     direct_kernel<<<grid, kDirectThreads, 0, st>>>(rec, n_pad, n_frames, g, plan.atoms_per_split, part, I, amp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || plan.splits == 1) return e;
     const int64_t items = n_frames * P;
     const int64_t blocks = min((items + 255) / 256, (int64_t)65536);
+    ++tl_kernel_launches;
     reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(part, plan.splits, items, I, amp);
     return cudaGetLastError();
 }

@@ -14,6 +14,10 @@
 
 using namespace xs;
 
+namespace xs {
+thread_local int64_t tl_kernel_launches = 0;
+}
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -54,6 +58,28 @@ bool invert3(const double* h, double* out) {
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+int64_t gcd64(int64_t a, int64_t b) {
+    while (b) {
+        const int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// odd multiplier near 0.618 n coprime with n: k -> k*a mod n visits the atoms
+// far apart in input order (a bijection on [0, n))
+int64_t coprime_stride(int64_t n) {
+    if (n <= 2) return 1;
+    int64_t a = (int64_t)(0.6180339887498949 * (double)n) | 1;
+    while (gcd64(a, n) != 1) a += 2;
+    return a % n == 0 ? 1 : a;
+}
+
+bool is_ortho(const double* hinv) {
+    return hinv[1] == 0.0 && hinv[2] == 0.0 && hinv[3] == 0.0 && hinv[5] == 0.0 && hinv[6] == 0.0 && hinv[7] == 0.0;
+}
+
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -86,6 +112,27 @@ struct xs_context {
         size_t bytes = 0;
     };
     std::map<std::string, ConstSlot> consts;
+    // tracing
+    struct ProfRec {
+        std::string name;
+        cudaEvent_t a, b;
+        int64_t kernels;
+    };
+    bool prof_on = false;
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> event_pool;
+    int64_t launches = 0;
+
+    cudaEvent_t take_event() {
+        if (!event_pool.empty()) {
+            cudaEvent_t e = event_pool.back();
+            event_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
 
     void* raw_alloc(size_t bytes) {
         if (has_alloc) return alloc.alloc(bytes, alloc.ctx);
@@ -166,6 +213,31 @@ xs_status check_grid(const xs_qgrid* g) {
 
 GridDesc to_desc(const xs_qgrid* g) { return GridDesc{g->nx0, g->nx, g->ny0, g->ny, g->nz0, g->nz}; }
 
+// Runs one launch_* call: counts its kernels and, when tracing, brackets it
+// with events on the launching stream.
+template <class F>
+cudaError_t traced(xs_context* ctx, const char* name, cudaStream_t st, F&& launch) {
+    const int64_t before = tl_kernel_launches;
+    cudaEvent_t a = nullptr;
+    if (ctx->prof_on) {
+        a = ctx->take_event();
+        if (a) cudaEventRecord(a, st);
+    }
+    const cudaError_t e = launch();
+    const int64_t n = tl_kernel_launches - before;
+    ctx->launches += n;
+    if (ctx->prof_on && a) {
+        cudaEvent_t b = ctx->take_event();
+        if (b) {
+            cudaEventRecord(b, st);
+            ctx->prof.push_back({name, a, b, n});
+        } else {
+            ctx->event_pool.push_back(a);
+        }
+    }
+    return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -220,6 +292,11 @@ xs_status xs_context_destroy(xs_context* ctx) {
         if (ctx->ev_consumed[i]) cudaEventDestroy(ctx->ev_consumed[i]);
     }
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    for (auto& r : ctx->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     delete ctx;
     return XS_OK;
 }
@@ -227,6 +304,45 @@ xs_status xs_context_destroy(xs_context* ctx) {
 xs_status xs_set_wait_timeout_ns(xs_context* ctx, int64_t ns) {
     if (!ctx || ns <= 0) return fail(XS_ERR_INVALID_ARG, "bad context or timeout");
     ctx->timeout_ns = ns;
+    return XS_OK;
+}
+
+xs_status xs_profile_enable(xs_context* ctx, int32_t on) {
+    if (!ctx) return fail(XS_ERR_INVALID_ARG, "context is NULL");
+    ctx->prof_on = on != 0;
+    return XS_OK;
+}
+
+xs_status xs_profile_read(xs_context* ctx, const char* prefix, double* total_ms, int64_t* launches) {
+    if (!ctx || !total_ms || !launches) return fail(XS_ERR_INVALID_ARG, "missing argument");
+    const std::string pre = prefix ? prefix : "";
+    double ms = 0.0;
+    int64_t n = 0;
+    xs_status st = XS_OK;
+    std::vector<xs_context::ProfRec> keep;
+    for (auto& r : ctx->prof) {
+        if (r.name.compare(0, pre.size(), pre) != 0) {
+            keep.push_back(r);
+            continue;
+        }
+        float e = 0.0f;
+        cudaError_t err = cudaEventSynchronize(r.b);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&e, r.a, r.b);
+        if (err != cudaSuccess && st == XS_OK) st = fail(XS_ERR_CUDA, "profile event: %s", cudaGetErrorString(err));
+        ms += e;
+        n += r.kernels;
+        ctx->event_pool.push_back(r.a);
+        ctx->event_pool.push_back(r.b);
+    }
+    ctx->prof.swap(keep);
+    *total_ms = ms;
+    *launches = n;
+    return st;
+}
+
+xs_status xs_launch_count(xs_context* ctx, int64_t* count) {
+    if (!ctx || !count) return fail(XS_ERR_INVALID_ARG, "missing argument");
+    *count = ctx->launches;
     return XS_OK;
 }
 
@@ -276,6 +392,10 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
     for (int i = 0; i < 9; ++i) hm.a[i] = hinv[i];
     const int64_t N = traj->n_atoms;
     const int64_t n_pad = round_up(N > 0 ? N : 1, 64);
+    PhaseOpts popt;
+    popt.ortho = is_ortho(hinv);
+    popt.need_z = !(g.nz == 1 && g.nz0 == 0);
+    popt.perm_mul = use_tc ? coprime_stride(n_pad) : 1;
 
     // frames per chunk: records and (for host positions) staged positions
     const size_t rec_per_frame = (size_t)n_pad * sizeof(AtomRec);
@@ -287,12 +407,14 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
     if (fchunk > 65535) fchunk = 65535;
 
     DirectPlan dplan{};
-    int chunk_stages = 64;
+    TcPlan tplan0{};
+    int chunk_stages = 128;
     if (use_tc) {
         auto key = std::make_tuple(n_pad, g.nx, g.ny, g.nz, (int)prec);
         auto it = ctx->tuned_chunk.find(key);
         if (it != ctx->tuned_chunk.end()) chunk_stages = it->second;
         if (chunk_override > 0) chunk_stages = chunk_override;
+        tplan0 = plan_tc(n_pad, fchunk, g, ctx->num_sms, chunk_stages);
     } else {
         dplan = plan_direct(n_pad, fchunk, g, ctx->num_sms);
     }
@@ -305,7 +427,7 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
         return o;
     };
     const size_t o_rec = carve((size_t)fchunk * rec_per_frame);
-    const size_t o_part = carve(use_tc ? 0 : dplan.partial_bytes);
+    const size_t o_part = carve(use_tc ? tc_scratch_bytes(tplan0) : dplan.partial_bytes);
     const size_t o_pos0 = carve(pos_host ? (size_t)fchunk * pos_per_frame : 0);
     const size_t o_pos1 = carve(pos_host ? (size_t)fchunk * pos_per_frame : 0);
     const size_t o_f = carve(pos_host ? (size_t)N * sizeof(float) : 0);
@@ -361,16 +483,18 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
             } else {
                 pos_c = traj->pos + (size_t)t0 * N * 3;
             }
-            XS_CUDA(launch_phase(pos_c, f_dev, N, nf, n_pad, hm, rec, ctx->d_err, st));
+            XS_CUDA(traced(ctx, "phase", st, [&] { return launch_phase(pos_c, f_dev, N, nf, n_pad, hm, popt, rec, ctx->d_err, st); }));
             if (pos_host) XS_CUDA(cudaEventRecord(ctx->ev_consumed[c & 1], st));
             if (use_tc) {
                 TcPlan pc = plan_tc(n_pad, nf, g, ctx->num_sms, chunk_stages);
-                XS_CUDA(launch_tc(rec, n_pad, nf, g, pc, prec == XS_PREC_SPLIT_BF16, Ic, Ac, ctx->d_err,
-                                  ctx->timeout_ns, st));
+                XS_CUDA(traced(ctx, "tc", st, [&] {
+                    return launch_tc(rec, n_pad, nf, g, pc, prec == XS_PREC_SPLIT_BF16, Ic, Ac,
+                                     reinterpret_cast<double*>(ws + o_part), ctx->d_err, ctx->timeout_ns, st);
+                }));
             } else {
                 DirectPlan pc = plan_direct(n_pad, nf, g, ctx->num_sms);
                 if (pc.partial_bytes > dplan.partial_bytes) return fail(XS_ERR_CUDA, "internal: partial plan grew");
-                XS_CUDA(launch_direct(rec, n_pad, nf, g, pc, ws + o_part, Ic, Ac, st));
+                XS_CUDA(traced(ctx, "direct", st, [&] { return launch_direct(rec, n_pad, nf, g, pc, ws + o_part, Ic, Ac, st); }));
             }
         }
         if (!out_dev) {
@@ -421,8 +545,8 @@ xs_status xs_tune(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, xs
     cudaEvent_t e0, e1;
     XS_CUDA(cudaEventCreate(&e0));
     XS_CUDA(cudaEventCreate(&e1));
-    const int cands[] = {16, 32, 64, 128, 256};
-    int best = 64;
+    const int cands[] = {32, 64, 128, 256, 512};
+    int best = 128;
     float best_ms = 1e30f;
     for (int c : cands) {
         s = intensity_impl(ctx, &sub, grid, prec, out, nullptr, st, c);  // warm-up
@@ -467,7 +591,7 @@ xs_status xs_g2(xs_context* ctx, const float* I, int64_t T, int64_t P, const int
     xs_status s = upload_const(ctx, "g2", blob, st, &d);
     if (s != XS_OK) return s;
     const int32_t* d_taus = reinterpret_cast<const int32_t*>(static_cast<char*>(d) + o_tau);
-    XS_CUDA(launch_g2(I, T, P, d_taus, n_tau, g2_out, mean_out, st));
+    XS_CUDA(traced(ctx, "g2", st, [&] { return launch_g2(I, T, P, d_taus, n_tau, g2_out, mean_out, st); }));
     return XS_OK;
 }
 
@@ -592,11 +716,11 @@ xs_status xs_xsvs_contrast(xs_context* ctx, const float* I, int64_t T, const xs_
     s = ensure_ws(ctx, off + 256);
     if (s != XS_OK) return s;
     char* ws = static_cast<char*>(ctx->ws);
-    XS_CUDA(launch_xsvs(I, T, P, reinterpret_cast<const int32_t*>(dc + o_perm), reinterpret_cast<const int4*>(dc + o_chunks),
+    XS_CUDA(traced(ctx, "xsvs", st, [&] { return launch_xsvs(I, T, P, reinterpret_cast<const int32_t*>(dc + o_perm), reinterpret_cast<const int4*>(dc + o_chunks),
                         n_chunks, n_in, reinterpret_cast<const int32_t*>(dc + o_K), reinterpret_cast<const int64_t*>(dc + o_kw),
                         n_K, n_kw, reinterpret_cast<const int32_t*>(dc + o_first), reinterpret_cast<const int32_t*>(dc + o_count),
                         n_rings, reinterpret_cast<double*>(ws + o_prefix), reinterpret_cast<double2*>(ws + o_partial),
-                        beta_out, st));
+                        beta_out, st); }));
     return XS_OK;
 }
 
@@ -626,6 +750,9 @@ xs_status xs_intensity_backward(xs_context* ctx, const xs_traj* traj, const xs_q
     }
     Mat3 hm;
     for (int i = 0; i < 9; ++i) hm.a[i] = hinv[i];
+    PhaseOpts popt;
+    popt.ortho = is_ortho(hinv);
+    popt.need_z = !(g.nz == 1 && g.nz0 == 0);
     size_t off = 0;
     auto carve = [&](size_t bytes) {
         size_t o = round_up((int64_t)off, 256);
@@ -638,8 +765,8 @@ xs_status xs_intensity_backward(xs_context* ctx, const xs_traj* traj, const xs_q
     if (s != XS_OK) return s;
     char* ws = static_cast<char*>(ctx->ws);
     AtomRec* rec = reinterpret_cast<AtomRec*>(ws + o_rec);
-    XS_CUDA(launch_phase(traj->pos, traj->f, N, 1, n_pad, hm, rec, ctx->d_err, st));
-    XS_CUDA(launch_adjoint(rec, N, n_pad, g, hm, amp, dL_dI, ws + o_h, dL_dr_out, st));
+    XS_CUDA(traced(ctx, "phase", st, [&] { return launch_phase(traj->pos, traj->f, N, 1, n_pad, hm, popt, rec, ctx->d_err, st); }));
+    XS_CUDA(traced(ctx, "adjoint", st, [&] { return launch_adjoint(rec, N, n_pad, g, hm, amp, dL_dI, ws + o_h, dL_dr_out, st); }));
     return XS_OK;
 }
 

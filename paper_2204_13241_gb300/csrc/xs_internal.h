@@ -9,15 +9,27 @@
 
 namespace xs {
 
+// Kernels launched by the calling host thread (each launch_* adds its own);
+// the ABI layer turns the deltas into per-context counts.
+extern thread_local int64_t tl_kernel_launches;
+
 struct GridDesc {
     int nx0, nx, ny0, ny, nz0, nz;
     __host__ __device__ int64_t pixels() const { return (int64_t)nx * ny * nz; }
 };
 
 // ---- phase records (fractional coordinates as 32-bit turns) -------------
-// rec [n_frames][n_pad]; atoms >= n_atoms get f = 0 and U = 0.
+// rec [n_frames][n_pad]; slot k of a frame holds atom j = (k * perm_mul) mod
+// n_pad (perm_mul coprime with n_pad; 1 keeps the input order); atoms >=
+// n_atoms get f = 0 and U = 0.  `ortho`: h^-1 is diagonal; `need_z`: U_z is
+// used (otherwise it is left 0).
+struct PhaseOpts {
+    bool ortho = false;
+    bool need_z = true;
+    int64_t perm_mul = 1;
+};
 cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int64_t n_frames,
-                         int64_t n_pad, const Mat3& hinv, AtomRec* rec, int* err,
+                         int64_t n_pad, const Mat3& hinv, const PhaseOpts& opt, AtomRec* rec, int* err,
                          cudaStream_t st);
 
 // ---- plain FP32 direct sum ----------------------------------------------
@@ -38,9 +50,11 @@ struct TcPlan {
     int tiles_x, tiles_y;  // 128-pixel tiles per frame plane along x and y
 };
 bool tc_supported(const GridDesc& g);
+int64_t tc_atom_multiple();
 TcPlan plan_tc(int64_t n_pad, int64_t n_frames, const GridDesc& g, int num_sms, int chunk_stages);
+size_t tc_scratch_bytes(const TcPlan& plan);  // FP64 running totals, one block per CTA
 cudaError_t launch_tc(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g,
-                      const TcPlan& plan, bool bf16, float* I, float* amp, int* err,
+                      const TcPlan& plan, bool bf16, float* I, float* amp, double* scratch, int* err,
                       int64_t timeout_ns, cudaStream_t st);
 
 // ---- g2 -----------------------------------------------------------------
