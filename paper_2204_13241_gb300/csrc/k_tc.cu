@@ -10,22 +10,27 @@
 // The real product D = A B^T holds the four real partial sums:
 //   Re S = D[Re x][Re y] - D[Im x][Im y],  Im S = D[Re x][Im y] + D[Im x][Re y].
 //
-// One CTA owns a tile of 64 n_x by 128 n_y of one frame and plane
-// (MMA M = 128, N = 256) and loops over all atoms 32 at a time (a stage):
-//   * 6 producer warps write the factor tables straight into shared memory in
+// A pair of CTAs (a cluster of two on neighbouring SMs) owns a tile of
+// 128 n_x by 128 n_y of one frame and plane and runs one M = 256, N = 256
+// tcgen05 contraction (cta_group::2) over all atoms, 64 atoms per stage.
+// CTA r holds the A rows of n_x [64r, 64r+64) and the B rows of n_y
+// [64r, 64r+64) of the tile, so each CTA builds only a quarter of the pair's
+// factor tables; the accumulator rows of CTA r (in its own tensor memory) are
+// its A rows against all 256 B columns.
+//   * 8 producer warps per CTA write the tables straight into shared memory in
 //     the MN-major, 128-byte-swizzled layout the tensor core reads.  Each
 //     thread owns one atom and a run of 32 consecutive n, held as pairs
-//     (n, n+1) in packed FP32x2 registers (real parts together, imaginary
-//     parts together): the run starts from exact seeds exp(i 2 pi n0 U) and
-//     exp(i 2 pi (n0+1) U) (U = 32-bit turn count, n U mod 2^32 is exact) and
-//     advances by the exact step exp(i 2 pi 2U).  Each value c is split into
-//     hi = RN(c) and lo = RN(c - hi) (FP16 or BF16).
-//   * 1 thread issues tcgen05.mma (hi*hi + hi*lo + lo*hi, FP32 accumulate)
-//     into one of two TMEM accumulators; after `chunk_stages` stages it hands
-//     the accumulator to the epilogue and continues in the other one.
-//   * 4 epilogue warps add each chunk's FP32 sums into FP64 running totals in
-//     an L2-resident scratch buffer (one per CTA) and, after the last chunk of
-//     a tile, recombine the quadrants in FP64 into S and I = |S|^2.
+//     (n, n+1) in packed FP32x2 registers: the run starts from exact seeds
+//     exp(i 2 pi n0 U) and exp(i 2 pi (n0+1) U) (U = 32-bit turn count, n U mod
+//     2^32 is exact) and advances by the exact step exp(i 2 pi 2U).  Each value
+//     c is split into hi = RN(c) and lo = RN(c - hi) (FP16 or BF16).
+//   * 1 thread of CTA 0 issues tcgen05.mma (hi*hi + hi*lo + lo*hi, FP32
+//     accumulate) into one of two TMEM accumulators; after `chunk_stages`
+//     stages it hands the accumulator to the epilogues and continues in the
+//     other one.
+//   * 4 epilogue warps per CTA add each chunk's FP32 sums into FP64 running
+//     totals in an L2-resident scratch block (one per CTA) and, after the last
+//     chunk of a tile, recombine the quadrants in FP64 into S and I = |S|^2.
 // The atoms arrive in a coprime-stride permuted order (see the phase kernel),
 // so the partial sums over a chunk behave like random walks even for ordered
 // crystals and the FP32 accumulator never sums a coherent run of terms.
@@ -40,35 +45,33 @@ namespace xs {
 
 namespace {
 
-constexpr int kBM = 128;   // MMA M: 64 complex n_x as interleaved Re/Im rows
-constexpr int kBN = 256;   // MMA N: 128 complex n_y as interleaved Re/Im columns
-constexpr int kBK = 32;    // atoms per stage
-constexpr int kStages = 4;
-constexpr int kTileX = 64;
-constexpr int kTileY = 128;
-constexpr int kRun = 32;   // consecutive n per producer thread and stage
+constexpr int kBN = 256;   // MMA N (and M of the pair): 128 complex n as Re/Im rows
+constexpr int kBK = 64;    // atoms per stage
+constexpr int kStages = 3;
+constexpr int kTile = 128;  // n_x and n_y per pair tile
+constexpr int kHalf = 64;   // n per CTA and axis
+constexpr int kRun = 32;    // consecutive n per producer thread and stage
 constexpr int kEpiWarps = 4;
 constexpr int kMmaWarp = 4;
-constexpr int kProdWarps = 6;
-constexpr int kProdThreads = kProdWarps * 32;
+constexpr int kProdWarps = 8;
 constexpr int kThreads = (kEpiWarps + 1 + kProdWarps) * 32;
 // MN-major SW128 tiles: blocks of 64 MN elements (128-byte rows), 8 K rows per
-// 1024-byte swizzle atom; a stage holds kBK / 8 = 4 K atoms per MN block.
-constexpr uint32_t kKAtoms = kBK / 8;
-constexpr uint32_t kMNBlockBytes = kKAtoms * 1024;                // 4 KB: LBO
-constexpr uint32_t kABytes = (kBM / 64) * kMNBlockBytes;          // 8 KB
-constexpr uint32_t kBBytes = (kBN / 64) * kMNBlockBytes;          // 16 KB
-constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;       // 48 KB
-constexpr uint32_t kTmemCols = 512;  // two 256-column FP32 accumulators
+// 1024-byte swizzle atom; a stage holds kBK / 8 = 8 K atoms per MN block.
+constexpr uint32_t kMNBlockBytes = (kBK / 8) * 1024;  // 8 KB: leading byte offset
+constexpr uint32_t kHalfBytes = 2 * kMNBlockBytes;     // 128 rows of one operand half
+constexpr uint32_t kStageBytes = 4 * kHalfBytes;       // A hi, A lo, B hi, B lo: 64 KB
+constexpr uint32_t kTmemCols = 512;                    // two 256-column FP32 accumulators
+constexpr int kTabSize = 256;
 
 struct SmemCtl {
-    uint64_t full[kStages];
-    uint64_t empty[kStages];
-    uint64_t acc_full[2];
-    uint64_t acc_empty[2];
+    uint64_t full[kStages];   // CTA 0: producer warps of both CTAs
+    uint64_t empty[kStages];  // each CTA: MMA commits
+    uint64_t acc_full[2];     // each CTA: MMA commits
+    uint64_t acc_empty[2];    // CTA 0: epilogue warps of both CTAs
     uint64_t drain;
     uint32_t tmem_base;
     int abort;
+    float2 tab[kTabSize];     // exp(i 2 pi k / 256)
 };
 
 constexpr size_t kSmemBytes = 1024 + kStages * kStageBytes + sizeof(SmemCtl);
@@ -95,15 +98,35 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// address of the same shared-memory object in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile(
-        "{\n\t.reg .b64 st;\n\t"
-        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
-        : "memory");
+// arrive (release at cluster scope) on a barrier given by its cluster address
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+
+// arrive (release at CTA scope) on a barrier of this CTA
+__device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // Test of the phase with parity `parity`; the thread may sleep in the barrier
@@ -112,7 +135,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity, ui
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
@@ -136,33 +159,38 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+// one warp of each CTA of the pair allocates the same columns in both
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
                  "r"(ncols)
                  : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_dealloc(uint32_t base, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols) : "memory");
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t base, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols) : "memory");
 }
 
-// D[tmem] (+)= A[smem] * B[smem]^T; accumulate unless acc == 0
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                     uint32_t acc) {
+// D[tmem of both CTAs] (+)= A[smem of both] * B[smem of both]^T (M = 256);
+// accumulate unless acc == 0.  Issued by one thread of CTA 0.
+__device__ __forceinline__ void umma_pair(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(acc)
         : "memory");
 }
 
-// arrive on `bar` once every tcgen05 operation issued so far by this thread completes
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
+// arrive on `bar` in the CTAs of `mask` once every tcgen05 operation issued so
+// far by this thread completes
+__device__ __forceinline__ void umma_commit_pair(uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
 }
 
 // 16 columns of this warp's 32 TMEM lanes; the registers are valid only after
@@ -226,6 +254,19 @@ __device__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_fla
 
 // ---- table construction ------------------------------------------------------
 
+// exp(i 2 pi P / 2^32) for a 32-bit turn count: the top 8 bits pick
+// exp(i 2 pi k / 256) from a table, the remaining angle t < 2 pi / 256 uses the
+// Taylor polynomials cos t = 1 - t^2/2 + t^4/24 and sin t = t - t^3/6 + t^5/120
+// (truncation below 3e-13), and the two factors are multiplied.
+__device__ __forceinline__ float2 cis_turns(uint32_t P, const float2* tab) {
+    const float2 a = tab[P >> 24];
+    const float t = (float)(P & 0xFFFFFFu) * 1.4629180792671596e-9f;  // 2 pi / 2^32
+    const float t2 = t * t;
+    const float c = fmaf(t2, fmaf(t2, 1.0f / 24.0f, -0.5f), 1.0f);
+    const float s = t * fmaf(t2, fmaf(t2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
+    return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+}
+
 // v = (v0, v1) -> packed hi = (RN(v0), RN(v1)) and lo = (RN(v0 - hi0), RN(v1 - hi1));
 // v - hi is exact in FP32, so hi + lo carries about twice the format's bits
 template <bool BF16>
@@ -271,7 +312,7 @@ __device__ __forceinline__ UnitPos decode_unit(int64_t u, const TcArgs& a) {
 }
 
 template <bool BF16>
-__global__ void __launch_bounds__(kThreads, 1) tc_kernel(TcArgs args) {
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kernel(TcArgs args) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
@@ -282,47 +323,53 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(TcArgs args) {
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();  // 0: issues the MMAs of the pair
+    const int64_t pair = blockIdx.x >> 1, n_pairs = gridDim.x >> 1;
 
+    for (int i = threadIdx.x; i < kTabSize; i += kThreads) {
+        double s, c;
+        sincospi((double)i / (kTabSize / 2), &s, &c);
+        ctl->tab[i] = make_float2((float)c, (float)s);
+    }
     if (threadIdx.x == kMmaWarp * 32) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&ctl->full[s], kProdThreads);
+            mbar_init(&ctl->full[s], 2 * kProdWarps);
             mbar_init(&ctl->empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&ctl->acc_full[b], 1);
-            mbar_init(&ctl->acc_empty[b], kEpiWarps * 32);
+            mbar_init(&ctl->acc_empty[b], 2 * kEpiWarps);
         }
         mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
         fence_barrier_init();
     }
-    if (warp == 0) tmem_alloc(&ctl->tmem_base, kTmemCols);
+    if (warp == 0) tmem_alloc_pair(&ctl->tmem_base, kTmemCols);
     tc_fence_before();
-    __syncthreads();
+    cluster_sync();  // barriers of both CTAs initialised, tensor memory allocated
     tc_fence_after();
     const uint32_t tmem = ctl->tmem_base;
 
-    const int64_t my_units =
-        args.n_units > blockIdx.x ? (args.n_units - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t my_units = args.n_units > pair ? (args.n_units - 1 - pair) / n_pairs + 1 : 0;
     const int n_chunks = (args.n_stages + args.chunk_stages - 1) / args.chunk_stages;
 
     if (warp >= kMmaWarp + 1) {
         // ------------------------------------------------------------ producers
-        // warp seg 0,1: A rows for n_x run [32 seg, +32); seg 2..5: B rows for
-        // n_y run [32 (seg-2), +32); lane = atom of the stage
-        const int seg = warp - (kMmaWarp + 1);
-        const bool is_a = seg < 2;
-        const int run0 = (is_a ? seg : seg - 2) * kRun;
-        const int k = lane;
+        // warp w: atoms [32 (w & 1), +32) of the stage; w >> 1 = 0, 1: A rows for
+        // n_x run [32 (w>>1), +32) of this CTA's half, 2, 3: B rows for n_y
+        const int w = warp - (kMmaWarp + 1);
+        const int ri = w >> 1;
+        const bool is_a = ri < 2;
+        const int run0 = kRun * (ri & 1);
+        const int k = 32 * (w & 1) + lane;
         const int n_st = args.n_stages;
+        const uint32_t full_c0 = map_to_rank(smem_u32(&ctl->full[0]), 0);
         int slot = 0;
         uint32_t phase = 0;  // parity of the current pass over the ring of stages
-        // records are prefetched one stage ahead; positions of the next tile
-        // are decoded once per tile (no integer division inside the stage loop)
         const uint4* rec_cur = nullptr;
         UnitPos up{};
         if (my_units > 0) {
-            up = decode_unit(blockIdx.x, args);
+            up = decode_unit(pair, args);
             rec_cur = args.rec + (int64_t)up.t * args.n_pad + k;
         }
         uint4 r_next = make_uint4(0, 0, 0, 0);
@@ -332,11 +379,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(TcArgs args) {
             UnitPos up_next{};
             const uint4* rec_next_unit = nullptr;
             if (ku + 1 < my_units) {
-                up_next = decode_unit(blockIdx.x + (ku + 1) * gridDim.x, args);
+                up_next = decode_unit(pair + (ku + 1) * n_pairs, args);
                 rec_next_unit = args.rec + (int64_t)up_next.t * args.n_pad + k;
             }
-            const uint32_t n0 = is_a ? (uint32_t)(args.g.nx0 + up.tx * kTileX + run0)
-                                     : (uint32_t)(args.g.ny0 + up.ty * kTileY + run0);
+            const uint32_t n0 = is_a ? (uint32_t)(args.g.nx0 + up.tx * kTile + kHalf * (int)rank + run0)
+                                     : (uint32_t)(args.g.ny0 + up.ty * kTile + kHalf * (int)rank + run0);
             const uint32_t nz = (uint32_t)(args.g.nz0 + up.iz);
             for (int s = 0; s < n_st; ++s) {
                 const uint4 r = r_next;
@@ -346,22 +393,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(TcArgs args) {
                     r_next = __ldg(rec_next_unit);
                 // exact step z^2 and seeds E(n0), E(n0 + 1) of this thread's run
                 const uint32_t U = is_a ? r.x : r.y;
-                float c, sn;
-                phase_to_cs(2u * U, c, sn);
-                const float2 ZR = make_float2(c, c), ZI = make_float2(sn, sn), NZI = make_float2(-sn, -sn);
-                phase_to_cs(n0 * U, c, sn);
-                float2 E0 = make_float2(c, sn);
-                phase_to_cs((n0 + 1u) * U, c, sn);
-                float2 E1 = make_float2(c, sn);
+                const float2 z2 = cis_turns(2u * U, ctl->tab);
+                const float2 ZR = make_float2(z2.x, z2.x), ZI = make_float2(z2.y, z2.y);
+                const float2 NZI = make_float2(-z2.y, -z2.y);
+                float2 E0 = cis_turns(n0 * U, ctl->tab);
+                float2 E1 = cis_turns((n0 + 1u) * U, ctl->tab);
                 if (!is_a) {
                     const float f = __uint_as_float(r.w);
-                    float2 w = make_float2(f, 0.0f);
+                    float2 wv = make_float2(f, 0.0f);
                     if (nz != 0u) {
-                        phase_to_cs(nz * r.z, c, sn);
-                        w = make_float2(f * c, f * sn);
+                        const float2 ez = cis_turns(nz * r.z, ctl->tab);
+                        wv = make_float2(f * ez.x, f * ez.y);
                     }
-                    E0 = cmul(E0, w);
-                    E1 = cmul(E1, w);
+                    E0 = cmul(E0, wv);
+                    E1 = cmul(E1, wv);
                 }
                 float2 R = make_float2(E0.x, E1.x);   // Re of (n, n+1)
                 float2 Im = make_float2(E0.y, E1.y);  // Im of (n, n+1)
@@ -370,8 +415,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(TcArgs args) {
                     break;
                 }
                 const uint32_t sb = stage_base + (uint32_t)slot * kStageBytes;
-                const uint32_t hi_base = is_a ? sb : sb + 2 * kABytes;
-                const uint32_t lo_base = hi_base + (is_a ? kABytes : kBBytes);
+                const uint32_t hi_base = is_a ? sb : sb + 2 * kHalfBytes;
+                const uint32_t lo_base = hi_base + kHalfBytes;
 #pragma unroll
                 for (int g = 0; g < kRun / 4; ++g) {
                     // one 16-byte chunk = rows (Re n, Re n+1, Im n, Im n+1, Re n+2, Re n+3, Im n+2, Im n+3)
@@ -389,7 +434,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(TcArgs args) {
                     st_shared_v4(lo_base + off, l[0], l[1], l[2], l[3]);
                 }
                 fence_async_shared();
-                mbar_arrive(&ctl->full[slot]);
+                __syncwarp();
+                if (lane == 0) {
+                    // CTA 0's tables are read by its own MMAs: CTA-scope release is
+                    // enough; the peer's tables cross the pair and need cluster scope
+                    if (rank == 0)
+                        mbar_arrive_local(&ctl->full[slot]);
+                    else
+                        mbar_arrive_cluster(full_c0 + (uint32_t)slot * 8u);
+                }
                 if (++slot == kStages) {
                     slot = 0;
                     phase ^= 1u;
@@ -400,8 +453,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(TcArgs args) {
         }
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issue
-        if (lane == 0) {
-            constexpr uint32_t idesc = make_idesc(BF16, kBM, kBN);
+        if (rank == 0 && lane == 0) {
+            constexpr uint32_t idesc = make_idesc(BF16, 2 * 128, kBN);
             int64_t a_cnt = 0;
             int slot = 0;
             uint32_t phase = 0;
@@ -426,43 +479,45 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(TcArgs args) {
                         }
                         tc_fence_after();
                         const uint32_t a_hi = stage_base + (uint32_t)slot * kStageBytes;
-                        const uint32_t a_lo = a_hi + kABytes;
-                        const uint32_t b_hi = a_hi + 2 * kABytes;
-                        const uint32_t b_lo = b_hi + kBBytes;
+                        const uint32_t a_lo = a_hi + kHalfBytes;
+                        const uint32_t b_hi = a_hi + 2 * kHalfBytes;
+                        const uint32_t b_lo = b_hi + kHalfBytes;
 #pragma unroll
                         for (int kk = 0; kk < kBK / 16; ++kk) {
                             const uint32_t ko = (uint32_t)kk * 2048u;  // two 8-row K atoms per K = 16
-                            umma(d_tmem, mn_desc(a_hi + ko), mn_desc(b_hi + ko), idesc, (s > s0 || kk > 0) ? 1u : 0u);
-                            umma(d_tmem, mn_desc(a_hi + ko), mn_desc(b_lo + ko), idesc, 1u);
-                            umma(d_tmem, mn_desc(a_lo + ko), mn_desc(b_hi + ko), idesc, 1u);
+                            umma_pair(d_tmem, mn_desc(a_hi + ko), mn_desc(b_hi + ko), idesc,
+                                      (s > s0 || kk > 0) ? 1u : 0u);
+                            umma_pair(d_tmem, mn_desc(a_hi + ko), mn_desc(b_lo + ko), idesc, 1u);
+                            umma_pair(d_tmem, mn_desc(a_lo + ko), mn_desc(b_hi + ko), idesc, 1u);
                         }
-                        umma_commit(&ctl->empty[slot]);
+                        umma_commit_pair(&ctl->empty[slot], 0x3);
                         if (++slot == kStages) {
                             slot = 0;
                             phase ^= 1u;
                         }
                     }
-                    if (ok) umma_commit(&ctl->acc_full[b]);
+                    if (ok) umma_commit_pair(&ctl->acc_full[b], 0x3);
                 }
             }
             // every issued MMA must finish before tensor memory is released
-            umma_commit(&ctl->drain);
+            umma_commit_pair(&ctl->drain, 0x1);
             int no_abort = 0;
             wait_bar(&ctl->drain, 0u, &no_abort, args.err, 2000000000LL, 20000u);
         }
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
-        // TMEM lane = A row; rows 4g..4g+3 are (Re x, Re x+1, Im x, Im x+1), x = 2g
+        // TMEM lane = A row of this CTA; rows 4g..4g+3 are (Re x, Re x+1, Im x, Im x+1)
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
         const int row = warp * 32 + lane;
         const bool re_row = (lane & 2) == 0;
-        const int xi = 2 * (row >> 2) + (row & 1);
+        const int xi = kHalf * (int)rank + 2 * (row >> 2) + (row & 1);
         double* scr = args.scratch + (size_t)blockIdx.x * 256 * 128 + row;
+        const uint32_t acc_empty_c0 = map_to_rank(smem_u32(&ctl->acc_empty[0]), 0);
         int64_t a_cnt = 0;
         bool ok = true;
         for (int64_t ku = 0; ku < my_units && ok; ++ku) {
-            const UnitPos up = decode_unit(blockIdx.x + ku * gridDim.x, args);
+            const UnitPos up = decode_unit(pair + ku * n_pairs, args);
             for (int c = 0; c < n_chunks; ++c, ++a_cnt) {
                 const int b = (int)(a_cnt & 1);
                 const uint32_t use = (uint32_t)(a_cnt >> 1);
@@ -503,7 +558,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(TcArgs args) {
                         const double snd = re_row ? v[8 + i] : v[i];
                         rcv[i] = __shfl_xor_sync(0xffffffffu, snd, 2);
                     }
-                    const int ix = up.tx * kTileX + xi;
+                    const int ix = up.tx * kTile + xi;
                     if (ix < args.g.nx) {
 #pragma unroll
                         for (int hh = 0; hh < 2; ++hh) {
@@ -516,7 +571,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(TcArgs args) {
                                 const double sre = p_rr - p_ii;
                                 const double sim = p_ri + p_ir;
                                 const int m = 8 * j + (re_row ? 0 : 4) + 2 * hh + t;
-                                const int iy = up.ty * kTileY + m;
+                                const int iy = up.ty * kTile + m;
                                 if (iy < args.g.ny) {
                                     const int64_t o =
                                         (((int64_t)up.t * args.g.nz + up.iz) * args.g.ny + iy) * args.g.nx + ix;
@@ -531,15 +586,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(TcArgs args) {
                     }
                 }
                 tc_fence_before();
-                mbar_arrive(&ctl->acc_empty[b]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(acc_empty_c0 + (uint32_t)b * 8u);
             }
         }
     }
 
+    __syncwarp();
     tc_fence_before();
-    __syncthreads();
+    cluster_sync();  // no CTA leaves while the pair's MMAs or its peer may still touch it
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+    if (warp == 0) tmem_dealloc_pair(tmem, kTmemCols);
 }
 
 }  // namespace
@@ -550,11 +607,36 @@ int64_t tc_atom_multiple() { return kBK; }
 
 TcPlan plan_tc(int64_t n_pad, int64_t n_frames, const GridDesc& g, int num_sms, int chunk_stages) {
     TcPlan p;
-    p.tiles_x = (g.nx + kTileX - 1) / kTileX;
-    p.tiles_y = (g.ny + kTileY - 1) / kTileY;
+    p.tiles_x = (g.nx + kTile - 1) / kTile;
+    p.tiles_y = (g.ny + kTile - 1) / kTile;
     const int64_t units = n_frames * g.nz * p.tiles_x * p.tiles_y;
-    p.grid = (int)std::min<int64_t>(units, num_sms);
-    p.chunk_stages = chunk_stages > 0 ? chunk_stages : 128;
+    // pairs that can be resident at once (a cluster needs two SMs of one GPC)
+    static int max_pairs = -1;
+    if (max_pairs < 0) {
+        cudaFuncSetAttribute((const void*)tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBytes);
+        cudaFuncSetAttribute((const void*)tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBytes);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * (unsigned)std::max(1, num_sms / 2), 1, 1);
+        cfg.blockDim = dim3(kThreads, 1, 1);
+        cfg.dynamicSmemBytes = kSmemBytes;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = 2;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, (const void*)tc_kernel<false>, &cfg) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            n = std::max(1, num_sms / 2);
+        }
+        max_pairs = n;
+    }
+    p.grid = 2 * (int)std::min<int64_t>(units, max_pairs);
+    p.chunk_stages = chunk_stages > 0 ? chunk_stages : 32;
     (void)n_pad;
     return p;
 }
