@@ -211,6 +211,32 @@ XS_API xs_status xs_profile_enable(xs_context* ctx, int32_t on);
 XS_API xs_status xs_profile_read(xs_context* ctx, const char* prefix, double* total_ms, int64_t* launches);
 XS_API xs_status xs_launch_count(xs_context* ctx, int64_t* count);
 
+/*
+ * The FP32 direct-sum intensity of xs_intensity(..., XS_PREC_FP32_DIRECT, ...)
+ * (the same kernels and the same result) for callers that cannot allocate
+ * device memory when they need it: code that runs while a CUDA stream is being
+ * captured into a graph (cudaMalloc is not allowed there), hosts that fix their
+ * device memory budget at start-up, and processes whose framework allocator
+ * already holds the whole device.  The paper has no counterpart: this is a
+ * service of the library, not a step of the method.
+ *   - No context and no allocation: the scratch (phase records, T * ceil64(N)
+ *     * 16 bytes, plus the partial amplitudes of the atom splits) lives in one
+ *     static device array of 16 MiB that every GPU loading the library keeps
+ *     until the process exits.  Requests needing more are rejected with
+ *     XS_ERR_INVALID_ARG and a message giving the bytes needed and available.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents (each
+ *     call writes every byte it reads).  Calls whose kernels overlap on the
+ *     GPU (unordered streams) race on it.
+ *   - traj->pos, traj->f, I_out and amp_out (nullable) are device memory laid
+ *     out as for xs_intensity; dev_err is an optional caller-owned device int
+ *     that the kernels OR with 2 when a position or form factor is not finite.
+ */
+XS_API xs_status xs_intensity_fp32_static(const xs_traj* traj, const xs_qgrid* grid, float* I_out,
+                                          float* amp_out, int* dev_err, void* cuda_stream);
+
 /* Library version string. */
 XS_API const char* xs_version(void);
 

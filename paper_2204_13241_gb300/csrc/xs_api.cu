@@ -19,8 +19,12 @@ thread_local int64_t tl_kernel_launches = 0;
 }
 
 namespace {
-
 thread_local std::string g_last_error;
+}
+
+void xs::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+namespace {
 
 xs_status fail(xs_status s, const char* fmt, ...) {
     char buf[512];

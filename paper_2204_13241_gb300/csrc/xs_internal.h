@@ -9,6 +9,9 @@
 
 namespace xs {
 
+// Sets the message xs_last_error() returns on the calling thread.
+void set_last_error(const char* msg);
+
 // Kernels launched by the calling host thread (each launch_* adds its own);
 // the ABI layer turns the deltas into per-context counts.
 extern thread_local int64_t tl_kernel_launches;
