@@ -118,24 +118,27 @@ __global__ void window_kernel(const double* __restrict__ C, int64_t n_in, const 
     }
 }
 
+// one warp per (K, ring): lanes take windows w = lane, lane + 32, ...; the
+// per-lane sums of beta_w are reduced by a fixed shuffle tree (deterministic)
 __global__ void finalize_kernel(const double2* __restrict__ partial, int n_chunks,
                                 const int32_t* __restrict__ Ks, const int64_t* __restrict__ kw_off, int n_K,
                                 int64_t T, const int32_t* __restrict__ ring_first_chunk,
                                 const int32_t* __restrict__ ring_count, int n_rings, double* __restrict__ beta) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= (int64_t)n_K * n_rings) return;
     const int ik = (int)(i / n_rings);
     const int r = (int)(i - (int64_t)ik * n_rings);
     const int n = ring_count[r];
     if (n == 0) {
-        beta[i] = __longlong_as_double(0x7ff8000000000000ll);  // NaN
+        if (lane == 0) beta[i] = __longlong_as_double(0x7ff8000000000000ll);  // NaN
         return;
     }
     const int c0 = ring_first_chunk[r], c1 = ring_first_chunk[r + 1];
     const int64_t K = Ks[ik];
     const int64_t W = T / K;
     double acc = 0.0;
-    for (int64_t w = 0; w < W; ++w) {
+    for (int64_t w = lane; w < W; w += 32) {
         const double2* row = partial + (kw_off[ik] + w) * n_chunks;
         double s1 = 0.0, s2 = 0.0;
         for (int c = c0; c < c1; ++c) {
@@ -145,7 +148,9 @@ __global__ void finalize_kernel(const double2* __restrict__ partial, int n_chunk
         const double m1 = s1 / n, m2 = s2 / n;
         acc += (m2 - m1 * m1) / (m1 * m1);
     }
-    beta[i] = acc / (double)W;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) beta[i] = acc / (double)W;
 }
 
 }  // namespace
@@ -176,9 +181,9 @@ cudaError_t launch_xsvs(const float* I, int64_t T, int64_t P, const int32_t* d_p
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    const int64_t items = (int64_t)n_K * n_rings;
+    const int64_t items = (int64_t)n_K * n_rings;  // one warp each
     ++tl_kernel_launches;
-    finalize_kernel<<<(unsigned)((items + 127) / 128), 128, 0, st>>>(partial, n_chunks, d_K, d_kw_off, n_K, T,
+    finalize_kernel<<<(unsigned)((items * 32 + 127) / 128), 128, 0, st>>>(partial, n_chunks, d_K, d_kw_off, n_K, T,
                                                                      d_ring_first_chunk, d_ring_count, n_rings, beta);
     return cudaGetLastError();
 }

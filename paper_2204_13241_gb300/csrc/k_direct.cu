@@ -27,41 +27,48 @@ constexpr int kDirectThreads = 256;
 constexpr int kDirectPX = 4;     // pixels per thread
 constexpr int kAtomTile = 256;   // atom records staged per shared-memory tile
 
-__global__ void phase_kernel(const float* __restrict__ pos, const float* __restrict__ f,
-                             int64_t n_atoms, int64_t n_frames, int64_t n_pad, Mat3 hinv, PhaseOpts opt,
-                             AtomRec* __restrict__ rec, int* err) {
-    const int64_t total = n_frames * n_pad;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = i / n_pad, k = i - t * n_pad;
-        const int64_t j = opt.perm_mul == 1 ? k : (int64_t)(((uint64_t)k * (uint64_t)opt.perm_mul) % (uint64_t)n_pad);
+// hs = 2^32 h^-1 (a power-of-two scaling, exact): rint(hs r) mod 2^32 equals
+// rint(frac(h^-1 r) 2^32) mod 2^32, one FP64 multiply-add chain per axis and
+// one conversion instead of floor, subtract, scale and convert
+__device__ __forceinline__ uint32_t turns_scaled(double v) { return (uint32_t)(unsigned long long)__double2ll_rn(v); }
+
+constexpr int kPhaseFrames = 8;  // frames per block of the phase kernel
+
+// grid: x = blocks of 256 slots, y = groups of kPhaseFrames frames; the atom of
+// a slot (one 64-bit modulo) is computed once and reused for every frame
+__global__ void __launch_bounds__(256)
+phase_kernel(const float* __restrict__ pos, const float* __restrict__ f, int64_t n_atoms, int64_t n_frames,
+             int64_t n_pad, Mat3 hs, PhaseOpts opt, AtomRec* __restrict__ rec, int* err) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n_pad) return;
+    const int64_t j = opt.perm_mul == 1 ? k : (int64_t)(((uint64_t)k * (uint64_t)opt.perm_mul) % (uint64_t)n_pad);
+    const bool real = j < n_atoms;
+    const float fj = real ? f[j] : 0.0f;
+    const int64_t t0 = (int64_t)blockIdx.y * kPhaseFrames;
+    const int64_t t1 = min(n_frames, t0 + kPhaseFrames);
+    for (int64_t t = t0; t < t1; ++t) {
         AtomRec r;
         r.ux = r.uy = r.uz = 0u;
         r.f = 0.0f;
-        if (j < n_atoms) {
+        if (real) {
             const float* p = pos + (t * n_atoms + j) * 3;
             const float x = p[0], y = p[1], z = p[2];
-            const float fj = f[j];
             if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(fj)) {
                 set_dev_error(err, kDevErrNonFinite);
             } else {
-                double sx, sy, sz = 0.0;
                 if (opt.ortho) {
-                    sx = (double)x * hinv.a[0];
-                    sy = (double)y * hinv.a[4];
-                    if (opt.need_z) sz = (double)z * hinv.a[8];
+                    r.ux = turns_scaled((double)x * hs.a[0]);
+                    r.uy = turns_scaled((double)y * hs.a[4]);
+                    if (opt.need_z) r.uz = turns_scaled((double)z * hs.a[8]);
                 } else {
-                    sx = hinv.a[0] * x + hinv.a[1] * y + hinv.a[2] * z;
-                    sy = hinv.a[3] * x + hinv.a[4] * y + hinv.a[5] * z;
-                    if (opt.need_z) sz = hinv.a[6] * x + hinv.a[7] * y + hinv.a[8] * z;
+                    r.ux = turns_scaled(hs.a[0] * x + hs.a[1] * y + hs.a[2] * z);
+                    r.uy = turns_scaled(hs.a[3] * x + hs.a[4] * y + hs.a[5] * z);
+                    if (opt.need_z) r.uz = turns_scaled(hs.a[6] * x + hs.a[7] * y + hs.a[8] * z);
                 }
-                r.ux = turns_u32(sx);
-                r.uy = turns_u32(sy);
-                if (opt.need_z) r.uz = turns_u32(sz);
                 r.f = fj;
             }
         }
-        rec[i] = r;
+        rec[t * n_pad + k] = r;
     }
 }
 
@@ -176,12 +183,14 @@ __global__ void reduce_kernel(const double2* __restrict__ partial, int splits, i
 cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int64_t n_frames,
                          int64_t n_pad, const Mat3& hinv, const PhaseOpts& opt, AtomRec* rec, int* err,
                          cudaStream_t st) {
-    const int64_t total = n_frames * n_pad;
-    if (total == 0) return cudaSuccess;
-    const int threads = 256;
-    const int64_t blocks = min((total + threads - 1) / threads, (int64_t)65536);
+    if (n_frames * n_pad == 0) return cudaSuccess;
+    const int64_t gy = (n_frames + kPhaseFrames - 1) / kPhaseFrames;
+    if (gy > 65535) return cudaErrorInvalidConfiguration;
+    Mat3 hs;
+    for (int i = 0; i < 9; ++i) hs.a[i] = hinv.a[i] * 4294967296.0;
+    dim3 grid((unsigned)((n_pad + 255) / 256), (unsigned)gy);
     ++tl_kernel_launches;
-    phase_kernel<<<(unsigned)blocks, threads, 0, st>>>(pos, f, n_atoms, n_frames, n_pad, hinv, opt, rec, err);
+    phase_kernel<<<grid, 256, 0, st>>>(pos, f, n_atoms, n_frames, n_pad, hs, opt, rec, err);
     return cudaGetLastError();
 }
 

@@ -31,14 +31,6 @@ __device__ __forceinline__ void set_dev_error(int* err, int bit) {
     if (err) atomicOr(err, bit);
 }
 
-// frac(s) in [0,1) quantised to 32-bit turns (FP64 throughout).
-__device__ __forceinline__ uint32_t turns_u32(double s) {
-    double fr = s - floor(s);
-    // fr*2^32 < 2^32; rounding may give 2^32, which wraps to 0 (the same turn)
-    unsigned long long u = __double2ull_rn(fr * 4294967296.0);
-    return (uint32_t)u;
-}
-
 // Phase factor exp(+i 2 pi P / 2^32) for a 32-bit turn count P.
 __device__ __forceinline__ void phase_to_cs(uint32_t P, float& c, float& s) {
     float x = (float)(int32_t)P * 0x1p-31f;  // P/2^31 in [-1, 1): angle = pi * x
