@@ -28,9 +28,10 @@
 //     accumulate) into one of two TMEM accumulators; after `chunk_stages`
 //     stages it hands the accumulator to the epilogues and continues in the
 //     other one.
-//   * 4 epilogue warps per CTA add each chunk's FP32 sums into FP64 running
-//     totals in an L2-resident scratch block (one per CTA) and, after the last
-//     chunk of a tile, recombine the quadrants in FP64 into S and I = |S|^2.
+//   * 4 epilogue warps per CTA add each chunk's FP32 sums into running totals
+//     kept as error-free FP32 pairs (hi + lo, updated by TwoSum) in an
+//     L2-resident scratch block (one per CTA) and, after the last chunk of a
+//     tile, recombine the quadrants in FP64 into S and I = |S|^2.
 // The atoms arrive in a coprime-stride permuted order (see the phase kernel),
 // so the partial sums over a chunk behave like random walks even for ordered
 // crystals and the FP32 accumulator never sums a coherent run of terms.
@@ -87,7 +88,7 @@ struct TcArgs {
     int chunk_stages;
     float* I;
     float* amp;
-    double* scratch;  // [gridDim.x][256][128] FP64 running totals
+    double* scratch;  // [gridDim.x][256][128] running totals as FP32 pairs (hi, lo)
     int* err;
     int64_t timeout_ns;
 };
@@ -512,7 +513,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
         const int row = warp * 32 + lane;
         const bool re_row = (lane & 2) == 0;
         const int xi = kHalf * (int)rank + 2 * (row >> 2) + (row & 1);
-        double* scr = args.scratch + (size_t)blockIdx.x * 256 * 128 + row;
+        float2* scr = reinterpret_cast<float2*>(args.scratch) + (size_t)blockIdx.x * 256 * 128 + row;
         const uint32_t acc_empty_c0 = map_to_rank(smem_u32(&ctl->acc_empty[0]), 0);
         int64_t a_cnt = 0;
         bool ok = true;
@@ -537,17 +538,32 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                     uint32_t r[16];
                     tmem_ld16(dcol + 16 * j, r);
                     tmem_wait16(r);
-                    double v[16];
+                    // running total per value as an unevaluated FP32 pair hi + lo,
+                    // updated with the error-free sum TwoSum(hi, chunk)
+                    float hi[16], lo[16];
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        v[i] = (double)__uint_as_float(r[i]);
-                        if (!first) v[i] += scr[(size_t)(16 * j + i) * 128];
+                        const float c = __uint_as_float(r[i]);
+                        if (first) {
+                            hi[i] = c;
+                            lo[i] = 0.0f;
+                        } else {
+                            const float2 t = scr[(size_t)(16 * j + i) * 128];
+                            const float s = t.x + c;
+                            const float bb = s - t.x;
+                            const float e = (t.x - (s - bb)) + (c - bb);
+                            hi[i] = s;
+                            lo[i] = t.y + e;
+                        }
                     }
                     if (!last) {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) scr[(size_t)(16 * j + i) * 128] = v[i];
+                        for (int i = 0; i < 16; ++i) scr[(size_t)(16 * j + i) * 128] = make_float2(hi[i], lo[i]);
                         continue;
                     }
+                    double v[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = (double)hi[i] + (double)lo[i];
                     // columns 16j .. 16j+15 hold n_y local m = 8j .. 8j+7 in groups of 4
                     // (Re m, Re m+1, Im m, Im m+1); the Re lane finishes m = 8j..8j+3 with
                     // the Im values of its partner lane (lane ^ 2), the Im lane m = 8j+4..8j+7
