@@ -40,6 +40,10 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <queue>
+#include <vector>
+
 #include "xs_internal.h"
 
 namespace xs {
@@ -78,17 +82,13 @@ struct SmemCtl {
 constexpr size_t kSmemBytes = 1024 + kStages * kStageBytes + sizeof(SmemCtl);
 
 struct TcArgs {
-    const uint4* rec;
-    int64_t n_pad;
-    int n_frames;
-    GridDesc g;
-    int tiles_x, tiles_y;
-    int64_t n_units;
-    int n_stages;
+    TcTraj single;          // the trajectory when `units` is null
+    int64_t single_units;   // its units, assigned round-robin to the pairs
+    const TcTraj* trajs;    // batched: trajectory table
+    const int4* units;      // batched: (traj, frame, plane, tile_x | tile_y << 16), pair by pair
+    const int* pair_start;  // batched: [n_pairs + 1] offsets into `units`
     int chunk_stages;
-    float* I;
-    float* amp;
-    double* scratch;  // [gridDim.x][256][128] running totals as FP32 pairs (hi, lo)
+    double* scratch;        // [gridDim.x][256][128] running totals as FP32 pairs (hi, lo)
     int* err;
     int64_t timeout_ns;
 };
@@ -297,19 +297,54 @@ __device__ __forceinline__ uint32_t chunk_off(int mn, int k) {
            ((uint32_t)(((mn & 63) >> 3) ^ (k & 7)) << 4);
 }
 
-struct UnitPos {
+// one tile of one frame and plane, with what every role needs to work on it
+struct Unit {
+    const uint4* rec;  // records of the unit's frame
+    float* I;
+    float* amp;
+    int n_stages;
+    int nx0, nx, ny0, ny, nz0, nz;
     int t, iz, tx, ty;
 };
 
-__device__ __forceinline__ UnitPos decode_unit(int64_t u, const TcArgs& a) {
-    UnitPos p;
-    p.tx = (int)(u % a.tiles_x);
-    int64_t r = u / a.tiles_x;
-    p.ty = (int)(r % a.tiles_y);
-    r /= a.tiles_y;
-    p.iz = (int)(r % a.g.nz);
-    p.t = (int)(r / a.g.nz);
-    return p;
+__device__ __forceinline__ Unit make_unit(const TcTraj& tr, int t, int iz, int tx, int ty) {
+    Unit u;
+    u.rec = tr.rec + (int64_t)t * tr.n_pad;
+    u.I = tr.I;
+    u.amp = tr.amp;
+    u.n_stages = tr.n_stages;
+    u.nx0 = tr.nx0;
+    u.nx = tr.nx;
+    u.ny0 = tr.ny0;
+    u.ny = tr.ny;
+    u.nz0 = tr.nz0;
+    u.nz = tr.nz;
+    u.t = t;
+    u.iz = iz;
+    u.tx = tx;
+    u.ty = ty;
+    return u;
+}
+
+// unit k of `pair`: round-robin over a single trajectory, or the pair's list
+__device__ __forceinline__ Unit get_unit(const TcArgs& a, int64_t pair, int64_t n_pairs, int64_t k) {
+    if (!a.units) {
+        const TcTraj& tr = a.single;
+        const int64_t u = pair + k * n_pairs;
+        const int tx = (int)(u % tr.tiles_x);
+        int64_t r = u / tr.tiles_x;
+        const int ty = (int)(r % tr.tiles_y);
+        r /= tr.tiles_y;
+        const int iz = (int)(r % tr.nz);
+        return make_unit(tr, (int)(r / tr.nz), iz, tx, ty);
+    }
+    const int4 w = a.units[a.pair_start[pair] + k];
+    return make_unit(a.trajs[w.x], w.y, w.z, w.w & 0xFFFF, w.w >> 16);
+}
+
+__device__ __forceinline__ int64_t units_of_pair(const TcArgs& a, int64_t pair, int64_t n_pairs) {
+    if (!a.units) return a.single_units > pair ? (a.single_units - 1 - pair) / n_pairs + 1 : 0;
+    return a.pair_start[pair + 1] - a.pair_start[pair];
 }
 
 template <bool BF16>
@@ -351,8 +386,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
     tc_fence_after();
     const uint32_t tmem = ctl->tmem_base;
 
-    const int64_t my_units = args.n_units > pair ? (args.n_units - 1 - pair) / n_pairs + 1 : 0;
-    const int n_chunks = (args.n_stages + args.chunk_stages - 1) / args.chunk_stages;
+    const int64_t my_units = units_of_pair(args, pair, n_pairs);
 
     if (warp >= kMmaWarp + 1) {
         // ------------------------------------------------------------ producers
@@ -363,35 +397,29 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
         const bool is_a = ri < 2;
         const int run0 = kRun * (ri & 1);
         const int k = 32 * (w & 1) + lane;
-        const int n_st = args.n_stages;
         const uint32_t full_c0 = map_to_rank(smem_u32(&ctl->full[0]), 0);
         int slot = 0;
         uint32_t phase = 0;  // parity of the current pass over the ring of stages
-        const uint4* rec_cur = nullptr;
-        UnitPos up{};
-        if (my_units > 0) {
-            up = decode_unit(pair, args);
-            rec_cur = args.rec + (int64_t)up.t * args.n_pad + k;
-        }
+        Unit up{};
+        if (my_units > 0) up = get_unit(args, pair, n_pairs, 0);
         uint4 r_next = make_uint4(0, 0, 0, 0);
-        if (my_units > 0) r_next = __ldg(rec_cur);
+        if (my_units > 0) r_next = __ldg(up.rec + k);
         bool stop = false;
         for (int64_t ku = 0; ku < my_units && !stop; ++ku) {
-            UnitPos up_next{};
-            const uint4* rec_next_unit = nullptr;
-            if (ku + 1 < my_units) {
-                up_next = decode_unit(pair + (ku + 1) * n_pairs, args);
-                rec_next_unit = args.rec + (int64_t)up_next.t * args.n_pad + k;
-            }
-            const uint32_t n0 = is_a ? (uint32_t)(args.g.nx0 + up.tx * kTile + kHalf * (int)rank + run0)
-                                     : (uint32_t)(args.g.ny0 + up.ty * kTile + kHalf * (int)rank + run0);
-            const uint32_t nz = (uint32_t)(args.g.nz0 + up.iz);
+            Unit up_next{};
+            const bool has_next = ku + 1 < my_units;
+            if (has_next) up_next = get_unit(args, pair, n_pairs, ku + 1);
+            const int n_st = up.n_stages;
+            const uint4* rec_cur = up.rec + k;
+            const uint32_t n0 = is_a ? (uint32_t)(up.nx0 + up.tx * kTile + kHalf * (int)rank + run0)
+                                     : (uint32_t)(up.ny0 + up.ty * kTile + kHalf * (int)rank + run0);
+            const uint32_t nz = (uint32_t)(up.nz0 + up.iz);
             for (int s = 0; s < n_st; ++s) {
                 const uint4 r = r_next;
                 if (s + 1 < n_st)
                     r_next = __ldg(rec_cur + (int64_t)(s + 1) * kBK);
-                else if (rec_next_unit)
-                    r_next = __ldg(rec_next_unit);
+                else if (has_next)
+                    r_next = __ldg(up_next.rec + k);
                 // exact step z^2 and seeds E(n0), E(n0 + 1) of this thread's run
                 const uint32_t U = is_a ? r.x : r.y;
                 const float2 z2 = cis_turns(2u * U, ctl->tab);
@@ -450,7 +478,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                 }
             }
             up = up_next;
-            rec_cur = rec_next_unit;
         }
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issue
@@ -461,6 +488,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
             uint32_t phase = 0;
             bool ok = true;
             for (int64_t ku = 0; ku < my_units && ok; ++ku) {
+                const int n_stages = get_unit(args, pair, n_pairs, ku).n_stages;
+                const int n_chunks = (n_stages + args.chunk_stages - 1) / args.chunk_stages;
                 for (int c = 0; c < n_chunks && ok; ++c, ++a_cnt) {
                     const int b = (int)(a_cnt & 1);
                     const uint32_t use = (uint32_t)(a_cnt >> 1);
@@ -472,7 +501,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                     tc_fence_after();
                     const uint32_t d_tmem = tmem + (uint32_t)b * 256u;
                     const int s0 = c * args.chunk_stages;
-                    const int s1 = min(args.n_stages, s0 + args.chunk_stages);
+                    const int s1 = min(n_stages, s0 + args.chunk_stages);
                     for (int s = s0; s < s1; ++s) {
                         if (!wait_bar(&ctl->full[slot], phase, abort_flag, args.err, args.timeout_ns, 20000u)) {
                             ok = false;
@@ -518,7 +547,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
         int64_t a_cnt = 0;
         bool ok = true;
         for (int64_t ku = 0; ku < my_units && ok; ++ku) {
-            const UnitPos up = decode_unit(pair + ku * n_pairs, args);
+            const Unit up = get_unit(args, pair, n_pairs, ku);
+            const int n_chunks = (up.n_stages + args.chunk_stages - 1) / args.chunk_stages;
             for (int c = 0; c < n_chunks; ++c, ++a_cnt) {
                 const int b = (int)(a_cnt & 1);
                 const uint32_t use = (uint32_t)(a_cnt >> 1);
@@ -575,7 +605,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                         rcv[i] = __shfl_xor_sync(0xffffffffu, snd, 2);
                     }
                     const int ix = up.tx * kTile + xi;
-                    if (ix < args.g.nx) {
+                    if (ix < up.nx) {
 #pragma unroll
                         for (int hh = 0; hh < 2; ++hh) {
 #pragma unroll
@@ -588,13 +618,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                                 const double sim = p_ri + p_ir;
                                 const int m = 8 * j + (re_row ? 0 : 4) + 2 * hh + t;
                                 const int iy = up.ty * kTile + m;
-                                if (iy < args.g.ny) {
-                                    const int64_t o =
-                                        (((int64_t)up.t * args.g.nz + up.iz) * args.g.ny + iy) * args.g.nx + ix;
-                                    args.I[o] = (float)(sre * sre + sim * sim);
-                                    if (args.amp) {
-                                        args.amp[2 * o] = (float)sre;
-                                        args.amp[2 * o + 1] = (float)sim;
+                                if (iy < up.ny) {
+                                    const int64_t o = (((int64_t)up.t * up.nz + up.iz) * up.ny + iy) * up.nx + ix;
+                                    up.I[o] = (float)(sre * sre + sim * sim);
+                                    if (up.amp) {
+                                        up.amp[2 * o] = (float)sre;
+                                        up.amp[2 * o + 1] = (float)sim;
                                     }
                                 }
                             }
@@ -621,11 +650,7 @@ bool tc_supported(const GridDesc& g) { return g.nx >= 1 && g.ny >= 1 && g.nz >= 
 
 int64_t tc_atom_multiple() { return kBK; }
 
-TcPlan plan_tc(int64_t n_pad, int64_t n_frames, const GridDesc& g, int num_sms, int chunk_stages) {
-    TcPlan p;
-    p.tiles_x = (g.nx + kTile - 1) / kTile;
-    p.tiles_y = (g.ny + kTile - 1) / kTile;
-    const int64_t units = n_frames * g.nz * p.tiles_x * p.tiles_y;
+int tc_pair_capacity(int num_sms) {
     // pairs that can be resident at once (a cluster needs two SMs of one GPC)
     static int max_pairs = -1;
     if (max_pairs < 0) {
@@ -651,43 +676,108 @@ TcPlan plan_tc(int64_t n_pad, int64_t n_frames, const GridDesc& g, int num_sms, 
         }
         max_pairs = n;
     }
-    p.grid = 2 * (int)std::min<int64_t>(units, max_pairs);
-    p.chunk_stages = chunk_stages > 0 ? chunk_stages : 32;
-    (void)n_pad;
-    return p;
+    return max_pairs;
 }
 
-size_t tc_scratch_bytes(const TcPlan& plan) { return (size_t)plan.grid * 256 * 128 * sizeof(double); }
+TcTraj tc_traj(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g, float* I, float* amp) {
+    TcTraj t;
+    t.rec = reinterpret_cast<const uint4*>(rec);
+    t.I = I;
+    t.amp = amp;
+    t.n_pad = n_pad;
+    t.n_stages = (int)(n_pad / kBK);
+    t.tiles_x = (g.nx + kTile - 1) / kTile;
+    t.tiles_y = (g.ny + kTile - 1) / kTile;
+    t.nx0 = g.nx0;
+    t.nx = g.nx;
+    t.ny0 = g.ny0;
+    t.ny = g.ny;
+    t.nz0 = g.nz0;
+    t.nz = g.nz;
+    t.n_frames = (int)n_frames;
+    return t;
+}
 
-cudaError_t launch_tc(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g, const TcPlan& plan,
-                      bool bf16, float* I, float* amp, double* scratch, int* err, int64_t timeout_ns,
-                      cudaStream_t st) {
-    if (n_pad % kBK != 0) return cudaErrorInvalidValue;
-    TcArgs a;
-    a.rec = reinterpret_cast<const uint4*>(rec);
-    a.n_pad = n_pad;
-    a.n_frames = (int)n_frames;
-    a.g = g;
-    a.tiles_x = plan.tiles_x;
-    a.tiles_y = plan.tiles_y;
-    a.n_units = n_frames * g.nz * plan.tiles_x * plan.tiles_y;
-    a.n_stages = (int)(n_pad / kBK);
-    a.chunk_stages = plan.chunk_stages;
-    a.I = I;
-    a.amp = amp;
-    a.scratch = scratch;
-    a.err = err;
-    a.timeout_ns = timeout_ns;
-    if (a.n_units == 0) return cudaSuccess;
+int64_t tc_units(const TcTraj& t) { return (int64_t)t.n_frames * t.nz * t.tiles_x * t.tiles_y; }
+
+size_t tc_scratch_bytes(int n_pairs) { return (size_t)(2 * n_pairs) * 256 * 128 * sizeof(double); }
+
+void tc_build_lists(const std::vector<TcTraj>& trajs, int n_pairs, std::vector<int4>& units,
+                    std::vector<int>& pair_start) {
+    // longest-processing-time first: units sorted by cost (stages), each given
+    // to the least loaded pair; ties keep trajectory, frame and tile order
+    struct Item {
+        int64_t cost;
+        int4 u;
+    };
+    std::vector<Item> items;
+    for (size_t i = 0; i < trajs.size(); ++i) {
+        const TcTraj& t = trajs[i];
+        for (int f = 0; f < t.n_frames; ++f)
+            for (int z = 0; z < t.nz; ++z)
+                for (int ty = 0; ty < t.tiles_y; ++ty)
+                    for (int tx = 0; tx < t.tiles_x; ++tx)
+                        items.push_back({t.n_stages, make_int4((int)i, f, z, tx | (ty << 16))});
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.cost > b.cost; });
+    using Load = std::pair<int64_t, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int p = 0; p < n_pairs; ++p) heap.push({0, p});
+    std::vector<std::vector<int4>> per(n_pairs);
+    for (const Item& it : items) {
+        Load l = heap.top();
+        heap.pop();
+        per[l.second].push_back(it.u);
+        heap.push({l.first + it.cost, l.second});
+    }
+    units.clear();
+    pair_start.assign((size_t)n_pairs + 1, 0);
+    for (int p = 0; p < n_pairs; ++p) {
+        pair_start[p] = (int)units.size();
+        units.insert(units.end(), per[p].begin(), per[p].end());
+    }
+    pair_start[n_pairs] = (int)units.size();
+}
+
+static cudaError_t launch(const TcArgs& a, int n_pairs, bool bf16, cudaStream_t st) {
     const void* fn = bf16 ? (const void*)tc_kernel<true> : (const void*)tc_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
     ++tl_kernel_launches;
     if (bf16)
-        tc_kernel<true><<<plan.grid, kThreads, kSmemBytes, st>>>(a);
+        tc_kernel<true><<<2 * n_pairs, kThreads, kSmemBytes, st>>>(a);
     else
-        tc_kernel<false><<<plan.grid, kThreads, kSmemBytes, st>>>(a);
+        tc_kernel<false><<<2 * n_pairs, kThreads, kSmemBytes, st>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_tc_single(const TcTraj& tr, int n_pairs, int chunk_stages, bool bf16, double* scratch, int* err,
+                             int64_t timeout_ns, cudaStream_t st) {
+    if (tr.n_pad % kBK != 0) return cudaErrorInvalidValue;
+    TcArgs a{};
+    a.single = tr;
+    a.single_units = tc_units(tr);
+    a.chunk_stages = chunk_stages > 0 ? chunk_stages : 32;
+    a.scratch = scratch;
+    a.err = err;
+    a.timeout_ns = timeout_ns;
+    if (a.single_units == 0) return cudaSuccess;
+    n_pairs = (int)std::min<int64_t>(n_pairs, a.single_units);
+    return launch(a, n_pairs, bf16, st);
+}
+
+cudaError_t launch_tc_batch(const TcTraj* d_trajs, const int4* d_units, const int* d_pair_start, int n_pairs,
+                            int chunk_stages, bool bf16, double* scratch, int* err, int64_t timeout_ns,
+                            cudaStream_t st) {
+    TcArgs a{};
+    a.trajs = d_trajs;
+    a.units = d_units;
+    a.pair_start = d_pair_start;
+    a.chunk_stages = chunk_stages > 0 ? chunk_stages : 32;
+    a.scratch = scratch;
+    a.err = err;
+    a.timeout_ns = timeout_ns;
+    return launch(a, n_pairs, bf16, st);
 }
 
 }  // namespace xs

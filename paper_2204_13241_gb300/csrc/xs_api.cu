@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <string>
 #include <tuple>
@@ -122,6 +123,15 @@ struct xs_context {
         cudaEvent_t a, b;
         int64_t kernels;
     };
+    struct Graph {
+        cudaGraphExec_t exec;
+        int64_t kernels;
+    };
+    std::map<std::string, Graph> graphs;  // captured batched launches
+    void clear_graphs() {
+        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.exec);
+        graphs.clear();
+    }
     bool prof_on = false;
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> event_pool;
@@ -164,6 +174,7 @@ xs_status ensure_ws(xs_context* ctx, size_t bytes) {
     if (bytes <= ctx->ws_bytes) return XS_OK;
     if (ctx->ws) {
         XS_CUDA(cudaDeviceSynchronize());
+        ctx->clear_graphs();  // captured launches point into the old block
         ctx->raw_free(ctx->ws);
         ctx->ws = nullptr;
         ctx->ws_bytes = 0;
@@ -186,6 +197,7 @@ xs_status upload_const(xs_context* ctx, const char* tag, const std::vector<char>
     // earlier launches on the stream may still read the old tables
     XS_CUDA(cudaStreamSynchronize(st));
     if (blob.size() > slot.bytes) {
+        ctx->clear_graphs();  // captured launches may point into the old tables
         ctx->raw_free(slot.dev);
         slot.bytes = blob.size() + 4096;
         slot.dev = ctx->raw_alloc(slot.bytes);
@@ -288,6 +300,7 @@ xs_status xs_context_create(const xs_allocator* allocator, xs_context** out) {
 xs_status xs_context_destroy(xs_context* ctx) {
     if (!ctx) return XS_OK;
     cudaDeviceSynchronize();
+    ctx->clear_graphs();
     ctx->raw_free(ctx->ws);
     ctx->raw_free(ctx->d_err);
     for (auto& kv : ctx->consts) ctx->raw_free(kv.second.dev);
@@ -376,7 +389,8 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
         return fail(XS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
     if (traj->n_atoms < 0 || traj->n_frames < 0) return fail(XS_ERR_INVALID_ARG, "negative atom or frame count");
     if (traj->n_atoms > (int64_t)1 << 31) return fail(XS_ERR_INVALID_ARG, "more than 2^31 atoms");
-    if (traj->n_atoms > 0 && (!traj->pos || !traj->f)) return fail(XS_ERR_INVALID_ARG, "positions or form factors are NULL");
+    if (traj->n_atoms > 0 && traj->n_frames > 0 && (!traj->pos || !traj->f))
+        return fail(XS_ERR_INVALID_ARG, "positions or form factors are NULL");
     double hinv[9];
     if (!invert3(traj->box.h, hinv)) return fail(XS_ERR_INVALID_ARG, "singular or non-finite cell matrix");
     const GridDesc g = to_desc(grid);
@@ -411,14 +425,14 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
     if (fchunk > 65535) fchunk = 65535;
 
     DirectPlan dplan{};
-    TcPlan tplan0{};
+    int tc_pairs = 0;
     int chunk_stages = 32;
     if (use_tc) {
         auto key = std::make_tuple(n_pad, g.nx, g.ny, g.nz, (int)prec);
         auto it = ctx->tuned_chunk.find(key);
         if (it != ctx->tuned_chunk.end()) chunk_stages = it->second;
         if (chunk_override > 0) chunk_stages = chunk_override;
-        tplan0 = plan_tc(n_pad, fchunk, g, ctx->num_sms, chunk_stages);
+        tc_pairs = tc_pair_capacity(ctx->num_sms);
     } else {
         dplan = plan_direct(n_pad, fchunk, g, ctx->num_sms);
     }
@@ -431,7 +445,7 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
         return o;
     };
     const size_t o_rec = carve((size_t)fchunk * rec_per_frame);
-    const size_t o_part = carve(use_tc ? tc_scratch_bytes(tplan0) : dplan.partial_bytes);
+    const size_t o_part = carve(use_tc ? tc_scratch_bytes(tc_pairs) : dplan.partial_bytes);
     const size_t o_pos0 = carve(pos_host ? (size_t)fchunk * pos_per_frame : 0);
     const size_t o_pos1 = carve(pos_host ? (size_t)fchunk * pos_per_frame : 0);
     const size_t o_f = carve(pos_host ? (size_t)N * sizeof(float) : 0);
@@ -490,10 +504,10 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
             XS_CUDA(traced(ctx, "phase", st, [&] { return launch_phase(pos_c, f_dev, N, nf, n_pad, hm, popt, rec, ctx->d_err, st); }));
             if (pos_host) XS_CUDA(cudaEventRecord(ctx->ev_consumed[c & 1], st));
             if (use_tc) {
-                TcPlan pc = plan_tc(n_pad, nf, g, ctx->num_sms, chunk_stages);
+                const TcTraj tr = tc_traj(rec, n_pad, nf, g, Ic, Ac);
                 XS_CUDA(traced(ctx, "tc", st, [&] {
-                    return launch_tc(rec, n_pad, nf, g, pc, prec == XS_PREC_SPLIT_BF16, Ic, Ac,
-                                     reinterpret_cast<double*>(ws + o_part), ctx->d_err, ctx->timeout_ns, st);
+                    return launch_tc_single(tr, tc_pairs, chunk_stages, prec == XS_PREC_SPLIT_BF16,
+                                            reinterpret_cast<double*>(ws + o_part), ctx->d_err, ctx->timeout_ns, st);
                 }));
             } else {
                 DirectPlan pc = plan_direct(n_pad, nf, g, ctx->num_sms);
@@ -521,12 +535,153 @@ xs_status xs_intensity(xs_context* ctx, const xs_traj* traj, const xs_qgrid* gri
 xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, int32_t n_traj,
                                xs_precision prec, float* const* I_out, void* cuda_stream) {
     if (!ctx || !traj || !grid || !I_out || n_traj < 1) return fail(XS_ERR_INVALID_ARG, "bad batched arguments");
-    for (int32_t i = 0; i < n_traj; ++i) {
-        if (traj[i].pos_on_host) return fail(XS_ERR_INVALID_ARG, "batched trajectories need device positions");
-        xs_status s = intensity_impl(ctx, &traj[i], &grid[i], prec, I_out[i], nullptr,
-                                     static_cast<cudaStream_t>(cuda_stream), 0);
-        if (s != XS_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (prec == XS_PREC_FP32_DIRECT) {
+        for (int32_t i = 0; i < n_traj; ++i) {
+            if (traj[i].pos_on_host) return fail(XS_ERR_INVALID_ARG, "batched trajectories need device positions");
+            xs_status s = intensity_impl(ctx, &traj[i], &grid[i], prec, I_out[i], nullptr, st, 0);
+            if (s != XS_OK) return s;
+        }
+        return XS_OK;
     }
+    if (prec != XS_PREC_SPLIT_FP16 && prec != XS_PREC_SPLIT_BF16)
+        return fail(XS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    // validate and lay out the phase records of every trajectory
+    struct Job {
+        int64_t N, T, n_pad;
+        double hinv[9];
+        GridDesc g;
+        size_t rec_off;
+    };
+    std::vector<Job> jobs((size_t)n_traj);
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        size_t o = round_up((int64_t)off, 256);
+        off = o + bytes;
+        return o;
+    };
+    for (int32_t i = 0; i < n_traj; ++i) {
+        const xs_traj& t = traj[i];
+        xs_status s = check_grid(&grid[i]);
+        if (s != XS_OK) return s;
+        if (t.pos_on_host) return fail(XS_ERR_INVALID_ARG, "trajectory %d: batched positions must be on the device", i);
+        if (t.n_atoms < 0 || t.n_frames < 0) return fail(XS_ERR_INVALID_ARG, "trajectory %d: negative size", i);
+        if (t.n_atoms > 0 && t.n_frames > 0 && (!t.pos || !t.f))
+            return fail(XS_ERR_INVALID_ARG, "trajectory %d: NULL positions", i);
+        if (t.n_frames > 0 && grid[i].nx * (int64_t)grid[i].ny * grid[i].nz > 0 && !I_out[i])
+            return fail(XS_ERR_INVALID_ARG, "trajectory %d: NULL output", i);
+        Job& j = jobs[(size_t)i];
+        if (!invert3(t.box.h, j.hinv)) return fail(XS_ERR_INVALID_ARG, "trajectory %d: singular cell matrix", i);
+        j.N = t.n_atoms;
+        j.T = t.n_frames;
+        j.n_pad = round_up(j.N > 0 ? j.N : 1, 64);
+        j.g = to_desc(&grid[i]);
+        if (j.T > 65535 * 8) return fail(XS_ERR_INVALID_ARG, "trajectory %d: too many frames", i);
+        j.rec_off = carve((size_t)j.T * j.n_pad * sizeof(AtomRec));
+    }
+    const int cap = tc_pair_capacity(ctx->num_sms);
+    const size_t o_scratch = carve(tc_scratch_bytes(cap));
+    xs_status s = ensure_ws(ctx, off + 256);
+    if (s != XS_OK) return s;
+    char* ws = static_cast<char*>(ctx->ws);
+
+    // trajectory table and per-pair unit lists (longest first)
+    std::vector<TcTraj> trs;
+    std::vector<int> which;  // trajectory index of each table entry
+    std::vector<int> empty;  // trajectories without atoms: I = 0
+    for (int32_t i = 0; i < n_traj; ++i) {
+        const Job& j = jobs[(size_t)i];
+        if (j.T == 0 || j.g.pixels() == 0) continue;
+        if (j.N == 0) {
+            empty.push_back(i);
+            continue;
+        }
+        trs.push_back(tc_traj(reinterpret_cast<AtomRec*>(ws + j.rec_off), j.n_pad, j.T, j.g, I_out[i], nullptr));
+        which.push_back(i);
+    }
+    for (int i : empty)
+        XS_CUDA(cudaMemsetAsync(I_out[i], 0, (size_t)jobs[(size_t)i].T * jobs[(size_t)i].g.pixels() * sizeof(float), st));
+    if (trs.empty()) return XS_OK;
+    int64_t total_units = 0;
+    for (const TcTraj& t : trs) total_units += tc_units(t);
+    const int n_pairs = (int)std::min<int64_t>(cap, total_units);
+    std::vector<int4> units;
+    std::vector<int> pair_start;
+    tc_build_lists(trs, n_pairs, units, pair_start);
+    if (units.size() > (size_t)INT32_MAX) return fail(XS_ERR_UNSUPPORTED, "too many work units");
+    std::vector<char> blob;
+    const size_t o_tr = push(blob, trs.data(), trs.size());
+    const size_t o_units = push(blob, units.data(), units.size());
+    const size_t o_ps = push(blob, pair_start.data(), pair_start.size());
+    void* d = nullptr;
+    s = upload_const(ctx, "tc_batch", blob, st, &d);
+    if (s != XS_OK) return s;
+    char* dc = static_cast<char*>(d);
+    int chunk = 32;
+    {
+        auto it = ctx->tuned_chunk.find(std::make_tuple(trs[trs.size() / 2].n_pad, trs[trs.size() / 2].nx,
+                                                        trs[trs.size() / 2].ny, trs[trs.size() / 2].nz, (int)prec));
+        if (it != ctx->tuned_chunk.end()) chunk = it->second;
+    }
+    const bool bf16 = prec == XS_PREC_SPLIT_BF16;
+    auto enqueue = [&]() -> cudaError_t {
+        for (size_t e = 0; e < trs.size(); ++e) {
+            const Job& j = jobs[(size_t)which[e]];
+            const xs_traj& t = traj[which[e]];
+            Mat3 hm;
+            for (int k = 0; k < 9; ++k) hm.a[k] = j.hinv[k];
+            PhaseOpts popt;
+            popt.ortho = is_ortho(j.hinv);
+            popt.need_z = !(j.g.nz == 1 && j.g.nz0 == 0);
+            popt.perm_mul = coprime_stride(j.n_pad);
+            cudaError_t err = launch_phase(t.pos, t.f, j.N, j.T, j.n_pad, hm, popt,
+                                           reinterpret_cast<AtomRec*>(ws + j.rec_off), ctx->d_err, st);
+            if (err != cudaSuccess) return err;
+        }
+        return launch_tc_batch(reinterpret_cast<const TcTraj*>(dc + o_tr), reinterpret_cast<const int4*>(dc + o_units),
+                               reinterpret_cast<const int*>(dc + o_ps), n_pairs, chunk, bf16,
+                               reinterpret_cast<double*>(ws + o_scratch), ctx->d_err, ctx->timeout_ns, st);
+    };
+    // the same batch (same tables, inputs, outputs and workspace) replays a
+    // captured graph; anything else is captured once and kept
+    std::string key(blob.begin(), blob.end());
+    for (int32_t i = 0; i < n_traj; ++i) {
+        const void* ptrs[2] = {traj[i].pos, traj[i].f};
+        key.append(reinterpret_cast<const char*>(ptrs), sizeof(ptrs));
+        key.append(reinterpret_cast<const char*>(traj[i].box.h), sizeof(traj[i].box.h));
+    }
+    key.append(reinterpret_cast<const char*>(&chunk), sizeof(chunk));
+    key.append(reinterpret_cast<const char*>(&ctx->timeout_ns), sizeof(ctx->timeout_ns));
+    key.append(bf16 ? "b" : "h");
+    const void* wsp = ctx->ws;
+    key.append(reinterpret_cast<const char*>(&wsp), sizeof(wsp));
+    const cudaError_t launched = traced(ctx, "batched", st, [&]() -> cudaError_t {
+        auto it = ctx->graphs.find(key);
+        if (it == ctx->graphs.end() && st != nullptr) {
+            cudaGraph_t graph = nullptr;
+            const int64_t before = tl_kernel_launches;
+            cudaError_t err = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (err == cudaSuccess) {
+                const cudaError_t le = enqueue();
+                err = cudaStreamEndCapture(st, &graph);
+                if (le != cudaSuccess) err = le;
+            }
+            const int64_t captured = tl_kernel_launches - before;
+            tl_kernel_launches = before;  // counted again at each replay
+            cudaGraphExec_t exec = nullptr;
+            if (err == cudaSuccess) err = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (err != cudaSuccess) {
+                cudaGetLastError();
+                return err;
+            }
+            it = ctx->graphs.emplace(key, xs_context::Graph{exec, captured}).first;
+        }
+        if (it == ctx->graphs.end()) return enqueue();  // legacy default stream: no capture
+        tl_kernel_launches += it->second.kernels;
+        return cudaGraphLaunch(it->second.exec, st);
+    });
+    if (launched != cudaSuccess) return fail(XS_ERR_CUDA, "batched launch: %s", cudaGetErrorString(launched));
     return XS_OK;
 }
 

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "xs_common.cuh"
@@ -47,18 +48,32 @@ cudaError_t launch_direct(const AtomRec* rec, int64_t n_pad, int64_t n_frames, c
                           cudaStream_t st);
 
 // ---- tensor-core split-precision contraction ----------------------------
-struct TcPlan {
-    int chunk_stages;      // stages of 64 atoms accumulated in TMEM before a flush
-    int grid;              // persistent CTAs
-    int tiles_x, tiles_y;  // 128-pixel tiles per frame plane along x and y
+// One trajectory of a launch: phase records [n_frames][n_pad] (slot order of
+// the phase kernel), outputs, and its grid; tiles are 128 x 128 pixels.
+struct TcTraj {
+    const uint4* rec;
+    float* I;
+    float* amp;
+    int64_t n_pad;
+    int n_stages;  // n_pad / 64
+    int tiles_x, tiles_y;
+    int nx0, nx, ny0, ny, nz0, nz;
+    int n_frames;
 };
 bool tc_supported(const GridDesc& g);
 int64_t tc_atom_multiple();
-TcPlan plan_tc(int64_t n_pad, int64_t n_frames, const GridDesc& g, int num_sms, int chunk_stages);
-size_t tc_scratch_bytes(const TcPlan& plan);  // FP64 running totals, one block per CTA
-cudaError_t launch_tc(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g,
-                      const TcPlan& plan, bool bf16, float* I, float* amp, double* scratch, int* err,
-                      int64_t timeout_ns, cudaStream_t st);
+int tc_pair_capacity(int num_sms);  // co-resident CTA pairs
+TcTraj tc_traj(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g, float* I, float* amp);
+int64_t tc_units(const TcTraj& t);  // frames x planes x tiles
+size_t tc_scratch_bytes(int n_pairs);
+// per-pair unit lists (traj, frame, plane, tile_x | tile_y << 16), longest first
+void tc_build_lists(const std::vector<TcTraj>& trajs, int n_pairs, std::vector<int4>& units,
+                    std::vector<int>& pair_start);
+cudaError_t launch_tc_single(const TcTraj& tr, int n_pairs, int chunk_stages, bool bf16, double* scratch, int* err,
+                             int64_t timeout_ns, cudaStream_t st);
+cudaError_t launch_tc_batch(const TcTraj* d_trajs, const int4* d_units, const int* d_pair_start, int n_pairs,
+                            int chunk_stages, bool bf16, double* scratch, int* err, int64_t timeout_ns,
+                            cudaStream_t st);
 
 // ---- g2 -----------------------------------------------------------------
 cudaError_t launch_g2(const float* I, int64_t T, int64_t P, const int32_t* d_taus, int n_tau,
