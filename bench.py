@@ -36,6 +36,13 @@ import numpy as np  # noqa: E402
 METRIC = "atom*pixel*frames/s"
 FALLBACK_PEAK = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0}
 
+# DRAM bytes (read + write) of one tc_kernel launch per frame of the 256,000-atom
+# workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
+# of a 160-frame launch of this exact kernel source: 656.05 MB + 12.98 MB.
+# The records streamed are proportional to the frames, so a launch over T
+# frames moves T times this.  Reported only while k_tc.cu is unchanged.
+TC_TRAFFIC = {"k_tc_sha256_prefix": "c382ee4acc296ffe", "bytes_per_frame": (656.046848e6 + 12.983296e6) / 160}
+
 
 def _args():
     ap = argparse.ArgumentParser()
@@ -49,6 +56,19 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     return ap.parse_args()
+
+
+def _tc_traffic(frames: int):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2204_13241_gb300", "csrc", "k_tc.cu")
+    try:
+        with open(src, "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+    except OSError:
+        return None
+    if not sha.startswith(TC_TRAFFIC["k_tc_sha256_prefix"]):
+        return None
+    return TC_TRAFFIC["bytes_per_frame"] * frames
 
 
 def _peaks():
@@ -248,7 +268,10 @@ def run_ours(args):
     peak = float(peaks.get("bf16_tflops_sustained", FALLBACK_PEAK["bf16_tflops_sustained"]))
     achieved = alg_flops / (tc_launch_ms * 1e-3) / 1e12
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": _tc_traffic(T),
+                "traffic_note": "ncu DRAM bytes of a 160-frame capture scaled by frames; "
+                                "algorithmic bytes per launch = T x (N x 16 B records + P x 4 B)",
+                "algorithmic_bytes": float(T) * (N * 16.0 + P * 4.0),
                 "kernel": "tc_kernel (split-FP16 contraction)", "kernel_ms_per_launch": tc_launch_ms,
                 "peak_source": f"{peak_src} bf16 sustained (fp16 dense rate = bf16)",
                 "executed_tflops": exe_flops / (tc_launch_ms * 1e-3) / 1e12,
