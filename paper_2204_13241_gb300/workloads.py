@@ -234,6 +234,16 @@ def config3() -> tuple[Trajectory, np.ndarray, QGrid]:
     return traj, target.astype(np.float32)[None], centered_plane(256)
 
 
+def config4(keep=None, n_frames: int = 10_000) -> tuple[Trajectory, QGrid]:
+    """FCC crystal of 100^3 cells (a = 4 A, L = 400 A, 4,000,000 sites) with 20 %
+    vacancies (3,200,000 atoms), thermal sigma 0.2 A, f = 1, 10,000 Brownian
+    frames of sigma 0.02 A, 512^2 plane (the volume mode uses
+    centered_volume(128)).  `keep` selects the frames to materialise: all
+    10,000 would be 384 GB of positions."""
+    traj = fcc_crystal(SEED_BASE + 4, 100, 4.0, 0.2, 0.2, (1.0,), n_frames, 0.02, keep)
+    return traj, centered_plane(512)
+
+
 def config2_params(n_traj: int = 64, seed: int = SEED_BASE + 2) -> list[dict]:
     """Per-trajectory parameters of the batched ideal-gas workload: atom
     counts log-uniform in [2e3, 5e5], density 0.02 A^-3, frame counts uniform
@@ -259,3 +269,47 @@ def weights_inverse_q2(grid: QGrid, box: np.ndarray) -> np.ndarray:
     L = float(box[0, 0])
     m = grid.miller().astype(np.float64) * (2.0 * math.pi / L)
     return (1.0 / (1.0 + (m ** 2).sum(axis=1))).astype(np.float32)
+
+
+def gas_on_device(params: dict, device, dtype_f=None):
+    """One ideal-gas trajectory of `config2_params` drawn on a CUDA device with
+    a seeded torch generator (the full batched workload is 75 GB of
+    positions, too much to draw on the host): base positions uniform in
+    [0, L)^3, then Brownian steps of sigma per component, accumulated in
+    float32.  Returns (pos float32 [T][N][3], f = 1 float32 [N], box)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(params["seed"]))
+    N, T, L = int(params["n_atoms"]), int(params["n_frames"]), float(params["L"])
+    pos = torch.empty((T, N, 3), dtype=torch.float32, device=device)
+    pos[0] = torch.rand((N, 3), generator=g, device=device, dtype=torch.float32) * L
+    if T > 1:
+        pos[1:] = torch.randn((T - 1, N, 3), generator=g, device=device, dtype=torch.float32) * params["sigma"]
+    pos.cumsum_(0)
+    f = torch.ones(N, dtype=torch.float32, device=device)
+    return pos, f, cubic_box(L)
+
+
+def speckle_series(seed: int, T: int, rho, device):
+    """Synthetic speckle intensities I(t, p) = |a(t, p)|^2 of a circular complex
+    Gaussian AR(1) amplitude a(t) = rho a(t-1) + sqrt(1 - rho^2) xi(t) with
+    E|a|^2 = 1, per pixel correlation `rho` (float32 tensor [P] on `device`).
+    Drawn on the device with a seeded torch generator; float32 [T][P].
+    For this process <I(t) I(t+tau)> / <I>^2 = 1 + rho^(2 tau)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    rho = rho.to(device=device, dtype=torch.float32)
+    P = rho.shape[0]
+    s = torch.sqrt(1.0 - rho * rho)
+    out = torch.empty((T, P), dtype=torch.float32, device=device)
+    a = torch.complex(torch.randn(P, generator=g, device=device), torch.randn(P, generator=g, device=device))
+    a = a * (0.5 ** 0.5)
+    for t in range(T):
+        if t > 0:
+            xi = torch.complex(torch.randn(P, generator=g, device=device), torch.randn(P, generator=g, device=device))
+            a = rho * a + s * xi * (0.5 ** 0.5)
+        out[t] = a.real * a.real + a.imag * a.imag
+    return out

@@ -1,0 +1,180 @@
+"""Full-size workloads on the tensor-core path, checked on sampled outputs.
+
+* The batched ideal-gas workload at its full size: 64 trajectories, 6.2e9
+  atom-frames, one persistent launch. Each trajectory is checked against the
+  FP64 oracle on its last frame. Its g2 is checked against the Brownian closed
+  form g2 - 1 = beta0 exp(-2 D q^2 tau) (Sec. 2.3, Eqs. g2_from_fq and fq_exp).
+* The large crystal: 3.2 million atoms, FCC with vacancies.
+  - A 512^2 plane, with positions streamed from host memory. This must equal
+    the device-resident path and match the oracle on sampled pixels.
+  - A 128^3 volume, sampled against the oracle.
+* g2 on 64 log-spaced delays and the XSVS contrast for K up to 1,000 summed
+  frames, both on 10,000 frames of a 512^2 speckle series. g2 is checked
+  against the oracle on sampled pixels and XSVS on sampled rings. Both are
+  also checked against the AR(1) closed forms.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import e_I
+from paper_2204_13241_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xs():
+    from paper_2204_13241_gb300 import build
+    build.build()
+    from paper_2204_13241_gb300 import api
+    return api
+
+
+def _sample_pixels(m, n, seed):
+    rng = np.random.default_rng(seed)
+    zero = np.flatnonzero(np.all(m == 0, axis=1))
+    pick = rng.choice(m.shape[0], min(n, m.shape[0]), replace=False)
+    return np.unique(np.concatenate([zero, pick]))
+
+
+def test_batched_ideal_gas_full_size(xs):
+    params = wl.config2_params()
+    trajs, grids = [], []
+    for p in params:
+        pos, f, box = wl.gas_on_device(p, "cuda")
+        trajs.append((pos, f, box))
+        grids.append(wl.centered_plane(p["side"]))
+    outs = xs.intensity_batched(trajs, grids, "bf16")
+    xs.Context.get().sync_status()
+    n_g2_checked = 0
+    for i, (p, (pos, f, box), grid, I) in enumerate(zip(params, trajs, grids, outs)):
+        T = p["n_frames"]
+        assert I.shape == (T, 1, grid.ny, grid.nx)
+        m = grid.miller()
+        pix = _sample_pixels(m, 64, 500 + i)
+        ref = oracle.intensity(pos[T - 1:T].cpu().numpy(), f.cpu().numpy(), box, m[pix])
+        got = I.reshape(T, -1)[T - 1:T, pix].cpu().numpy()
+        e, e0 = e_I(got, ref, m[pix])
+        assert e <= 1e-4 and e0 <= 1e-4, (i, e, e0)
+        # Brownian closed form on shells whose finite-T estimator bias
+        # (about 3 coth(D q^2) / T) stays below 0.01
+        if T < 1000:
+            continue
+        taus = [1, 2, 3]
+        g, _ = xs.g2(I.reshape(T, -1), taus)
+        g = g.cpu().numpy()
+        nn = np.sqrt((m.astype(np.float64) ** 2).sum(axis=1))
+        D, L, N = p["D"], p["L"], p["n_atoms"]
+        checked = 0
+        for shell in range(2, grid.nx // 2):
+            sel = np.abs(nn - shell) < 0.5
+            dq2 = D * (2 * math.pi * shell / L) ** 2
+            if sel.sum() < 20 or not (0.25 <= dq2 <= 1.0) or 3.0 / math.tanh(dq2) / T > 0.01:
+                continue
+            for it, tau in enumerate(taus):
+                est = g[it, sel].mean() - 1
+                want = (1 - 1.0 / N) * math.exp(-2 * dq2 * tau)
+                se = g[it, sel].std() / math.sqrt(sel.sum())
+                assert abs(est - want) < 5 * se + 0.02, (i, shell, tau, est, want)
+            checked += 1
+        n_g2_checked += checked > 0
+    assert n_g2_checked >= 5
+    del trajs, outs
+    torch.cuda.empty_cache()
+
+
+@pytest.fixture(scope="module")
+def crystal4():
+    traj, grid = wl.config4(keep=range(16))
+    return traj, grid
+
+
+def test_large_crystal_plane_streamed_from_host(xs, crystal4):
+    traj, grid = crystal4
+    pos_h = torch.from_numpy(traj.pos)
+    f_h = torch.from_numpy(traj.f)
+    I_h = xs.intensity(pos_h, f_h, traj.box, grid, "fp16")    # host in, host out
+    xs.Context.get().sync_status()
+    assert not I_h.is_cuda
+    pos_d = pos_h.cuda()
+    I_d = xs.intensity(pos_d, f_h.cuda(), traj.box, grid, "fp16")
+    xs.Context.get().sync_status()
+    assert torch.equal(I_h, I_d.cpu())
+    del pos_d, I_d
+    m = grid.miller()
+    pix = _sample_pixels(m, 512, 41)
+    frames = [0, 15]
+    ref = oracle.intensity(traj.pos[frames], traj.f, traj.box, m[pix])
+    got = I_h.reshape(I_h.shape[0], -1)[frames][:, pix].cpu().numpy()
+    e, e0 = e_I(got, ref, m[pix])
+    assert e <= 1e-4 and e0 <= 1e-4, (e, e0)
+    assert torch.isfinite(I_h).all()
+
+
+def test_large_crystal_volume(xs, crystal4):
+    traj, _ = crystal4
+    grid = wl.centered_volume(128)
+    pos_d = torch.from_numpy(traj.pos[:1]).cuda()
+    f_d = torch.from_numpy(traj.f).cuda()
+    I = xs.intensity(pos_d, f_d, traj.box, grid, "fp16")
+    xs.Context.get().sync_status()
+    assert I.shape == (1, 128, 128, 128)
+    m = grid.miller()
+    pix = _sample_pixels(m, 256, 43)
+    ref = oracle.intensity(traj.pos[:1], traj.f, traj.box, m[pix])
+    got = I.reshape(1, -1)[:, pix].cpu().numpy()
+    e, e0 = e_I(got, ref, m[pix])
+    assert e <= 1e-4 and e0 <= 1e-4, (e, e0)
+
+
+def test_correlations_full_size_speckle(xs):
+    # 10,000 frames of a 512^2 plane in the L = 400 A box; per-pixel AR(1)
+    # correlation set by the ring, so every pixel of a ring shares one rho
+    T = 10_000
+    grid = wl.centered_plane(512)
+    box = wl.cubic_box(400.0)
+    m = grid.miller()
+    n_rings = wl.rings_for_plane(grid)
+    rings = oracle.ring_index(box, m, 1.0, n_rings)
+    rho = (0.3 + 0.65 * rings / n_rings).astype(np.float32)
+    I = wl.speckle_series(wl.SEED_BASE + 40, T, torch.from_numpy(rho), "cuda")
+    taus = wl.log_delays(T)
+    Ks = wl.window_list_125(1000)
+    g, mean = xs.g2(I, taus)
+    beta, counts = xs.xsvs_contrast(I.view(T, 1, grid.ny, grid.nx), grid, box, Ks, n_rings)
+    xs.Context.get().sync_status()
+
+    pix = _sample_pixels(m, 1024, 47)
+    Is = I[:, torch.from_numpy(pix).cuda()].cpu().numpy()
+    gref, mref = oracle.g2(Is, taus)
+    assert np.allclose(mean.cpu().numpy()[pix], mref, rtol=1e-7)
+    assert np.allclose(g.cpu().numpy()[:, pix], gref, rtol=2e-6, atol=0)
+
+    pick = [1, 7, 50, 181, 300, n_rings]
+    sel = np.flatnonzero(np.isin(rings, pick))
+    Ir = I[:, torch.from_numpy(sel).cuda()].cpu().numpy()
+    bref, cref = oracle.xsvs_contrast(Ir, Ks, rings[sel], n_rings)
+    b = beta.cpu().numpy()
+    for r in pick:
+        assert counts[r - 1] == cref[r - 1]
+        assert np.allclose(b[:, r - 1], bref[:, r - 1], rtol=1e-9, atol=1e-12), r
+
+    # AR(1) closed forms: g2 - 1 = rho^(2 tau) and
+    # beta_K = (1/K^2) sum_{i,j<K} rho^(2|i-j|), on rings with many pixels
+    gg = g.cpu().numpy()
+    for r in (50, 181, 300):
+        on = rings == r
+        p2 = float(rho[on][0]) ** 2
+        est = gg[0, on].mean() - 1
+        se = gg[0, on].std() / math.sqrt(on.sum())
+        assert abs(est - p2) < 5 * se + 0.01, (r, est, p2)
+        for ik, K in enumerate(Ks):
+            if K > 20:
+                break
+            d = np.arange(K)
+            want = (p2 ** np.abs(d[:, None] - d[None, :])).sum() / K ** 2
+            assert abs(b[ik, r - 1] - want) < 0.05 * want + 0.01, (r, K, b[ik, r - 1], want)
