@@ -32,6 +32,10 @@
 //     kept as error-free FP32 pairs (hi + lo, updated by TwoSum) in an
 //     L2-resident scratch block (one per CTA) and, after the last chunk of a
 //     tile, recombine the quadrants in FP64 into S and I = |S|^2.
+// On centred tiles (n_x, n_y in [-64, 64), n_z = 0) the tables use Friedel
+// symmetry of the factors, E(-n) = conj E(n) and w(-n) = conj w(n) for real
+// f: each CTA holds n in [32r, 32r + 32) and their negatives, builds 33 base
+// values per operand instead of 64 and stores each twice (see centred_index).
 // The atoms arrive in a coprime-stride permuted order (see the phase kernel),
 // so the partial sums over a chunk behave like random walks even for ordered
 // crystals and the FP32 accumulator never sums a coherent run of terms.
@@ -297,6 +301,24 @@ __device__ __forceinline__ uint32_t chunk_off(int mn, int k) {
            ((uint32_t)(((mn & 63) >> 3) ^ (k & 7)) << 4);
 }
 
+// Centred tiles (n in [-64, 64) on both axes, n_z = 0) use E(-n) = conj E(n)
+// and, with real f and E_z = 1, w(-n) = conj w(n).  CTA r holds the rows of
+// n in [32r, 32r + 32) and of their negatives, so it builds the 33 base values
+// X(32r + s), s = 0..32, of each operand and stores every one twice: slot s
+// (s < 32) holds X(32r + s) for n = 32r + s; slot 32 + s (s = 1..31) holds the
+// same X(32r + s) for n = -(32r + s), and slot 32 holds X(32r + 32) for
+// n = -(32r + 32).  The mirrored slots keep X itself, so their Im rows carry
+// the sign of conj; the epilogue applies it.
+__device__ __forceinline__ int centred_index(int slot, int r, float& sign) {
+    if (slot < 32) {
+        sign = 1.0f;
+        return 32 * r + slot + kHalf;
+    }
+    const int s = slot - 32;
+    sign = -1.0f;
+    return kHalf - 32 * r - (s == 0 ? 32 : s);
+}
+
 // one tile of one frame and plane, with what every role needs to work on it
 struct Unit {
     const uint4* rec;  // records of the unit's frame
@@ -305,6 +327,7 @@ struct Unit {
     int n_stages;
     int nx0, nx, ny0, ny, nz0, nz;
     int t, iz, tx, ty;
+    bool centred;  // tile n_x, n_y in [-64, 64) on the plane n_z = 0
 };
 
 __device__ __forceinline__ Unit make_unit(const TcTraj& tr, int t, int iz, int tx, int ty) {
@@ -323,6 +346,7 @@ __device__ __forceinline__ Unit make_unit(const TcTraj& tr, int t, int iz, int t
     u.iz = iz;
     u.tx = tx;
     u.ty = ty;
+    u.centred = tr.nx0 + tx * kTile == -kHalf && tr.ny0 + ty * kTile == -kHalf && tr.nz0 + iz == 0;
     return u;
 }
 
@@ -390,12 +414,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
 
     if (warp >= kMmaWarp + 1) {
         // ------------------------------------------------------------ producers
-        // warp w: atoms [32 (w & 1), +32) of the stage; w >> 1 = 0, 1: A rows for
-        // n_x run [32 (w>>1), +32) of this CTA's half, 2, 3: B rows for n_y
+        // warp w: atoms [32 (w & 1), +32) of the stage; w >> 1 = 0, 1: A rows
+        // (n_x), 2, 3: B rows (n_y)
         const int w = warp - (kMmaWarp + 1);
         const int ri = w >> 1;
         const bool is_a = ri < 2;
+        // general tiles: a run of 32 consecutive n of this CTA's half;
+        // centred tiles: base values X(32 rank + s), s in [s0, s0 + 16)
         const int run0 = kRun * (ri & 1);
+        const int s0 = (kRun / 2) * (ri & 1);
         const int k = 32 * (w & 1) + lane;
         const uint32_t full_c0 = map_to_rank(smem_u32(&ctl->full[0]), 0);
         int slot = 0;
@@ -411,8 +438,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
             if (has_next) up_next = get_unit(args, pair, n_pairs, ku + 1);
             const int n_st = up.n_stages;
             const uint4* rec_cur = up.rec + k;
-            const uint32_t n0 = is_a ? (uint32_t)(up.nx0 + up.tx * kTile + kHalf * (int)rank + run0)
-                                     : (uint32_t)(up.ny0 + up.ty * kTile + kHalf * (int)rank + run0);
+            const bool centred = up.centred;
+            const bool extra = centred && (ri & 1) == 0;  // also builds X(32 rank + 32)
+            const uint32_t n0 =
+                centred ? (uint32_t)(32 * (int)rank + s0)
+                        : (is_a ? (uint32_t)(up.nx0 + up.tx * kTile + kHalf * (int)rank + run0)
+                                : (uint32_t)(up.ny0 + up.ty * kTile + kHalf * (int)rank + run0));
             const uint32_t nz = (uint32_t)(up.nz0 + up.iz);
             for (int s = 0; s < n_st; ++s) {
                 const uint4 r = r_next;
@@ -427,6 +458,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                 const float2 NZI = make_float2(-z2.y, -z2.y);
                 float2 E0 = cis_turns(n0 * U, ctl->tab);
                 float2 E1 = cis_turns((n0 + 1u) * U, ctl->tab);
+                float2 Ex = make_float2(0.0f, 0.0f);
+                if (extra) Ex = cis_turns((uint32_t)(32 * (int)rank + 32) * U, ctl->tab);
                 if (!is_a) {
                     const float f = __uint_as_float(r.w);
                     float2 wv = make_float2(f, 0.0f);
@@ -436,6 +469,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                     }
                     E0 = cmul(E0, wv);
                     E1 = cmul(E1, wv);
+                    Ex = cmul(Ex, wv);
                 }
                 float2 R = make_float2(E0.x, E1.x);   // Re of (n, n+1)
                 float2 Im = make_float2(E0.y, E1.y);  // Im of (n, n+1)
@@ -446,21 +480,51 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                 const uint32_t sb = stage_base + (uint32_t)slot * kStageBytes;
                 const uint32_t hi_base = is_a ? sb : sb + 2 * kHalfBytes;
                 const uint32_t lo_base = hi_base + kHalfBytes;
+                if (centred) {
+                    uint32_t xh = 0u, xl = 0u;  // X(32 rank + 32) as packed (Re, Im)
+                    if (extra) split2<BF16>(Ex, xh, xl);
 #pragma unroll
-                for (int g = 0; g < kRun / 4; ++g) {
-                    // one 16-byte chunk = rows (Re n, Re n+1, Im n, Im n+1, Re n+2, Re n+3, Im n+2, Im n+3)
-                    uint32_t h[4], l[4];
+                    for (int g = 0; g < kRun / 8; ++g) {
+                        uint32_t h[4], l[4];
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        split2<BF16>(R, h[2 * q], l[2 * q]);
-                        split2<BF16>(Im, h[2 * q + 1], l[2 * q + 1]);
-                        const float2 Rn = __ffma2_rn(R, ZR, __fmul2_rn(Im, NZI));
-                        Im = __ffma2_rn(R, ZI, __fmul2_rn(Im, ZR));
-                        R = Rn;
+                        for (int q = 0; q < 2; ++q) {
+                            split2<BF16>(R, h[2 * q], l[2 * q]);
+                            split2<BF16>(Im, h[2 * q + 1], l[2 * q + 1]);
+                            const float2 Rn = __ffma2_rn(R, ZR, __fmul2_rn(Im, NZI));
+                            Im = __ffma2_rn(R, ZI, __fmul2_rn(Im, ZR));
+                            R = Rn;
+                        }
+                        const uint32_t off = chunk_off(2 * (s0 + 4 * g), k);
+                        st_shared_v4(hi_base + off, h[0], h[1], h[2], h[3]);
+                        st_shared_v4(lo_base + off, l[0], l[1], l[2], l[3]);
+                        if (g == 0 && extra) {
+                            // slot 32 takes X(32 rank + 32) in place of X(32 rank)
+                            h[0] = __byte_perm(xh, h[0], 0x7610);
+                            h[1] = __byte_perm(xh, h[1], 0x7632);
+                            l[0] = __byte_perm(xl, l[0], 0x7610);
+                            l[1] = __byte_perm(xl, l[1], 0x7632);
+                        }
+                        const uint32_t moff = chunk_off(2 * (32 + s0 + 4 * g), k);
+                        st_shared_v4(hi_base + moff, h[0], h[1], h[2], h[3]);
+                        st_shared_v4(lo_base + moff, l[0], l[1], l[2], l[3]);
                     }
-                    const uint32_t off = chunk_off(2 * (run0 + 4 * g), k);
-                    st_shared_v4(hi_base + off, h[0], h[1], h[2], h[3]);
-                    st_shared_v4(lo_base + off, l[0], l[1], l[2], l[3]);
+                } else {
+#pragma unroll
+                    for (int g = 0; g < kRun / 4; ++g) {
+                        // one 16-byte chunk = rows (Re n, Re n+1, Im n, Im n+1, Re n+2, Re n+3, Im n+2, Im n+3)
+                        uint32_t h[4], l[4];
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            split2<BF16>(R, h[2 * q], l[2 * q]);
+                            split2<BF16>(Im, h[2 * q + 1], l[2 * q + 1]);
+                            const float2 Rn = __ffma2_rn(R, ZR, __fmul2_rn(Im, NZI));
+                            Im = __ffma2_rn(R, ZI, __fmul2_rn(Im, ZR));
+                            R = Rn;
+                        }
+                        const uint32_t off = chunk_off(2 * (run0 + 4 * g), k);
+                        st_shared_v4(hi_base + off, h[0], h[1], h[2], h[3]);
+                        st_shared_v4(lo_base + off, l[0], l[1], l[2], l[3]);
+                    }
                 }
                 fence_async_shared();
                 __syncwarp();
@@ -541,7 +605,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
         const int row = warp * 32 + lane;
         const bool re_row = (lane & 2) == 0;
-        const int xi = kHalf * (int)rank + 2 * (row >> 2) + (row & 1);
+        const int x_slot = 2 * (row >> 2) + (row & 1);
+        float sx_c;
+        const int xi_c = centred_index(x_slot, (int)rank, sx_c);
         float2* scr = reinterpret_cast<float2*>(args.scratch) + (size_t)blockIdx.x * 256 * 128 + row;
         const uint32_t acc_empty_c0 = map_to_rank(smem_u32(&ctl->acc_empty[0]), 0);
         int64_t a_cnt = 0;
@@ -549,6 +615,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
         for (int64_t ku = 0; ku < my_units && ok; ++ku) {
             const Unit up = get_unit(args, pair, n_pairs, ku);
             const int n_chunks = (up.n_stages + args.chunk_stages - 1) / args.chunk_stages;
+            const bool centred = up.centred;
+            const int xi = centred ? xi_c : kHalf * (int)rank + x_slot;
+            const double sx = centred ? (double)sx_c : 1.0;  // sign of the stored Im x rows
             for (int c = 0; c < n_chunks; ++c, ++a_cnt) {
                 const int b = (int)(a_cnt & 1);
                 const uint32_t use = (uint32_t)(a_cnt >> 1);
@@ -614,10 +683,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                                 const double* vi = re_row ? rcv : own;  // D[Im x][...]
                                 const double p_rr = vr[4 * hh + t], p_ri = vr[4 * hh + 2 + t];
                                 const double p_ir = vi[4 * hh + t], p_ii = vi[4 * hh + 2 + t];
-                                const double sre = p_rr - p_ii;
-                                const double sim = p_ri + p_ir;
                                 const int m = 8 * j + (re_row ? 0 : 4) + 2 * hh + t;
-                                const int iy = up.ty * kTile + m;
+                                int yi = m;
+                                double sy = 1.0;  // sign of the stored Im y rows
+                                if (centred) {
+                                    float f;
+                                    yi = centred_index(m & (kHalf - 1), m / kHalf, f);
+                                    sy = (double)f;
+                                }
+                                const double sre = p_rr - sx * sy * p_ii;
+                                const double sim = sy * p_ri + sx * p_ir;
+                                const int iy = up.ty * kTile + yi;
                                 if (iy < up.ny) {
                                     const int64_t o = (((int64_t)up.t * up.nz + up.iz) * up.ny + iy) * up.nx + ix;
                                     up.I[o] = (float)(sre * sre + sim * sim);
