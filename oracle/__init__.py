@@ -13,6 +13,10 @@ What each function follows (arXiv 2204.13241):
                           Sec. 2.3 Eqs. inte_Iq and bq_Iq (finite-exposure
                           intensity as a sum of K frames, optical contrast
                           over a |q| ring), averaged over exposures (Sec. 4.3).
+  isf, contrast_from_isf  Sec. 2.3 Eqs. Fq_pq and norm_Fq (intermediate
+                          scattering function from the amplitudes) and Eq.
+                          beta_alt_int (contrast predicted through the
+                          Siegert relation, in its K-frame form).
   grad_analytic           derivative of I = |S|^2 with respect to the atomic
                           positions (the adjoint of Eq. pe_ri).
   grad_fd                 central finite differences of a caller loss, with an
@@ -199,6 +203,61 @@ def xsvs_contrast(I: np.ndarray, Ks: Sequence[int], rings: np.ndarray, n_rings: 
             with np.errstate(divide="ignore", invalid="ignore"):
                 beta_w = (m2 - m1 * m1) / (m1 * m1)
             out[ik, r - 1] = beta_w.sum() / W
+    return out, counts
+
+
+# ----------------------------------------------------------------------------
+# intermediate scattering function and the contrast it predicts
+# ----------------------------------------------------------------------------
+
+def isf(S: np.ndarray, taus: Sequence[int], sum_f2: float) -> tuple[np.ndarray, np.ndarray]:
+    """F(q,tau) and F_hat(q,tau), complex128 [n_tau][P] each.
+
+    F = <p(t) p*(t+tau)>_t / sum_j f_j^2 (Sec. 2.3 Eq. Fq_pq) with p the
+    conjugate of S, so the product is conj(S(t)) S(t+tau), averaged over the
+    T - tau available t; F_hat = F / F(q,0) (Eq. norm_Fq) with F(q,0) the mean
+    of |S|^2 over all T frames divided by sum_j f_j^2."""
+    x = np.asarray(S, dtype=np.complex128)
+    T = x.shape[0]
+    F0 = (x.real ** 2 + x.imag ** 2).sum(axis=0) / T / float(sum_f2)
+    F = np.empty((len(taus),) + x.shape[1:], dtype=np.complex128)
+    for k, tau in enumerate(taus):
+        tau = int(tau)
+        if tau < 0 or tau >= T:
+            raise ValueError("delay out of range")
+        F[k] = (np.conj(x[: T - tau]) * x[tau:]).sum(axis=0) / (T - tau) / float(sum_f2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        Fhat = F / F0
+    return F, Fhat
+
+
+def contrast_from_isf(Fhat_dense: np.ndarray, Ks: Sequence[int], rings: np.ndarray, n_rings: int
+                      ) -> tuple[np.ndarray, np.ndarray]:
+    """beta_K / beta_0 per ring predicted from |F_hat|^2 through the Siegert
+    relation (Sec. 2.3 Eq. beta_alt_int), float64 [n_K][n_rings], and pixels
+    per ring.
+
+    Fhat_dense [Kmax][P] holds the delays 0 .. Kmax-1.  For an exposure that
+    sums K frames the integral over the exposure becomes the double sum
+    (1/K^2) sum_{i,j<K} |F_hat(|i-j|)|^2, with |F_hat(0)|^2 = 1 by definition;
+    it is evaluated per pixel and averaged over the ring's pixels."""
+    a = np.abs(np.asarray(Fhat_dense, dtype=np.complex128)) ** 2
+    rings = np.asarray(rings).reshape(-1)
+    counts = np.array([(rings == r).sum() for r in range(1, n_rings + 1)], dtype=np.int64)
+    out = np.full((len(Ks), n_rings), np.nan, dtype=np.float64)
+    for ik, K in enumerate(Ks):
+        K = int(K)
+        if K < 1 or K > a.shape[0]:
+            raise ValueError("window length out of range")
+        # (i, j) pairs with |i - j| = d: K for d = 0, 2 (K - d) for d >= 1
+        per_pixel = np.full(a.shape[1:], float(K), dtype=np.float64)
+        for d in range(1, K):
+            per_pixel += 2.0 * (K - d) * a[d]
+        per_pixel /= K * K
+        for r in range(1, n_rings + 1):
+            sel = rings == r
+            if sel.any():
+                out[ik, r - 1] = per_pixel[sel].mean()
     return out, counts
 
 
