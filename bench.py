@@ -38,10 +38,10 @@ FALLBACK_PEAK = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gb
 
 # DRAM bytes (read + write) of one tc_kernel launch per frame of the 256,000-atom
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
-# of a 160-frame launch of this exact kernel source: 656.05 MB + 12.98 MB.
+# of a 160-frame launch of this exact kernel source: 656.25 MB + 11.98 MB.
 # The records streamed are proportional to the frames, so a launch over T
 # frames moves T times this.  Reported only while k_tc.cu is unchanged.
-TC_TRAFFIC = {"k_tc_sha256_prefix": "c382ee4acc296ffe", "bytes_per_frame": (656.046848e6 + 12.983296e6) / 160}
+TC_TRAFFIC = {"k_tc_sha256_prefix": "22ff0289144ae001", "bytes_per_frame": (656.251904e6 + 11.979264e6) / 160}
 
 
 def _args():

@@ -24,6 +24,9 @@
 //     exp(i 2 pi n0 U) and exp(i 2 pi (n0+1) U) (U = 32-bit turn count, n U mod
 //     2^32 is exact) and advances by the exact step exp(i 2 pi 2U).  Each value
 //     c is split into hi = RN(c) and lo = RN(c - hi) (FP16 or BF16).
+//   * Producer warps arrive on a barrier of their own CTA (CTA-scope
+//     release); in CTA 1 one relay thread forwards each filled stage to CTA 0
+//     with a single cluster-scope release.
 //   * 1 thread of CTA 0 issues tcgen05.mma (hi*hi + hi*lo + lo*hi, FP32
 //     accumulate) into one of two TMEM accumulators; after `chunk_stages`
 //     stages it hands the accumulator to the epilogues and continues in the
@@ -73,7 +76,8 @@ constexpr uint32_t kTmemCols = 512;                    // two 256-column FP32 ac
 constexpr int kTabSize = 256;
 
 struct SmemCtl {
-    uint64_t full[kStages];   // CTA 0: producer warps of both CTAs
+    uint64_t full[kStages];   // CTA 0: its producer warps and the peer's relay
+    uint64_t fill[kStages];   // CTA 1: its producer warps (forwarded by the relay)
     uint64_t empty[kStages];  // each CTA: MMA commits
     uint64_t acc_full[2];     // each CTA: MMA commits
     uint64_t acc_empty[2];    // CTA 0: epilogue warps of both CTAs
@@ -393,7 +397,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
     }
     if (threadIdx.x == kMmaWarp * 32) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&ctl->full[s], 2 * kProdWarps);
+            mbar_init(&ctl->full[s], kProdWarps + 1);
+            mbar_init(&ctl->fill[s], kProdWarps);
             mbar_init(&ctl->empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -424,7 +429,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
         const int run0 = kRun * (ri & 1);
         const int s0 = (kRun / 2) * (ri & 1);
         const int k = 32 * (w & 1) + lane;
-        const uint32_t full_c0 = map_to_rank(smem_u32(&ctl->full[0]), 0);
         int slot = 0;
         uint32_t phase = 0;  // parity of the current pass over the ring of stages
         Unit up{};
@@ -529,12 +533,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                 fence_async_shared();
                 __syncwarp();
                 if (lane == 0) {
-                    // CTA 0's tables are read by its own MMAs: CTA-scope release is
-                    // enough; the peer's tables cross the pair and need cluster scope
-                    if (rank == 0)
-                        mbar_arrive_local(&ctl->full[slot]);
-                    else
-                        mbar_arrive_cluster(full_c0 + (uint32_t)slot * 8u);
+                    // CTA-scope release on a barrier of this CTA; in CTA 1 the relay
+                    // thread forwards the completed stage to CTA 0 at cluster scope,
+                    // once per stage instead of once per producer warp
+                    mbar_arrive_local(rank == 0 ? &ctl->full[slot] : &ctl->fill[slot]);
                 }
                 if (++slot == kStages) {
                     slot = 0;
@@ -597,6 +599,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
             umma_commit_pair(&ctl->drain, 0x1);
             int no_abort = 0;
             wait_bar(&ctl->drain, 0u, &no_abort, args.err, 2000000000LL, 20000u);
+        } else if (rank == 1 && lane == 0) {
+            // relay: when this CTA's producers have filled a stage (acquired at
+            // CTA scope), arrive on CTA 0's full barrier with a cluster-scope
+            // release, which carries their stores to the pair's MMAs
+            const uint32_t full_c0 = map_to_rank(smem_u32(&ctl->full[0]), 0);
+            int slot = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int64_t ku = 0; ku < my_units && ok; ++ku) {
+                const int n_stages = get_unit(args, pair, n_pairs, ku).n_stages;
+                for (int s = 0; s < n_stages; ++s) {
+                    if (!wait_bar(&ctl->fill[slot], phase, abort_flag, args.err, args.timeout_ns, 20000u)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_cluster(full_c0 + (uint32_t)slot * 8u);
+                    if (++slot == kStages) {
+                        slot = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
         }
         __syncwarp();
     } else {
