@@ -132,6 +132,26 @@ XS_API xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, cons
                                void* cuda_stream);
 
 /*
+ * Intensity with q-dependent form factors of several atom species (Sec. 2.1:
+ * f_i(q), each species' form factor a sum of Gaussians in |q|):
+ *   S(q,t) = sum_j f_j F_{s_j}(q) exp(+i q.r_j(t)),   I = |S|^2,
+ *   F_s(q) = sum_{k<4} a_k exp(-b_k (|q|/4 pi)^2) + c,
+ * with f_j = traj->f[j] a per-atom weight (1 for plain species; 0 drops an
+ * atom, as for tracer labelling).  Each species runs through the phase and
+ * contraction kernels of xs_intensity on its own atoms; the per-species
+ * amplitudes are combined in FP64.
+ *   traj      device positions (pos_on_host = 0) and device weights f [N]
+ *   species   HOST int32 [N], values in [0, n_species)
+ *   coef      HOST float64 [n_species][9] = (a1, b1, a2, b2, a3, b3, a4, b4, c),
+ *             b in A^2 (|q| in 1/A)
+ *   I_out     device float32 [T][nz][ny][nx]; amp_out device float32 [...][2] or NULL
+ * Uses context workspace for one species' records and three per-frame buffers.
+ */
+XS_API xs_status xs_intensity_species(xs_context* ctx, const xs_traj* traj, const int32_t* species,
+                                      int32_t n_species, const double* coef, const xs_qgrid* grid,
+                                      xs_precision prec, float* I_out, float* amp_out, void* cuda_stream);
+
+/*
  * XPCS autocorrelation, Sec. 2.3 Eq. g2_def, per pixel:
  *   mean(p) = (1/T) sum_{t<T} I(t,p)
  *   g2(tau,p) = [(1/(T-tau)) sum_{t<T-tau} I(t,p) I(t+tau,p)] / mean(p)^2
@@ -160,6 +180,41 @@ XS_API xs_status xs_xsvs_contrast(xs_context* ctx, const float* I, int64_t T, co
                            const xs_box* box, const int32_t* Ks, int32_t n_K, double ring_width,
                            int32_t n_rings, double* beta_out, int32_t* ring_count_out,
                            void* cuda_stream);
+
+/*
+ * Intermediate scattering function from the amplitudes, Sec. 2.3 Eqs. Fq_pq
+ * and norm_Fq.  The paper's p^e is the conjugate of the amplitude S returned
+ * by xs_intensity, so
+ *   F(tau,p)    = [(1/(T-tau)) sum_{t<T-tau} conj(S(t,p)) S(t+tau,p)] / sum_f2
+ *   F_hat(tau,p) = F(tau,p) / F(0,p),  F(0,p) = [(1/T) sum_{t<T} |S(t,p)|^2] / sum_f2
+ *   amp       device float32 [T][P][2] (re, im), as written by xs_intensity
+ *   taus      HOST int32 [n_tau], each 0 <= tau < T
+ *   sum_f2    sum_j f_j^2 of the atoms (> 0)
+ *   F_out     device float64 [n_tau][P][2]
+ *   Fhat_out  device float64 [n_tau][P][2], or NULL; NaN where F(0,p) == 0
+ */
+XS_API xs_status xs_isf(xs_context* ctx, const float* amp, int64_t T, int64_t P, const int32_t* taus,
+                        int32_t n_tau, double sum_f2, double* F_out, double* Fhat_out, void* cuda_stream);
+
+/*
+ * Contrast predicted from F_hat through the Siegert relation, Sec. 2.3 Eq.
+ * beta_alt_int, in the form that matches exposures summing K frames (as in
+ * xs_xsvs_contrast):
+ *   ratio_K(r) = mean over the pixels p of ring r of
+ *                (1/K^2) sum_{i,j<K} |F_hat(|i-j|,p)|^2,   |F_hat(0,p)|^2 = 1,
+ * i.e. beta_K(r) / beta_0(r).  Rings as in xs_xsvs_contrast.
+ *   Fhat           device float64 [Kmax][P][2] for the delays 0..Kmax-1 (row 0
+ *                  is not read)
+ *   Ks             HOST int32 [n_K], 1 <= K <= Kmax, any order (NULL if n_K == 0)
+ *   ratio_out      device float64 [n_K][n_rings]; NaN for an empty ring (NULL
+ *                  allowed when n_K or n_rings is 0)
+ *   ring_count_out HOST int32 [n_rings] pixels per ring, or NULL
+ * Uses n_K * (pixels in rings) float64 of context workspace.
+ */
+XS_API xs_status xs_contrast_from_isf(xs_context* ctx, const double* Fhat, int64_t Kmax, const xs_qgrid* grid,
+                                      const xs_box* box, const int32_t* Ks, int32_t n_K, double ring_width,
+                                      int32_t n_rings, double* ratio_out, int32_t* ring_count_out,
+                                      void* cuda_stream);
 
 /*
  * Host-side helper (no GPU work): the ring of every pixel of `grid` as used by

@@ -8,6 +8,9 @@ stages are written out below in numpy float64.
 What each function follows (arXiv 2204.13241):
   amplitude / intensity   Sec. 2.2 Eqs. pe_ri, Iq_pq; Sec. 3.1 Eq.
                           sq_cut_simple and Algorithm 1 (direct method).
+  form_factor, amplitude_species, intensity_species
+                          Sec. 2.1: per-atom form factors f_i(q), each a sum
+                          of Gaussians in |q| for its species.
   g2                      Sec. 2.3 Eq. g2_def (XPCS autocorrelation).
   ring_index, xsvs_contrast
                           Sec. 2.3 Eqs. inte_Iq and bq_Iq (finite-exposure
@@ -128,6 +131,46 @@ def amplitude(pos: np.ndarray, f: np.ndarray, box: np.ndarray, miller: np.ndarra
 def intensity(pos, f, box, miller, threads: int = 0) -> np.ndarray:
     """I(q,t) = |S(q,t)|^2, float64 [T][P]."""
     s = amplitude(pos, f, box, miller, threads)
+    return s.real ** 2 + s.imag ** 2
+
+
+# ----------------------------------------------------------------------------
+# q-dependent form factors of several atom species
+# ----------------------------------------------------------------------------
+
+def form_factor(coef: np.ndarray, qnorm: np.ndarray) -> np.ndarray:
+    """f(q) as a sum of Gaussians (Sec. 2.1): with s = |q| / (4 pi),
+    f = sum_{k<4} a_k exp(-b_k s^2) + c, coef = (a1, b1, a2, b2, a3, b3, a4, b4, c).
+    Returns float64 shaped like qnorm."""
+    c = np.asarray(coef, dtype=np.float64).reshape(9)
+    s2 = (np.asarray(qnorm, dtype=np.float64) / (4.0 * math.pi)) ** 2
+    out = np.full(s2.shape, c[8])
+    for k in range(4):
+        out = out + c[2 * k] * np.exp(-c[2 * k + 1] * s2)
+    return out
+
+
+def amplitude_species(pos, f, species, coef, box, miller, threads: int = 0) -> np.ndarray:
+    """S(q,t) = sum_j f_j F_{s_j}(q) exp(+i q.r_j(t)) (Sec. 2.1 with per-atom
+    form factors f_i(q)); f_j is a per-atom weight, F_s the Gaussian-sum form
+    factor of species s (`coef` [n_species][9]).  The sum is grouped by
+    species: each group is the plain direct sum of its atoms, scaled by its
+    F_s(q).  complex128 [T][P]."""
+    sp = np.asarray(species).reshape(-1)
+    cf = np.asarray(coef, dtype=np.float64).reshape(-1, 9)
+    fw = np.asarray(f, dtype=np.float64).reshape(-1)
+    qn = np.sqrt((qvectors(box, miller) ** 2).sum(axis=1))
+    total = None
+    for s_id in range(cf.shape[0]):
+        part = amplitude(pos, np.where(sp == s_id, fw, 0.0), box, miller, threads)
+        part = part * form_factor(cf[s_id], qn)[None, :]
+        total = part if total is None else total + part
+    return total
+
+
+def intensity_species(pos, f, species, coef, box, miller, threads: int = 0) -> np.ndarray:
+    """|S|^2 of :func:`amplitude_species`, float64 [T][P]."""
+    s = amplitude_species(pos, f, species, coef, box, miller, threads)
     return s.real ** 2 + s.imag ** 2
 
 

@@ -154,6 +154,29 @@ def intensity(pos: torch.Tensor, f: torch.Tensor, box, grid, precision: str = "f
     return (out, amp_out) if want_amp else out
 
 
+def intensity_species(pos: torch.Tensor, f: torch.Tensor, species, coef, box, grid, precision: str = "fp16",
+                      want_amp: bool = False):
+    """I(q,t) with q-dependent form factors per species (Sec. 2.1):
+    S = sum_j f_j F_{s_j}(q) exp(i q.r_j); `species` int [N] (host), `coef`
+    float64 [n_species][9] Gaussian-sum coefficients (a1, b1, .., a4, b4, c)."""
+    tr, host = _traj(pos, f, box)
+    if host:
+        raise ValueError("the species path takes device positions")
+    sp = np.ascontiguousarray(np.asarray(species, dtype=np.int32).reshape(-1))
+    cf = np.ascontiguousarray(np.asarray(coef, dtype=np.float64).reshape(-1, 9))
+    if sp.size != tr.n_atoms:
+        raise ValueError("one species per atom")
+    g = _grid(grid)
+    shape = (int(tr.n_frames), g.nz, g.ny, g.nx)
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    amp = torch.empty(shape + (2,), dtype=torch.float32, device="cuda") if want_amp else None
+    ctx = Context.get()
+    nat.check(ctx.lib.xs_intensity_species(ctx.handle, ctypes.byref(tr), sp.ctypes.data_as(ctypes.c_void_p),
+                                           cf.shape[0], cf.ctypes.data_as(ctypes.c_void_p), ctypes.byref(g),
+                                           nat.PRECISIONS[precision], out.data_ptr(), _ptr(amp), _stream()))
+    return (out, amp) if want_amp else out
+
+
 def intensity_batched(trajs: Sequence[tuple], grids: Sequence, precision: str = "bf16",
                       outs: Optional[Sequence[torch.Tensor]] = None):
     """Many trajectories (pos, f, box) on their own grids in one call."""
@@ -213,6 +236,44 @@ def xsvs_contrast(I: torch.Tensor, grid, box, Ks: Sequence[int], n_rings: int, r
                                        k.ctypes.data_as(ctypes.c_void_p), k.size, float(ring_width), int(n_rings),
                                        beta.data_ptr(), counts.ctypes.data_as(ctypes.c_void_p), _stream()))
     return beta, counts
+
+
+def isf(amp: torch.Tensor, taus: Sequence[int], sum_f2: float, want_hat: bool = True):
+    """Intermediate scattering function (Sec. 2.3 Eqs. Fq_pq, norm_Fq) of the
+    amplitudes amp [T][...][2] written by `intensity(..., want_amp=True)`;
+    returns (F, F_hat) as complex128 [n_tau][P] (F_hat None unless want_hat)."""
+    _need(amp, "amp")
+    if amp.shape[-1] != 2:
+        raise ValueError("amp must end in a (re, im) axis of 2")
+    T = amp.shape[0]
+    P = amp.numel() // max(2 * T, 1)
+    t = np.ascontiguousarray(np.asarray(taus, dtype=np.int32))
+    F = torch.empty((t.size, P, 2), dtype=torch.float64, device=amp.device)
+    Fh = torch.empty((t.size, P, 2), dtype=torch.float64, device=amp.device) if want_hat else None
+    ctx = Context.get()
+    nat.check(ctx.lib.xs_isf(ctx.handle, amp.data_ptr(), T, P, t.ctypes.data_as(ctypes.c_void_p), t.size,
+                             float(sum_f2), F.data_ptr(), _ptr(Fh), _stream()))
+    F = torch.view_as_complex(F)
+    return F, (torch.view_as_complex(Fh) if want_hat else None)
+
+
+def contrast_from_isf(Fhat: torch.Tensor, grid, box, Ks: Sequence[int], n_rings: int, ring_width: float = 1.0):
+    """beta_K / beta_0 per ring predicted from F_hat (Sec. 2.3 Eq. beta_alt_int,
+    K-frame form); Fhat complex128 [Kmax][P] on the delays 0..Kmax-1.
+    Returns (ratio float64 [n_K][n_rings], pixels per ring int32 [n_rings])."""
+    if Fhat.dtype != torch.complex128 or not Fhat.is_cuda or not Fhat.is_contiguous():
+        raise ValueError("Fhat must be a contiguous complex128 CUDA tensor")
+    g = _grid(grid)
+    b = _box(box)
+    k = np.ascontiguousarray(np.asarray(Ks, dtype=np.int32))
+    out = torch.empty((k.size, n_rings), dtype=torch.float64, device=Fhat.device)
+    counts = np.zeros(n_rings, dtype=np.int32)
+    ctx = Context.get()
+    nat.check(ctx.lib.xs_contrast_from_isf(ctx.handle, Fhat.data_ptr(), Fhat.shape[0], ctypes.byref(g),
+                                           ctypes.byref(b), k.ctypes.data_as(ctypes.c_void_p), k.size,
+                                           float(ring_width), int(n_rings), out.data_ptr(),
+                                           counts.ctypes.data_as(ctypes.c_void_p), _stream()))
+    return out, counts
 
 
 def ring_index(grid, box, ring_width: float, n_rings: int) -> np.ndarray:

@@ -13,6 +13,17 @@
 //                   x = C[(w+1)K][p'] - C[wK][p'] (one warp per (K,w))
 //   finalize_kernel per (K, ring): ring sums over the ring's chunks in a fixed
 //                   order, beta per window, mean over windows.
+//
+// Intermediate scattering function on the amplitude series S[t][p] (Sec. 2.3,
+// Eqs. Fq_pq, norm_Fq) and the contrast it predicts (Eq. beta_alt_int):
+//   isf_kernel      like g2_kernel with complex products conj(S(t)) S(t+tau)
+//                   (compensated FP32 over 64-frame blocks, FP64 block sums),
+//                   F = mean / sum f^2 and F_hat = F / F(q,0)
+//   isf_contrast_kernel per in-ring pixel, one pass over the delays d:
+//                   (1/K^2) [K + 2 (K sum_{d<K} |F_hat|^2 - sum_{d<K} d |F_hat|^2)]
+//   ring_mean_kernel per (K, ring), fixed-order mean over the ring's pixels.
+#include <algorithm>
+
 #include "xs_internal.h"
 
 namespace xs {
@@ -73,6 +84,116 @@ g2_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __re
     }
 }
 
+constexpr int kIsfGroup = 8;
+
+__global__ void __launch_bounds__(kG2Threads)
+isf_kernel(const float2* __restrict__ S, int64_t T, int64_t P, const int32_t* __restrict__ taus, int n_tau,
+           double inv_sum_f2, double2* __restrict__ F, double2* __restrict__ Fhat) {
+    __shared__ int s_tau[kIsfGroup];
+    const int g0 = blockIdx.y * kIsfGroup;
+    const int nt = min(kIsfGroup, n_tau - g0);
+    if (threadIdx.x < kIsfGroup) s_tau[threadIdx.x] = threadIdx.x < nt ? taus[g0 + threadIdx.x] : 0;
+    __syncthreads();
+    const int64_t p = blockIdx.x * (int64_t)kG2Threads + threadIdx.x;
+    if (p >= P) return;
+    int tau[kIsfGroup];
+#pragma unroll
+    for (int k = 0; k < kIsfGroup; ++k) tau[k] = s_tau[k];
+    float are[kIsfGroup], cre[kIsfGroup], aim[kIsfGroup], cim[kIsfGroup];
+    double dre[kIsfGroup], dim[kIsfGroup];
+#pragma unroll
+    for (int k = 0; k < kIsfGroup; ++k) {
+        are[k] = cre[k] = aim[k] = cim[k] = 0.0f;
+        dre[k] = dim[k] = 0.0;
+    }
+    double dmean = 0.0;
+    for (int64_t t0 = 0; t0 < T; t0 += kFlush) {
+        const int64_t t1 = min(T, t0 + kFlush);
+        for (int64_t t = t0; t < t1; ++t) {
+            const float2 a = S[t * P + p];
+            dmean = fma((double)a.x, (double)a.x, fma((double)a.y, (double)a.y, dmean));
+#pragma unroll
+            for (int k = 0; k < kIsfGroup; ++k) {
+                if (k < nt && t + tau[k] < T) {
+                    const float2 b = S[(t + tau[k]) * P + p];
+                    // conj(a) b = (a.x b.x + a.y b.y) + i (a.x b.y - a.y b.x)
+                    const float yr = fmaf(a.x, b.x, fmaf(a.y, b.y, -cre[k]));
+                    const float sr = are[k] + yr;
+                    cre[k] = (sr - are[k]) - yr;
+                    are[k] = sr;
+                    const float yi = fmaf(a.x, b.y, fmaf(-a.y, b.x, -cim[k]));
+                    const float si = aim[k] + yi;
+                    cim[k] = (si - aim[k]) - yi;
+                    aim[k] = si;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kIsfGroup; ++k) {
+            dre[k] += (double)are[k] - (double)cre[k];
+            dim[k] += (double)aim[k] - (double)cim[k];
+            are[k] = cre[k] = aim[k] = cim[k] = 0.0f;
+        }
+    }
+    const double m = dmean / (double)T;  // F(q,0) sum f^2
+#pragma unroll
+    for (int k = 0; k < kIsfGroup; ++k) {
+        if (k < nt) {
+            const double n = (double)(T - tau[k]);
+            const double re = dre[k] / n, im = dim[k] / n;
+            const int64_t o = (int64_t)(g0 + k) * P + p;
+            F[o] = make_double2(re * inv_sum_f2, im * inv_sum_f2);
+            if (Fhat) Fhat[o] = make_double2(re / m, im / m);
+        }
+    }
+}
+
+// one thread per in-ring pixel (ring-major order); Ks sorted ascending, row
+// k_row[i] of the output receives K = Ks[i]
+__global__ void isf_contrast_kernel(const double2* __restrict__ Fhat, int64_t Kmax, int64_t P,
+                                    const int32_t* __restrict__ perm, int64_t n_in,
+                                    const int32_t* __restrict__ Ks, const int32_t* __restrict__ k_row, int n_K,
+                                    double* __restrict__ b) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n_in) return;
+    const int64_t p = perm[q];
+    double A = 0.0, B = 0.0;  // sums over d in [1, K) of |F_hat(d)|^2 and d |F_hat(d)|^2
+    int i = 0;
+    for (int64_t d = 1; d <= Kmax && i < n_K; ++d) {
+        while (i < n_K && Ks[i] == d) {
+            const double K = (double)d;
+            b[(int64_t)k_row[i] * n_in + q] = (K + 2.0 * (K * A - B)) / (K * K);
+            ++i;
+        }
+        if (d == Kmax) break;
+        const double2 z = Fhat[d * P + p];
+        const double a = fma(z.x, z.x, z.y * z.y);
+        A += a;
+        B = fma((double)d, a, B);
+    }
+}
+
+// one warp per (K, ring): mean of b over the ring's pixels, fixed order
+__global__ void ring_mean_kernel(const double* __restrict__ b, int64_t n_in, const int64_t* __restrict__ ring_start,
+                                 int n_rings, int n_K, double* __restrict__ out) {
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= (int64_t)n_K * n_rings) return;
+    const int ik = (int)(i / n_rings);
+    const int r = (int)(i - (int64_t)ik * n_rings);
+    const int64_t a0 = ring_start[r], a1 = ring_start[r + 1];
+    if (a1 == a0) {
+        if (lane == 0) out[i] = __longlong_as_double(0x7ff8000000000000ll);  // NaN
+        return;
+    }
+    const double* row = b + (int64_t)ik * n_in;
+    double acc = 0.0;
+    for (int64_t a = a0 + lane; a < a1; a += 32) acc += row[a];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[i] = acc / (double)(a1 - a0);
+}
+
 __global__ void prefix_kernel(const float* __restrict__ I, int64_t T, int64_t P,
                               const int32_t* __restrict__ perm, int64_t n_in, double* __restrict__ C) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -86,16 +207,19 @@ __global__ void prefix_kernel(const float* __restrict__ I, int64_t T, int64_t P,
     }
 }
 
-// block = one chunk (ring, start, count); warps stride over the (K,w) list
+// block = one chunk (ring, start, count) and a slice of `kw_slice` entries of
+// the (K,w) list; its warps stride over the slice
 __global__ void window_kernel(const double* __restrict__ C, int64_t n_in, const int4* __restrict__ chunks,
                               int n_chunks, const int32_t* __restrict__ Ks, const int64_t* __restrict__ kw_off,
-                              int n_K, int64_t n_kw, double2* __restrict__ partial) {
+                              int n_K, int64_t n_kw, int64_t kw_slice, double2* __restrict__ partial) {
     const int4 ch = chunks[blockIdx.x];  // (ring, start, count, 0)
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
+    const int64_t kw0 = (int64_t)blockIdx.y * kw_slice;
+    const int64_t kw1 = min(n_kw, kw0 + kw_slice);
     int ik = 0;
-    for (int64_t kw = warp; kw < n_kw; kw += nwarps) {
+    for (int64_t kw = kw0 + warp; kw < kw1; kw += nwarps) {
         while (ik + 1 < n_K && kw >= kw_off[ik + 1]) ++ik;
         while (ik > 0 && kw < kw_off[ik]) --ik;
         const int64_t K = Ks[ik];
@@ -164,6 +288,34 @@ cudaError_t launch_g2(const float* I, int64_t T, int64_t P, const int32_t* d_tau
     return cudaGetLastError();
 }
 
+cudaError_t launch_isf(const float* amp, int64_t T, int64_t P, const int32_t* d_taus, int n_tau, double inv_sum_f2,
+                       double* F, double* Fhat, cudaStream_t st) {
+    if (P == 0 || n_tau == 0) return cudaSuccess;
+    dim3 grid((unsigned)((P + kG2Threads - 1) / kG2Threads), (unsigned)((n_tau + kIsfGroup - 1) / kIsfGroup));
+    ++tl_kernel_launches;
+    isf_kernel<<<grid, kG2Threads, 0, st>>>(reinterpret_cast<const float2*>(amp), T, P, d_taus, n_tau, inv_sum_f2,
+                                            reinterpret_cast<double2*>(F), reinterpret_cast<double2*>(Fhat));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_isf_contrast(const double* Fhat, int64_t Kmax, int64_t P, const int32_t* d_perm, int64_t n_in,
+                                const int32_t* d_K_sorted, const int32_t* d_k_row, int n_K,
+                                const int64_t* d_ring_start, int n_rings, double* b_pixel, double* out,
+                                cudaStream_t st) {
+    if (n_in > 0) {
+        ++tl_kernel_launches;
+        isf_contrast_kernel<<<(unsigned)((n_in + 127) / 128), 128, 0, st>>>(
+            reinterpret_cast<const double2*>(Fhat), Kmax, P, d_perm, n_in, d_K_sorted, d_k_row, n_K, b_pixel);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t items = (int64_t)n_K * n_rings;
+    ++tl_kernel_launches;
+    ring_mean_kernel<<<(unsigned)((items * 32 + 127) / 128), 128, 0, st>>>(b_pixel, n_in, d_ring_start, n_rings,
+                                                                         n_K, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_xsvs(const float* I, int64_t T, int64_t P, const int32_t* d_perm,
                         const int4* d_chunks, int n_chunks, int64_t n_in_rings,
                         const int32_t* d_K, const int64_t* d_kw_off, int n_K, int64_t n_kw,
@@ -175,9 +327,13 @@ cudaError_t launch_xsvs(const float* I, int64_t T, int64_t P, const int32_t* d_p
         prefix_kernel<<<(unsigned)((n_in_rings + 127) / 128), 128, 0, st>>>(I, T, P, d_perm, n_in_rings, prefix);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        // slices of the (K,w) list give enough blocks to keep the SMs busy
+        int64_t slice = 64;
+        if ((n_kw + slice - 1) / slice > 65535) slice = (n_kw + 65534) / 65535;
+        const dim3 wgrid((unsigned)n_chunks, (unsigned)std::max<int64_t>(1, (n_kw + slice - 1) / slice));
         ++tl_kernel_launches;
-        window_kernel<<<n_chunks, 256, 0, st>>>(prefix, n_in_rings, d_chunks, n_chunks, d_K, d_kw_off, n_K,
-                                                n_kw, partial);
+        window_kernel<<<wgrid, 256, 0, st>>>(prefix, n_in_rings, d_chunks, n_chunks, d_K, d_kw_off, n_K, n_kw,
+                                             slice, partial);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -5,8 +5,11 @@
 //   turn count.  This is the only FP64 work per atom (one multiply per axis
 //   for an orthorhombic cell); every later phase n_x*U_x + n_y*U_y + n_z*U_z
 //   is exact integer arithmetic modulo one turn.  Slots may hold the atoms in
-//   a coprime-stride order (k -> k*a mod n_pad): summing in that order turns
-//   the coherent partial sums of an ordered crystal into random walks.
+//   a coprime-stride order (slot k holds atom k*a mod n_pad): summing in that
+//   order turns the coherent partial sums of an ordered crystal into random
+//   walks.  Threads follow the slots: the records are written coalesced and
+//   the positions gathered (scattering 16-byte records from coalesced reads
+//   measured 2.6x slower).
 //
 // direct_kernel: the plain reference-rate kernel.  A block owns 256*PX pixels
 //   of one frame and a range of atoms; atom records are staged in shared
@@ -17,6 +20,8 @@
 //   peaks), where every term has the same sign and size.  Atom ranges ("splits") give enough blocks
 //   for small grids; their FP64 partial amplitudes are added in a fixed order
 //   by reduce_kernel, so results are deterministic.
+#include <cmath>
+
 #include "xs_internal.h"
 
 namespace xs {
@@ -28,9 +33,17 @@ constexpr int kDirectPX = 4;     // pixels per thread
 constexpr int kAtomTile = 256;   // atom records staged per shared-memory tile
 
 // hs = 2^32 h^-1 (a power-of-two scaling, exact): rint(hs r) mod 2^32 equals
-// rint(frac(h^-1 r) 2^32) mod 2^32, one FP64 multiply-add chain per axis and
-// one conversion instead of floor, subtract, scale and convert
-__device__ __forceinline__ uint32_t turns_scaled(double v) { return (uint32_t)(unsigned long long)__double2ll_rn(v); }
+// rint(frac(h^-1 r) 2^32) mod 2^32.  Adding M = 1.5 * 2^52 to |v| < 2^51 gives
+// M + rint(v) (ties to even) in one FP64 rounding, and the low 32 bits of that
+// sum's encoding are rint(v) mod 2^32; in an FMA the product is not rounded
+// first.  GB300's FP64 pipe is narrow, so this replaces a multiply and a
+// conversion per axis by one FMA.
+constexpr double kRoundMagic = 6755399441055744.0;      // 1.5 * 2^52
+constexpr double kTurnLimit = 1125899906842624.0;       // 2^50: |v| bound checked
+__device__ __forceinline__ uint32_t turns_fma(double a, double b) {
+    return (uint32_t)__double2loint(fma(a, b, kRoundMagic));
+}
+__device__ __forceinline__ uint32_t turns_of(double v) { return (uint32_t)__double2loint(v + kRoundMagic); }
 
 constexpr int kPhaseFrames = 8;  // frames per block of the phase kernel
 
@@ -43,7 +56,10 @@ phase_kernel(const float* __restrict__ pos, const float* __restrict__ f, int64_t
     if (k >= n_pad) return;
     const int64_t j = opt.perm_mul == 1 ? k : (int64_t)(((uint64_t)k * (uint64_t)opt.perm_mul) % (uint64_t)n_pad);
     const bool real = j < n_atoms;
-    const float fj = real ? f[j] : 0.0f;
+    // atom j of this call is atom a of the frames (a subset when an index is given)
+    const int64_t a = (opt.index && real) ? (int64_t)opt.index[j] : j;
+    const int64_t stride = opt.index ? opt.pos_atoms : n_atoms;
+    const float fj = real ? f[a] : 0.0f;
     const int64_t t0 = (int64_t)blockIdx.y * kPhaseFrames;
     const int64_t t1 = min(n_frames, t0 + kPhaseFrames);
     for (int64_t t = t0; t < t1; ++t) {
@@ -51,22 +67,32 @@ phase_kernel(const float* __restrict__ pos, const float* __restrict__ f, int64_t
         r.ux = r.uy = r.uz = 0u;
         r.f = 0.0f;
         if (real) {
-            const float* p = pos + (t * n_atoms + j) * 3;
+            const float* p = pos + (t * stride + a) * 3;
             const float x = p[0], y = p[1], z = p[2];
-            if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(fj)) {
-                set_dev_error(err, kDevErrNonFinite);
-            } else {
-                if (opt.ortho) {
-                    r.ux = turns_scaled((double)x * hs.a[0]);
-                    r.uy = turns_scaled((double)y * hs.a[4]);
-                    if (opt.need_z) r.uz = turns_scaled((double)z * hs.a[8]);
-                } else {
-                    r.ux = turns_scaled(hs.a[0] * x + hs.a[1] * y + hs.a[2] * z);
-                    r.uy = turns_scaled(hs.a[3] * x + hs.a[4] * y + hs.a[5] * z);
-                    if (opt.need_z) r.uz = turns_scaled(hs.a[6] * x + hs.a[7] * y + hs.a[8] * z);
+            // NaN and Inf fail these comparisons too
+            bool ok = isfinite(fj);
+            if (opt.ortho) {
+                ok = ok && fabsf(x) < opt.lim[0] && fabsf(y) < opt.lim[1] && fabsf(z) < opt.lim[2];
+                if (ok) {
+                    r.ux = turns_fma((double)x, hs.a[0]);
+                    r.uy = turns_fma((double)y, hs.a[4]);
+                    if (opt.need_z) r.uz = turns_fma((double)z, hs.a[8]);
                 }
-                r.f = fj;
+            } else {
+                const double vx = hs.a[0] * x + hs.a[1] * y + hs.a[2] * z;
+                const double vy = hs.a[3] * x + hs.a[4] * y + hs.a[5] * z;
+                const double vz = hs.a[6] * x + hs.a[7] * y + hs.a[8] * z;
+                ok = ok && fabs(vx) < kTurnLimit && fabs(vy) < kTurnLimit && fabs(vz) < kTurnLimit;
+                if (ok) {
+                    r.ux = turns_of(vx);
+                    r.uy = turns_of(vy);
+                    if (opt.need_z) r.uz = turns_of(vz);
+                }
             }
+            if (ok)
+                r.f = fj;
+            else
+                set_dev_error(err, kDevErrNonFinite);
         }
         rec[t * n_pad + k] = r;
     }
@@ -188,9 +214,18 @@ cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int6
     if (gy > 65535) return cudaErrorInvalidConfiguration;
     Mat3 hs;
     for (int i = 0; i < 9; ++i) hs.a[i] = hinv.a[i] * 4294967296.0;
+    PhaseOpts o = opt;
+    // atom of slot k = k * a mod n_pad; the products stay below 2^64
+    if (o.perm_mul != 1 && n_pad >= ((int64_t)1 << 32)) return cudaErrorInvalidValue;
+    // orthorhombic cells: |x| < lim_x keeps |hs_xx x| below 2^50 (the FP32
+    // bound is rounded down, so the check is conservative)
+    for (int a = 0; a < 3; ++a) {
+        const double d = std::fabs(hs.a[4 * a]);
+        o.lim[a] = d > 0.0 ? std::nextafter((float)(1125899906842624.0 / d), 0.0f) : 3.0e38f;
+    }
     dim3 grid((unsigned)((n_pad + 255) / 256), (unsigned)gy);
     ++tl_kernel_launches;
-    phase_kernel<<<grid, 256, 0, st>>>(pos, f, n_atoms, n_frames, n_pad, hs, opt, rec, err);
+    phase_kernel<<<grid, 256, 0, st>>>(pos, f, n_atoms, n_frames, n_pad, hs, o, rec, err);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,99 @@
+// Several atom species with q-dependent form factors (Sec. 2.1: f_i(q), each
+// species' form factor a sum of Gaussians in |q|).  The amplitude splits by
+// species, S(q) = sum_s F_s(q) S_s(q) with S_s the plain direct sum over the
+// atoms of species s (per-atom weights kept), so each species runs through the
+// same phase and contraction kernels and these kernels combine the results:
+//   ff_table_kernel      F_s(|q_p|) for every species and pixel, FP64
+//   species_acc_kernel   acc[t][p] (+)= F_s(q_p) S_s[t][p], FP64 complex
+//   species_finish_kernel I = |acc|^2 and the amplitude, FP32
+#include <cmath>
+
+#include "xs_internal.h"
+
+namespace xs {
+
+namespace {
+
+// one thread per pixel: |q| = |2 pi h^-T n|, s = |q| / (4 pi),
+// F = sum_k a_k exp(-b_k s^2) + c for every species
+__global__ void ff_table_kernel(const double* __restrict__ coef, int n_species, GridDesc g, Mat3 hinv,
+                                double* __restrict__ table) {
+    const int64_t P = g.pixels();
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int64_t plane = (int64_t)g.nx * g.ny;
+    const int iz = (int)(p / plane);
+    const int64_t rem = p - (int64_t)iz * plane;
+    const int iy = (int)(rem / g.nx);
+    const int ix = (int)(rem - (int64_t)iy * g.nx);
+    const double n[3] = {(double)(g.nx0 + ix), (double)(g.ny0 + iy), (double)(g.nz0 + iz)};
+    double q2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        // q_a = 2 pi sum_b (h^-1)_{b a} n_b
+        const double qa = 6.283185307179586 * (hinv.a[0 * 3 + a] * n[0] + hinv.a[1 * 3 + a] * n[1] +
+                                               hinv.a[2 * 3 + a] * n[2]);
+        q2 += qa * qa;
+    }
+    const double s2 = q2 / (16.0 * 9.869604401089358);  // |q|^2 / (4 pi)^2
+    for (int sp = 0; sp < n_species; ++sp) {
+        const double* c = coef + 9 * sp;
+        double v = c[8];
+        for (int k = 0; k < 4; ++k) v += c[2 * k] * exp(-c[2 * k + 1] * s2);
+        table[(int64_t)sp * P + p] = v;
+    }
+}
+
+__global__ void species_acc_kernel(const float2* __restrict__ S, const double* __restrict__ ff, int64_t nf,
+                                   int64_t P, bool first, double2* __restrict__ acc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nf * P) return;
+    const double w = ff[i % P];
+    const float2 z = S[i];
+    double2 a = first ? make_double2(0.0, 0.0) : acc[i];
+    a.x = fma(w, (double)z.x, a.x);
+    a.y = fma(w, (double)z.y, a.y);
+    acc[i] = a;
+}
+
+__global__ void species_finish_kernel(const double2* __restrict__ acc, int64_t n, float* __restrict__ I,
+                                      float* __restrict__ amp) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 a = acc[i];
+    I[i] = (float)(a.x * a.x + a.y * a.y);
+    if (amp) {
+        amp[2 * i] = (float)a.x;
+        amp[2 * i + 1] = (float)a.y;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_ff_table(const double* d_coef, int n_species, const GridDesc& g, const Mat3& hinv, double* table,
+                            cudaStream_t st) {
+    const int64_t P = g.pixels();
+    if (P == 0 || n_species == 0) return cudaSuccess;
+    ++tl_kernel_launches;
+    ff_table_kernel<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(d_coef, n_species, g, hinv, table);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_species_acc(const float* S, const double* ff, int64_t nf, int64_t P, bool first, double* acc,
+                               cudaStream_t st) {
+    const int64_t n = nf * P;
+    if (n == 0) return cudaSuccess;
+    ++tl_kernel_launches;
+    species_acc_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const float2*>(S), ff, nf, P,
+                                                                    first, reinterpret_cast<double2*>(acc));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_species_finish(const double* acc, int64_t n, float* I, float* amp, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    ++tl_kernel_launches;
+    species_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const double2*>(acc), n, I,
+                                                                       amp);
+    return cudaGetLastError();
+}
+
+}  // namespace xs

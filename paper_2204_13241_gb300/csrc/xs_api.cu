@@ -371,7 +371,7 @@ xs_status xs_sync_status(xs_context* ctx, void* cuda_stream) {
     XS_CUDA(cudaMemcpy(&word, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     XS_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
     if (word & kDevErrTimeout) return fail(XS_ERR_TIMEOUT, "a kernel wait timed out (device error word %d)", word);
-    if (word & kDevErrNonFinite) return fail(XS_ERR_NUMERIC, "non-finite position or form factor (device error word %d)", word);
+    if (word & kDevErrNonFinite) return fail(XS_ERR_NUMERIC, "non-finite form factor, or a position that is non-finite or more than 2^18 cells from the origin (device error word %d)", word);
     return XS_OK;
 }
 
@@ -530,6 +530,148 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
 xs_status xs_intensity(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, xs_precision prec,
                        float* I_out, float* amp_out, void* cuda_stream) {
     return intensity_impl(ctx, traj, grid, prec, I_out, amp_out, static_cast<cudaStream_t>(cuda_stream), 0);
+}
+
+// --------------------------------------------------------------------------
+// several species with q-dependent form factors
+// --------------------------------------------------------------------------
+
+xs_status xs_intensity_species(xs_context* ctx, const xs_traj* traj, const int32_t* species, int32_t n_species,
+                               const double* coef, const xs_qgrid* grid, xs_precision prec, float* I_out,
+                               float* amp_out, void* cuda_stream) {
+    if (!ctx || !traj || !I_out) return fail(XS_ERR_INVALID_ARG, "context, trajectory and I_out are required");
+    xs_status s = check_grid(grid);
+    if (s != XS_OK) return s;
+    if (prec != XS_PREC_FP32_DIRECT && prec != XS_PREC_SPLIT_FP16 && prec != XS_PREC_SPLIT_BF16)
+        return fail(XS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (n_species < 1 || !coef) return fail(XS_ERR_INVALID_ARG, "need n_species >= 1 and the form factor table");
+    for (int64_t i = 0; i < (int64_t)n_species * 9; ++i)
+        if (!std::isfinite(coef[i])) return fail(XS_ERR_INVALID_ARG, "non-finite form factor coefficient");
+    if (traj->n_atoms < 0 || traj->n_frames < 0) return fail(XS_ERR_INVALID_ARG, "negative atom or frame count");
+    if (traj->n_atoms > (int64_t)1 << 31) return fail(XS_ERR_INVALID_ARG, "more than 2^31 atoms");
+    if (traj->n_atoms > 0 && traj->n_frames > 0 && (!traj->pos || !traj->f || !species))
+        return fail(XS_ERR_INVALID_ARG, "positions, weights or species are NULL");
+    if (traj->pos_on_host) return fail(XS_ERR_INVALID_ARG, "the species path takes device positions");
+    double hinv[9];
+    if (!invert3(traj->box.h, hinv)) return fail(XS_ERR_INVALID_ARG, "singular or non-finite cell matrix");
+    const GridDesc g = to_desc(grid);
+    const int64_t P = g.pixels(), T = traj->n_frames, N = traj->n_atoms;
+    if (P == 0 || T == 0) return XS_OK;
+    if (!is_device_ptr(I_out) || (amp_out && !is_device_ptr(amp_out)))
+        return fail(XS_ERR_INVALID_ARG, "the species path writes device outputs");
+    if (N > 0 && !is_device_ptr(traj->pos)) return fail(XS_ERR_INVALID_ARG, "positions must be in device memory");
+    const bool use_tc = prec != XS_PREC_FP32_DIRECT;
+    if (use_tc && !tc_supported(g)) return fail(XS_ERR_UNSUPPORTED, "grid not supported by the tensor-core path");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+    // atoms grouped by species (stable)
+    std::vector<int64_t> start((size_t)n_species + 1, 0);
+    for (int64_t j = 0; j < N; ++j) {
+        if (species[j] < 0 || species[j] >= n_species)
+            return fail(XS_ERR_INVALID_ARG, "atom %lld has species %d outside [0, %d)", (long long)j, species[j], n_species);
+        ++start[(size_t)species[j] + 1];
+    }
+    for (int sp = 0; sp < n_species; ++sp) start[(size_t)sp + 1] += start[(size_t)sp];
+    std::vector<int32_t> index((size_t)std::max<int64_t>(N, 1), 0);
+    {
+        std::vector<int64_t> fill(start.begin(), start.end() - 1);
+        for (int64_t j = 0; j < N; ++j) index[(size_t)fill[(size_t)species[j]]++] = (int32_t)j;
+    }
+    int64_t n_pad_max = 64;
+    for (int sp = 0; sp < n_species; ++sp)
+        n_pad_max = std::max<int64_t>(n_pad_max, round_up(start[(size_t)sp + 1] - start[(size_t)sp], 64));
+    std::vector<char> blob;
+    const size_t o_coef = push(blob, coef, (size_t)n_species * 9);
+    const size_t o_index = push(blob, index.data(), index.size());
+    void* d = nullptr;
+    s = upload_const(ctx, "species", blob, st, &d);
+    if (s != XS_OK) return s;
+    const double* d_coef = reinterpret_cast<const double*>(static_cast<char*>(d) + o_coef);
+    const int32_t* d_index = reinterpret_cast<const int32_t*>(static_cast<char*>(d) + o_index);
+
+    // frames per chunk: records plus the per-frame amplitude buffers
+    const size_t per_frame = (size_t)n_pad_max * sizeof(AtomRec) + (size_t)P * (2 * sizeof(float) + sizeof(float) + 2 * sizeof(double));
+    int64_t fchunk = std::max<int64_t>(1, std::min<int64_t>(T, (int64_t)(((size_t)6 << 30) / per_frame)));
+    if (fchunk > 65535) fchunk = 65535;
+    int tc_pairs = 0, chunk_stages = 32;
+    DirectPlan dmax{};
+    if (use_tc) {
+        tc_pairs = tc_pair_capacity(ctx->num_sms);
+    } else {
+        for (int sp = 0; sp < n_species; ++sp) {
+            const int64_t n = start[(size_t)sp + 1] - start[(size_t)sp];
+            if (n == 0) continue;
+            const DirectPlan pl = plan_direct(round_up(n, 64), fchunk, g, ctx->num_sms);
+            if (pl.partial_bytes > dmax.partial_bytes) dmax = pl;
+        }
+    }
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        size_t o = round_up((int64_t)off, 256);
+        off = o + bytes;
+        return o;
+    };
+    const size_t o_rec = carve((size_t)fchunk * n_pad_max * sizeof(AtomRec));
+    const size_t o_part = carve(use_tc ? tc_scratch_bytes(tc_pairs) : dmax.partial_bytes);
+    const size_t o_S = carve((size_t)fchunk * P * 2 * sizeof(float));
+    const size_t o_I = carve((size_t)fchunk * P * sizeof(float));
+    const size_t o_acc = carve((size_t)fchunk * P * 2 * sizeof(double));
+    const size_t o_ff = carve((size_t)n_species * P * sizeof(double));
+    s = ensure_ws(ctx, off + 256);
+    if (s != XS_OK) return s;
+    char* ws = static_cast<char*>(ctx->ws);
+    AtomRec* rec = reinterpret_cast<AtomRec*>(ws + o_rec);
+    float* S_tmp = reinterpret_cast<float*>(ws + o_S);
+    float* I_tmp = reinterpret_cast<float*>(ws + o_I);
+    double* acc = reinterpret_cast<double*>(ws + o_acc);
+    double* ff = reinterpret_cast<double*>(ws + o_ff);
+    Mat3 hm;
+    for (int i = 0; i < 9; ++i) hm.a[i] = hinv[i];
+    XS_CUDA(traced(ctx, "species", st, [&] { return launch_ff_table(d_coef, n_species, g, hm, ff, st); }));
+
+    for (int64_t t0 = 0; t0 < T; t0 += fchunk) {
+        const int64_t nf = std::min(fchunk, T - t0);
+        bool first = true;
+        for (int sp = 0; sp < n_species; ++sp) {
+            const int64_t ns = start[(size_t)sp + 1] - start[(size_t)sp];
+            if (ns == 0) continue;
+            const int64_t n_pad = round_up(ns, 64);
+            PhaseOpts popt;
+            popt.ortho = is_ortho(hinv);
+            popt.need_z = !(g.nz == 1 && g.nz0 == 0);
+            popt.perm_mul = use_tc ? coprime_stride(n_pad) : 1;
+            popt.index = d_index + start[(size_t)sp];
+            popt.pos_atoms = N;
+            const float* pos_c = traj->pos + (size_t)t0 * N * 3;
+            XS_CUDA(traced(ctx, "phase", st,
+                           [&] { return launch_phase(pos_c, traj->f, ns, nf, n_pad, hm, popt, rec, ctx->d_err, st); }));
+            if (use_tc) {
+                const TcTraj tr = tc_traj(rec, n_pad, nf, g, I_tmp, S_tmp);
+                XS_CUDA(traced(ctx, "tc", st, [&] {
+                    return launch_tc_single(tr, tc_pairs, chunk_stages, prec == XS_PREC_SPLIT_BF16,
+                                            reinterpret_cast<double*>(ws + o_part), ctx->d_err, ctx->timeout_ns, st);
+                }));
+            } else {
+                const DirectPlan pc = plan_direct(n_pad, nf, g, ctx->num_sms);
+                if (pc.partial_bytes > dmax.partial_bytes) return fail(XS_ERR_CUDA, "internal: partial plan grew");
+                XS_CUDA(traced(ctx, "direct", st,
+                               [&] { return launch_direct(rec, n_pad, nf, g, pc, ws + o_part, I_tmp, S_tmp, st); }));
+            }
+            XS_CUDA(traced(ctx, "species", st, [&] {
+                return launch_species_acc(S_tmp, ff + (size_t)sp * P, nf, P, first, acc, st);
+            }));
+            first = false;
+        }
+        float* Ic = I_out + (size_t)t0 * P;
+        float* Ac = amp_out ? amp_out + (size_t)t0 * P * 2 : nullptr;
+        if (first) {  // no atoms at all
+            XS_CUDA(cudaMemsetAsync(Ic, 0, (size_t)nf * P * sizeof(float), st));
+            if (Ac) XS_CUDA(cudaMemsetAsync(Ac, 0, (size_t)nf * P * 2 * sizeof(float), st));
+        } else {
+            XS_CUDA(traced(ctx, "species", st, [&] { return launch_species_finish(acc, nf * P, Ic, Ac, st); }));
+        }
+    }
+    return XS_OK;
 }
 
 xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, int32_t n_traj,
@@ -804,6 +946,32 @@ xs_status xs_ring_index(const xs_qgrid* grid, const xs_box* box, double ring_wid
     return XS_OK;
 }
 
+// pixels grouped ring by ring (stable within a ring): perm[start[r] ..
+// start[r+1]) are the pixels of ring r + 1
+struct RingLayout {
+    std::vector<int32_t> count;
+    std::vector<int64_t> start;
+    std::vector<int32_t> perm;
+};
+
+static xs_status ring_layout(const xs_qgrid* grid, const xs_box* box, double ring_width, int32_t n_rings,
+                             RingLayout& out) {
+    std::vector<int32_t> ring;
+    xs_status s = ring_of_pixels(grid, box, ring_width, n_rings, ring);
+    if (s != XS_OK) return s;
+    const int64_t P = (int64_t)ring.size();
+    out.count.assign((size_t)n_rings, 0);
+    for (int32_t r : ring)
+        if (r > 0) ++out.count[(size_t)r - 1];
+    out.start.assign((size_t)n_rings + 1, 0);
+    for (int r = 0; r < n_rings; ++r) out.start[(size_t)r + 1] = out.start[(size_t)r] + out.count[(size_t)r];
+    out.perm.assign((size_t)out.start[(size_t)n_rings], 0);
+    std::vector<int64_t> fill(out.start.begin(), out.start.end() - 1);
+    for (int64_t p = 0; p < P; ++p)
+        if (ring[(size_t)p] > 0) out.perm[(size_t)fill[(size_t)ring[(size_t)p] - 1]++] = (int32_t)p;
+    return XS_OK;
+}
+
 xs_status xs_xsvs_contrast(xs_context* ctx, const float* I, int64_t T, const xs_qgrid* grid, const xs_box* box,
                            const int32_t* Ks, int32_t n_K, double ring_width, int32_t n_rings, double* beta_out,
                            int32_t* ring_count_out, void* cuda_stream) {
@@ -816,23 +984,14 @@ xs_status xs_xsvs_contrast(xs_context* ctx, const float* I, int64_t T, const xs_
         if (Ks[k] < 1 || Ks[k] > T) return fail(XS_ERR_INVALID_ARG, "window length %d outside [1, T]", Ks[k]);
     if (n_K == 0 || n_rings == 0) return XS_OK;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    std::vector<int32_t> ring;
-    s = ring_of_pixels(grid, box, ring_width, n_rings, ring);
+    RingLayout lay;
+    s = ring_layout(grid, box, ring_width, n_rings, lay);
     if (s != XS_OK) return s;
-    const int64_t P = (int64_t)ring.size();
-    // pixels grouped ring by ring (stable within a ring)
-    std::vector<int32_t> count((size_t)n_rings, 0);
-    for (int32_t r : ring)
-        if (r > 0) ++count[(size_t)r - 1];
-    std::vector<int64_t> start((size_t)n_rings + 1, 0);
-    for (int r = 0; r < n_rings; ++r) start[(size_t)r + 1] = start[(size_t)r] + count[(size_t)r];
+    const int64_t P = (int64_t)grid->nx * grid->ny * grid->nz;
+    const std::vector<int32_t>& count = lay.count;
+    const std::vector<int64_t>& start = lay.start;
+    const std::vector<int32_t>& perm = lay.perm;
     const int64_t n_in = start[(size_t)n_rings];
-    std::vector<int32_t> perm((size_t)n_in);
-    {
-        std::vector<int64_t> fill(start.begin(), start.end() - 1);
-        for (int64_t p = 0; p < P; ++p)
-            if (ring[(size_t)p] > 0) perm[(size_t)fill[(size_t)ring[(size_t)p] - 1]++] = (int32_t)p;
-    }
     constexpr int kChunk = 128;
     std::vector<int32_t> chunks;  // int4 records (ring, start, count, 0)
     std::vector<int32_t> first((size_t)n_rings + 1, 0);
@@ -882,6 +1041,81 @@ xs_status xs_xsvs_contrast(xs_context* ctx, const float* I, int64_t T, const xs_
                         n_K, n_kw, reinterpret_cast<const int32_t*>(dc + o_first), reinterpret_cast<const int32_t*>(dc + o_count),
                         n_rings, reinterpret_cast<double*>(ws + o_prefix), reinterpret_cast<double2*>(ws + o_partial),
                         beta_out, st); }));
+    return XS_OK;
+}
+
+// --------------------------------------------------------------------------
+// intermediate scattering function and the contrast it predicts
+// --------------------------------------------------------------------------
+
+xs_status xs_isf(xs_context* ctx, const float* amp, int64_t T, int64_t P, const int32_t* taus, int32_t n_tau,
+                 double sum_f2, double* F_out, double* Fhat_out, void* cuda_stream) {
+    if (!ctx || !amp || !taus || !F_out) return fail(XS_ERR_INVALID_ARG, "context, amp, taus and F_out are required");
+    if (T < 1 || P < 0 || n_tau < 0) return fail(XS_ERR_INVALID_ARG, "need T >= 1, P >= 0, n_tau >= 0");
+    if (!(sum_f2 > 0.0) || !std::isfinite(sum_f2)) return fail(XS_ERR_INVALID_ARG, "sum_f2 must be finite and > 0");
+    for (int32_t k = 0; k < n_tau; ++k)
+        if (taus[k] < 0 || taus[k] >= T) return fail(XS_ERR_INVALID_ARG, "delay %d outside [0, T)", taus[k]);
+    if (P == 0 || n_tau == 0) return XS_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<char> blob;
+    const size_t o_tau = push(blob, taus, (size_t)n_tau);
+    void* d = nullptr;
+    xs_status s = upload_const(ctx, "isf", blob, st, &d);
+    if (s != XS_OK) return s;
+    const int32_t* d_taus = reinterpret_cast<const int32_t*>(static_cast<char*>(d) + o_tau);
+    XS_CUDA(traced(ctx, "isf", st,
+                   [&] { return launch_isf(amp, T, P, d_taus, n_tau, 1.0 / sum_f2, F_out, Fhat_out, st); }));
+    return XS_OK;
+}
+
+xs_status xs_contrast_from_isf(xs_context* ctx, const double* Fhat, int64_t Kmax, const xs_qgrid* grid,
+                               const xs_box* box, const int32_t* Ks, int32_t n_K, double ring_width,
+                               int32_t n_rings, double* ratio_out, int32_t* ring_count_out, void* cuda_stream) {
+    const bool empty = n_K == 0 || n_rings == 0;
+    if (!ctx || !Fhat || !box || (!Ks && n_K > 0) || (!ratio_out && !empty))
+        return fail(XS_ERR_INVALID_ARG, "missing argument");
+    xs_status s = check_grid(grid);
+    if (s != XS_OK) return s;
+    if (Kmax < 1 || n_K < 0 || n_rings < 0) return fail(XS_ERR_INVALID_ARG, "need Kmax >= 1, n_K >= 0, n_rings >= 0");
+    if (!(ring_width > 0.0 && ring_width <= 1.0)) return fail(XS_ERR_INVALID_ARG, "ring_width must be in (0, 1]");
+    for (int32_t k = 0; k < n_K; ++k)
+        if (Ks[k] < 1 || Ks[k] > Kmax) return fail(XS_ERR_INVALID_ARG, "window length %d outside [1, Kmax]", Ks[k]);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    RingLayout lay;
+    s = ring_layout(grid, box, ring_width, n_rings, lay);
+    if (s != XS_OK) return s;
+    if (ring_count_out && n_rings > 0) std::memcpy(ring_count_out, lay.count.data(), lay.count.size() * sizeof(int32_t));
+    if (n_K == 0 || n_rings == 0) return XS_OK;
+    const int64_t P = (int64_t)grid->nx * grid->ny * grid->nz;
+    const int64_t n_in = lay.start[(size_t)n_rings];
+    // window lengths in ascending order, each with its output row
+    std::vector<int32_t> order((size_t)n_K);
+    for (int32_t k = 0; k < n_K; ++k) order[(size_t)k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return Ks[a] < Ks[b]; });
+    std::vector<int32_t> k_sorted((size_t)n_K), k_row((size_t)n_K);
+    for (int32_t k = 0; k < n_K; ++k) {
+        k_sorted[(size_t)k] = Ks[order[(size_t)k]];
+        k_row[(size_t)k] = order[(size_t)k];
+    }
+    std::vector<char> blob;
+    const int64_t key[2] = {Kmax, P};
+    push(blob, key, 2);
+    const size_t o_perm = push(blob, lay.perm.data(), lay.perm.size());
+    const size_t o_start = push(blob, lay.start.data(), lay.start.size());
+    const size_t o_K = push(blob, k_sorted.data(), k_sorted.size());
+    const size_t o_row = push(blob, k_row.data(), k_row.size());
+    void* d = nullptr;
+    s = upload_const(ctx, "isf_contrast", blob, st, &d);
+    if (s != XS_OK) return s;
+    char* dc = static_cast<char*>(d);
+    s = ensure_ws(ctx, (size_t)std::max<int64_t>(1, (int64_t)n_K * n_in) * sizeof(double) + 256);
+    if (s != XS_OK) return s;
+    double* b_pixel = static_cast<double*>(ctx->ws);
+    XS_CUDA(traced(ctx, "isf_contrast", st, [&] {
+        return launch_isf_contrast(Fhat, Kmax, P, reinterpret_cast<const int32_t*>(dc + o_perm), n_in,
+                                   reinterpret_cast<const int32_t*>(dc + o_K), reinterpret_cast<const int32_t*>(dc + o_row),
+                                   n_K, reinterpret_cast<const int64_t*>(dc + o_start), n_rings, b_pixel, ratio_out, st);
+    }));
     return XS_OK;
 }
 

@@ -9,7 +9,7 @@ namespace xs {
 // Bits of the device error word (one int per context).
 enum : int {
     kDevErrTimeout = 1,    // a bounded wait expired
-    kDevErrNonFinite = 2,  // a non-finite position or form factor was read
+    kDevErrNonFinite = 2,  // a non-finite form factor, or a position non-finite or more than 2^18 cells out
 };
 
 // 3x3 inverse cell matrix (row-major), passed by value to kernels.

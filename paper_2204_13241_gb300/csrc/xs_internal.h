@@ -30,7 +30,10 @@ struct GridDesc {
 struct PhaseOpts {
     bool ortho = false;
     bool need_z = true;
-    int64_t perm_mul = 1;
+    int64_t perm_mul = 1;                // slot k holds atom k * perm_mul mod n_pad
+    float lim[3] = {0.0f, 0.0f, 0.0f};  // set by launch_phase
+    const int32_t* index = nullptr;      // optional device [n_atoms]: atoms of the frames to use
+    int64_t pos_atoms = 0;               // atoms per frame of `pos` when `index` is given
 };
 cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int64_t n_frames,
                          int64_t n_pad, const Mat3& hinv, const PhaseOpts& opt, AtomRec* rec, int* err,
@@ -85,6 +88,17 @@ struct XsvsLayout {
     int n_chunks;         // (ring, pixel range) chunks
     int64_t n_kw;         // sum over K of floor(T/K)
 };
+cudaError_t launch_ff_table(const double* d_coef, int n_species, const GridDesc& g, const Mat3& hinv, double* table,
+                            cudaStream_t st);
+cudaError_t launch_species_acc(const float* S, const double* ff, int64_t nf, int64_t P, bool first, double* acc,
+                               cudaStream_t st);
+cudaError_t launch_species_finish(const double* acc, int64_t n, float* I, float* amp, cudaStream_t st);
+cudaError_t launch_isf(const float* amp, int64_t T, int64_t P, const int32_t* d_taus, int n_tau, double inv_sum_f2,
+                       double* F, double* Fhat, cudaStream_t st);
+cudaError_t launch_isf_contrast(const double* Fhat, int64_t Kmax, int64_t P, const int32_t* d_perm, int64_t n_in,
+                                const int32_t* d_K_sorted, const int32_t* d_k_row, int n_K,
+                                const int64_t* d_ring_start, int n_rings, double* b_pixel, double* out,
+                                cudaStream_t st);
 cudaError_t launch_xsvs(const float* I, int64_t T, int64_t P, const int32_t* d_perm,
                         const int4* d_chunks, int n_chunks, int64_t n_in_rings,
                         const int32_t* d_K, const int64_t* d_kw_off, int n_K, int64_t n_kw,

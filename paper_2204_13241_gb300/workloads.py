@@ -291,6 +291,30 @@ def gas_on_device(params: dict, device, dtype_f=None):
     return pos, f, cubic_box(L)
 
 
+def speckle_amplitudes(seed: int, T: int, rho, device):
+    """The circular complex Gaussian AR(1) amplitude a(t) = rho a(t-1) +
+    sqrt(1 - rho^2) xi(t), E|a|^2 = 1, per pixel `rho` (float32 tensor [P]),
+    as float32 [T][P][2] (re, im) on `device`; its normalised intermediate
+    scattering function is rho^tau."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    rho = rho.to(device=device, dtype=torch.float32)
+    P = rho.shape[0]
+    s = torch.sqrt(1.0 - rho * rho)
+    out = torch.empty((T, P, 2), dtype=torch.float32, device=device)
+    a = torch.complex(torch.randn(P, generator=g, device=device), torch.randn(P, generator=g, device=device))
+    a = a * (0.5 ** 0.5)
+    for t in range(T):
+        if t > 0:
+            xi = torch.complex(torch.randn(P, generator=g, device=device), torch.randn(P, generator=g, device=device))
+            a = rho * a + s * xi * (0.5 ** 0.5)
+        out[t, :, 0] = a.real
+        out[t, :, 1] = a.imag
+    return out
+
+
 def speckle_series(seed: int, T: int, rho, device):
     """Synthetic speckle intensities I(t, p) = |a(t, p)|^2 of a circular complex
     Gaussian AR(1) amplitude a(t) = rho a(t-1) + sqrt(1 - rho^2) xi(t) with
