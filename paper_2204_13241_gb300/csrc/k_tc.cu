@@ -91,12 +91,18 @@ constexpr size_t kSmemBytes = 1024 + kStages * kStageBytes + sizeof(SmemCtl);
 
 struct TcArgs {
     TcTraj single;          // the trajectory when `units` is null
-    int64_t single_units;   // its units, assigned round-robin to the pairs
+    // single trajectory: units [0, full * n_pairs) round-robin, whole; the
+    // remaining `rem` units are split along the atoms into `parts` stage
+    // ranges each, and the rem * parts pieces are dealt round-robin as well
+    int64_t full, rem;
+    int parts;
     const TcTraj* trajs;    // batched: trajectory table
     const int4* units;      // batched: (traj, frame, plane, tile_x | tile_y << 16), pair by pair
     const int* pair_start;  // batched: [n_pairs + 1] offsets into `units`
     int chunk_stages;
     double* scratch;        // [gridDim.x][256][128] running totals as FP32 pairs (hi, lo)
+    double2* partial;       // split units: [rem][parts][128 x][128 y] partial amplitudes
+    int* counters;          // split units: [rem][2] finished epilogue warps per CTA half (start at 0)
     int* err;
     int64_t timeout_ns;
 };
@@ -328,10 +334,12 @@ struct Unit {
     const uint4* rec;  // records of the unit's frame
     float* I;
     float* amp;
-    int n_stages;
     int nx0, nx, ny0, ny, nz0, nz;
     int t, iz, tx, ty;
     bool centred;  // tile n_x, n_y in [-64, 64) on the plane n_z = 0
+    int s0, s1;    // stage range of this piece of the unit
+    int split;     // split unit index, or -1 for a whole unit
+    int part;
 };
 
 __device__ __forceinline__ Unit make_unit(const TcTraj& tr, int t, int iz, int tx, int ty) {
@@ -339,7 +347,6 @@ __device__ __forceinline__ Unit make_unit(const TcTraj& tr, int t, int iz, int t
     u.rec = tr.rec + (int64_t)t * tr.n_pad;
     u.I = tr.I;
     u.amp = tr.amp;
-    u.n_stages = tr.n_stages;
     u.nx0 = tr.nx0;
     u.nx = tr.nx;
     u.ny0 = tr.ny0;
@@ -351,28 +358,76 @@ __device__ __forceinline__ Unit make_unit(const TcTraj& tr, int t, int iz, int t
     u.tx = tx;
     u.ty = ty;
     u.centred = tr.nx0 + tx * kTile == -kHalf && tr.ny0 + ty * kTile == -kHalf && tr.nz0 + iz == 0;
+    u.s0 = 0;
+    u.s1 = tr.n_stages;
+    u.split = -1;
+    u.part = 0;
     return u;
 }
 
-// unit k of `pair`: round-robin over a single trajectory, or the pair's list
+__device__ __forceinline__ Unit single_unit(const TcTraj& tr, int64_t u) {
+    const int tx = (int)(u % tr.tiles_x);
+    int64_t r = u / tr.tiles_x;
+    const int ty = (int)(r % tr.tiles_y);
+    r /= tr.tiles_y;
+    const int iz = (int)(r % tr.nz);
+    return make_unit(tr, (int)(r / tr.nz), iz, tx, ty);
+}
+
+// piece k of `pair`: round-robin over a single trajectory (whole units, then
+// the pieces of the split ones), or the pair's list
 __device__ __forceinline__ Unit get_unit(const TcArgs& a, int64_t pair, int64_t n_pairs, int64_t k) {
     if (!a.units) {
         const TcTraj& tr = a.single;
-        const int64_t u = pair + k * n_pairs;
-        const int tx = (int)(u % tr.tiles_x);
-        int64_t r = u / tr.tiles_x;
-        const int ty = (int)(r % tr.tiles_y);
-        r /= tr.tiles_y;
-        const int iz = (int)(r % tr.nz);
-        return make_unit(tr, (int)(r / tr.nz), iz, tx, ty);
+        if (k < a.full) return single_unit(tr, pair + k * n_pairs);
+        const int64_t i = pair + (k - a.full) * n_pairs;  // piece index among the split units
+        const int64_t r = i / a.parts;
+        Unit u = single_unit(tr, a.full * n_pairs + r);
+        if (a.parts > 1) {
+            const int q = (int)(i - r * a.parts);
+            u.s0 = (int)((int64_t)q * tr.n_stages / a.parts);
+            u.s1 = (int)((int64_t)(q + 1) * tr.n_stages / a.parts);
+            u.split = (int)r;
+            u.part = q;
+        }
+        return u;
     }
     const int4 w = a.units[a.pair_start[pair] + k];
     return make_unit(a.trajs[w.x], w.y, w.z, w.w & 0xFFFF, w.w >> 16);
 }
 
 __device__ __forceinline__ int64_t units_of_pair(const TcArgs& a, int64_t pair, int64_t n_pairs) {
-    if (!a.units) return a.single_units > pair ? (a.single_units - 1 - pair) / n_pairs + 1 : 0;
+    if (!a.units) {
+        const int64_t pieces = a.rem * a.parts;
+        return a.full + (pieces > pair ? (pieces - 1 - pair) / n_pairs + 1 : 0);
+    }
     return a.pair_start[pair + 1] - a.pair_start[pair];
+}
+
+// Sum of the pieces of a split unit for the rows of CTA half `rank` (64 x
+// slots by 128 y), in part order, and I = |S|^2; one warp.
+__device__ __noinline__ void finish_split(const TcArgs& a, const Unit& up, int rank, int lane) {
+    const double2* base = a.partial + (size_t)up.split * a.parts * (kTile * kTile);
+    for (int idx = lane; idx < kHalf * kTile; idx += 32) {
+        const int x_slot = idx / kTile, yi = idx - x_slot * kTile;
+        float f;
+        const int xi = up.centred ? centred_index(x_slot, rank, f) : kHalf * rank + x_slot;
+        double re = 0.0, im = 0.0;
+        for (int q = 0; q < a.parts; ++q) {
+            const double2 v = __ldcg(base + (size_t)q * (kTile * kTile) + (size_t)xi * kTile + yi);
+            re += v.x;
+            im += v.y;
+        }
+        const int ix = up.tx * kTile + xi, iy = up.ty * kTile + yi;
+        if (ix < up.nx && iy < up.ny) {
+            const int64_t o = (((int64_t)up.t * up.nz + up.iz) * up.ny + iy) * up.nx + ix;
+            up.I[o] = (float)(re * re + im * im);
+            if (up.amp) {
+                up.amp[2 * o] = (float)re;
+                up.amp[2 * o + 1] = (float)im;
+            }
+        }
+    }
 }
 
 template <bool BF16>
@@ -434,13 +489,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
         Unit up{};
         if (my_units > 0) up = get_unit(args, pair, n_pairs, 0);
         uint4 r_next = make_uint4(0, 0, 0, 0);
-        if (my_units > 0) r_next = __ldg(up.rec + k);
+        if (my_units > 0) r_next = __ldg(up.rec + (int64_t)up.s0 * kBK + k);
         bool stop = false;
         for (int64_t ku = 0; ku < my_units && !stop; ++ku) {
             Unit up_next{};
             const bool has_next = ku + 1 < my_units;
             if (has_next) up_next = get_unit(args, pair, n_pairs, ku + 1);
-            const int n_st = up.n_stages;
+            const int st1 = up.s1;
             const uint4* rec_cur = up.rec + k;
             const bool centred = up.centred;
             const bool extra = centred && (ri & 1) == 0;  // also builds X(32 rank + 32)
@@ -449,12 +504,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                         : (is_a ? (uint32_t)(up.nx0 + up.tx * kTile + kHalf * (int)rank + run0)
                                 : (uint32_t)(up.ny0 + up.ty * kTile + kHalf * (int)rank + run0));
             const uint32_t nz = (uint32_t)(up.nz0 + up.iz);
-            for (int s = 0; s < n_st; ++s) {
+            for (int s = up.s0; s < st1; ++s) {
                 const uint4 r = r_next;
-                if (s + 1 < n_st)
+                if (s + 1 < st1)
                     r_next = __ldg(rec_cur + (int64_t)(s + 1) * kBK);
                 else if (has_next)
-                    r_next = __ldg(up_next.rec + k);
+                    r_next = __ldg(up_next.rec + (int64_t)up_next.s0 * kBK + k);
                 // exact step z^2 and seeds E(n0), E(n0 + 1) of this thread's run
                 const uint32_t U = is_a ? r.x : r.y;
                 const float2 z2 = cis_turns(2u * U, ctl->tab);
@@ -554,7 +609,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
             uint32_t phase = 0;
             bool ok = true;
             for (int64_t ku = 0; ku < my_units && ok; ++ku) {
-                const int n_stages = get_unit(args, pair, n_pairs, ku).n_stages;
+                const Unit uu = get_unit(args, pair, n_pairs, ku);
+                const int n_stages = uu.s1 - uu.s0;
                 const int n_chunks = (n_stages + args.chunk_stages - 1) / args.chunk_stages;
                 for (int c = 0; c < n_chunks && ok; ++c, ++a_cnt) {
                     const int b = (int)(a_cnt & 1);
@@ -608,7 +664,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
             uint32_t phase = 0;
             bool ok = true;
             for (int64_t ku = 0; ku < my_units && ok; ++ku) {
-                const int n_stages = get_unit(args, pair, n_pairs, ku).n_stages;
+                const Unit uu = get_unit(args, pair, n_pairs, ku);
+                const int n_stages = uu.s1 - uu.s0;
                 for (int s = 0; s < n_stages; ++s) {
                     if (!wait_bar(&ctl->fill[slot], phase, abort_flag, args.err, args.timeout_ns, 20000u)) {
                         ok = false;
@@ -638,7 +695,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
         bool ok = true;
         for (int64_t ku = 0; ku < my_units && ok; ++ku) {
             const Unit up = get_unit(args, pair, n_pairs, ku);
-            const int n_chunks = (up.n_stages + args.chunk_stages - 1) / args.chunk_stages;
+            const int n_chunks = (up.s1 - up.s0 + args.chunk_stages - 1) / args.chunk_stages;
             const bool centred = up.centred;
             const int xi = centred ? xi_c : kHalf * (int)rank + x_slot;
             const double sx = centred ? (double)sx_c : 1.0;  // sign of the stored Im x rows
@@ -698,7 +755,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                         rcv[i] = __shfl_xor_sync(0xffffffffu, snd, 2);
                     }
                     const int ix = up.tx * kTile + xi;
-                    if (ix < up.nx) {
+                    // a piece of a split unit keeps its partial amplitude of every pixel
+                    double2* part_dst = up.split >= 0 ? args.partial +
+                                                            ((size_t)up.split * args.parts + up.part) * (kTile * kTile) +
+                                                            (size_t)xi * kTile
+                                                      : nullptr;
+                    if (part_dst || ix < up.nx) {
 #pragma unroll
                         for (int hh = 0; hh < 2; ++hh) {
 #pragma unroll
@@ -718,7 +780,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                                 const double sre = p_rr - sx * sy * p_ii;
                                 const double sim = sy * p_ri + sx * p_ir;
                                 const int iy = up.ty * kTile + yi;
-                                if (iy < up.ny) {
+                                if (part_dst) {
+                                    part_dst[yi] = make_double2(sre, sim);
+                                } else if (iy < up.ny) {
                                     const int64_t o = (((int64_t)up.t * up.nz + up.iz) * up.ny + iy) * up.nx + ix;
                                     up.I[o] = (float)(sre * sre + sim * sim);
                                     if (up.amp) {
@@ -733,6 +797,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive_cluster(acc_empty_c0 + (uint32_t)b * 8u);
+                if (last && up.split >= 0) {
+                    // the last of the 4 x parts epilogue warps to finish this CTA's
+                    // half of a split unit adds the pieces in part order
+                    __threadfence();
+                    __syncwarp();
+                    int done = 0;
+                    if (lane == 0) done = atomicAdd(&args.counters[up.split * 2 + (int)rank], 1);
+                    done = __shfl_sync(0xffffffffu, done, 0);
+                    if (done == kEpiWarps * args.parts - 1) {
+                        __threadfence();
+                        finish_split(args, up, (int)rank, lane);
+                        __syncwarp();
+                        if (lane == 0) args.counters[up.split * 2 + (int)rank] = 0;
+                    }
+                }
             }
         }
     }
@@ -851,18 +930,68 @@ static cudaError_t launch(const TcArgs& a, int n_pairs, bool bf16, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_single(const TcTraj& tr, int n_pairs, int chunk_stages, bool bf16, double* scratch, int* err,
-                             int64_t timeout_ns, cudaStream_t st) {
+TcSplit tc_split_plan(int64_t units, int n_pairs, int n_stages, int chunk_stages) {
+    // Units are dealt round-robin; when the last wave is partial, its units
+    // are cut along the atoms into `parts` pieces so that the last wave takes
+    // ceil(rem * parts / n_pairs) / parts of a unit instead of a whole one.
+    constexpr int kMaxParts = 16;
+    constexpr int64_t kMaxPieces = 1024;  // 256 KB of partial amplitudes each
+    TcSplit sp;
+    sp.full = 0;
+    sp.rem = units;
+    sp.parts = 1;
+    if (units <= 0 || n_pairs <= 0) return sp;
+    const int64_t F = units / n_pairs, R = units % n_pairs;
+    if (R == 0) return sp;
+    const int chunk = chunk_stages > 0 ? chunk_stages : 32;
+    int best = 1;
+    double best_cost = 1.0;
+    for (int k = 2; k <= kMaxParts; ++k) {
+        if (n_stages / k < 2 * chunk || R * k > kMaxPieces) break;  // pieces of two chunks at least
+        const double cost = (double)((R * k + n_pairs - 1) / n_pairs) / k;
+        if (cost < best_cost - 1e-9) {
+            best = k;
+            best_cost = cost;
+        }
+    }
+    if (best == 1) return sp;
+    sp.full = F;
+    sp.rem = R;
+    sp.parts = best;
+    return sp;
+}
+
+size_t tc_split_bytes(const TcSplit& sp) {
+    if (sp.parts <= 1) return 0;
+    const size_t partial = (size_t)sp.rem * sp.parts * kTile * kTile * sizeof(double2);
+    return partial + (size_t)sp.rem * 2 * sizeof(int) + 256;
+}
+
+cudaError_t launch_tc_single(const TcTraj& tr, int n_pairs, const TcSplit& sp, int chunk_stages, bool bf16,
+                             double* scratch, void* split_buf, int* err, int64_t timeout_ns, cudaStream_t st) {
     if (tr.n_pad % kBK != 0) return cudaErrorInvalidValue;
+    const int64_t units = tc_units(tr);
+    if (units == 0) return cudaSuccess;
+    if (sp.full * n_pairs + sp.rem != units || sp.parts < 1) return cudaErrorInvalidValue;
     TcArgs a{};
     a.single = tr;
-    a.single_units = tc_units(tr);
+    a.full = sp.full;
+    a.rem = sp.rem;
+    a.parts = sp.parts;
     a.chunk_stages = chunk_stages > 0 ? chunk_stages : 32;
     a.scratch = scratch;
     a.err = err;
     a.timeout_ns = timeout_ns;
-    if (a.single_units == 0) return cudaSuccess;
-    n_pairs = (int)std::min<int64_t>(n_pairs, a.single_units);
+    if (sp.parts > 1) {
+        if (!split_buf) return cudaErrorInvalidValue;
+        a.partial = static_cast<double2*>(split_buf);
+        a.counters = reinterpret_cast<int*>(static_cast<char*>(split_buf) +
+                                            (size_t)sp.rem * sp.parts * kTile * kTile * sizeof(double2));
+        const cudaError_t e = cudaMemsetAsync(a.counters, 0, (size_t)sp.rem * 2 * sizeof(int), st);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t pieces = sp.full * n_pairs + sp.rem * sp.parts;
+    n_pairs = (int)std::min<int64_t>(n_pairs, pieces);
     return launch(a, n_pairs, bf16, st);
 }
 

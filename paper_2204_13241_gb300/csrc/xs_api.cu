@@ -446,6 +446,13 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
     };
     const size_t o_rec = carve((size_t)fchunk * rec_per_frame);
     const size_t o_part = carve(use_tc ? tc_scratch_bytes(tc_pairs) : dplan.partial_bytes);
+    auto split_of = [&](int64_t nf) {
+        return tc_split_plan(tc_units(tc_traj(nullptr, n_pad, nf, g, nullptr, nullptr)), tc_pairs,
+                             (int)(n_pad / tc_atom_multiple()), chunk_stages);
+    };
+    const size_t o_split = carve(use_tc ? std::max(tc_split_bytes(split_of(fchunk)),
+                                                   tc_split_bytes(split_of(T - (T - 1) / fchunk * fchunk)))
+                                        : 0);
     const size_t o_pos0 = carve(pos_host ? (size_t)fchunk * pos_per_frame : 0);
     const size_t o_pos1 = carve(pos_host ? (size_t)fchunk * pos_per_frame : 0);
     const size_t o_f = carve(pos_host ? (size_t)N * sizeof(float) : 0);
@@ -505,9 +512,11 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
             if (pos_host) XS_CUDA(cudaEventRecord(ctx->ev_consumed[c & 1], st));
             if (use_tc) {
                 const TcTraj tr = tc_traj(rec, n_pad, nf, g, Ic, Ac);
+                const TcSplit sp = split_of(nf);
                 XS_CUDA(traced(ctx, "tc", st, [&] {
-                    return launch_tc_single(tr, tc_pairs, chunk_stages, prec == XS_PREC_SPLIT_BF16,
-                                            reinterpret_cast<double*>(ws + o_part), ctx->d_err, ctx->timeout_ns, st);
+                    return launch_tc_single(tr, tc_pairs, sp, chunk_stages, prec == XS_PREC_SPLIT_BF16,
+                                            reinterpret_cast<double*>(ws + o_part), ws + o_split, ctx->d_err,
+                                            ctx->timeout_ns, st);
                 }));
             } else {
                 DirectPlan pc = plan_direct(n_pad, nf, g, ctx->num_sms);
@@ -613,6 +622,20 @@ xs_status xs_intensity_species(xs_context* ctx, const xs_traj* traj, const int32
     };
     const size_t o_rec = carve((size_t)fchunk * n_pad_max * sizeof(AtomRec));
     const size_t o_part = carve(use_tc ? tc_scratch_bytes(tc_pairs) : dmax.partial_bytes);
+    auto split_of = [&](int64_t n_pad, int64_t nf) {
+        return tc_split_plan(tc_units(tc_traj(nullptr, n_pad, nf, g, nullptr, nullptr)), tc_pairs,
+                             (int)(n_pad / tc_atom_multiple()), chunk_stages);
+    };
+    size_t split_bytes = 0;
+    if (use_tc) {
+        for (int sp = 0; sp < n_species; ++sp) {
+            const int64_t ns = start[(size_t)sp + 1] - start[(size_t)sp];
+            if (ns == 0) continue;
+            split_bytes = std::max(split_bytes, tc_split_bytes(split_of(round_up(ns, 64), fchunk)));
+            split_bytes = std::max(split_bytes, tc_split_bytes(split_of(round_up(ns, 64), T - (T - 1) / fchunk * fchunk)));
+        }
+    }
+    const size_t o_split = carve(split_bytes);
     const size_t o_S = carve((size_t)fchunk * P * 2 * sizeof(float));
     const size_t o_I = carve((size_t)fchunk * P * sizeof(float));
     const size_t o_acc = carve((size_t)fchunk * P * 2 * sizeof(double));
@@ -647,9 +670,11 @@ xs_status xs_intensity_species(xs_context* ctx, const xs_traj* traj, const int32
                            [&] { return launch_phase(pos_c, traj->f, ns, nf, n_pad, hm, popt, rec, ctx->d_err, st); }));
             if (use_tc) {
                 const TcTraj tr = tc_traj(rec, n_pad, nf, g, I_tmp, S_tmp);
+                const TcSplit spl = split_of(n_pad, nf);
                 XS_CUDA(traced(ctx, "tc", st, [&] {
-                    return launch_tc_single(tr, tc_pairs, chunk_stages, prec == XS_PREC_SPLIT_BF16,
-                                            reinterpret_cast<double*>(ws + o_part), ctx->d_err, ctx->timeout_ns, st);
+                    return launch_tc_single(tr, tc_pairs, spl, chunk_stages, prec == XS_PREC_SPLIT_BF16,
+                                            reinterpret_cast<double*>(ws + o_part), ws + o_split, ctx->d_err,
+                                            ctx->timeout_ns, st);
                 }));
             } else {
                 const DirectPlan pc = plan_direct(n_pad, nf, g, ctx->num_sms);

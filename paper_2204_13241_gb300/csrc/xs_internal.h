@@ -72,8 +72,17 @@ size_t tc_scratch_bytes(int n_pairs);
 // per-pair unit lists (traj, frame, plane, tile_x | tile_y << 16), longest first
 void tc_build_lists(const std::vector<TcTraj>& trajs, int n_pairs, std::vector<int4>& units,
                     std::vector<int>& pair_start);
-cudaError_t launch_tc_single(const TcTraj& tr, int n_pairs, int chunk_stages, bool bf16, double* scratch, int* err,
-                             int64_t timeout_ns, cudaStream_t st);
+// dealing of a single trajectory's units over the pairs: `full` whole waves,
+// then `rem` units cut into `parts` pieces along the atoms (parts = 1: plain
+// round-robin of all units, full = 0)
+struct TcSplit {
+    int64_t full = 0, rem = 0;
+    int parts = 1;
+};
+TcSplit tc_split_plan(int64_t units, int n_pairs, int n_stages, int chunk_stages);
+size_t tc_split_bytes(const TcSplit& sp);  // partial amplitudes and counters of the pieces
+cudaError_t launch_tc_single(const TcTraj& tr, int n_pairs, const TcSplit& sp, int chunk_stages, bool bf16,
+                             double* scratch, void* split_buf, int* err, int64_t timeout_ns, cudaStream_t st);
 cudaError_t launch_tc_batch(const TcTraj* d_trajs, const int4* d_units, const int* d_pair_start, int n_pairs,
                             int chunk_stages, bool bf16, double* scratch, int* err, int64_t timeout_ns,
                             cudaStream_t st);
