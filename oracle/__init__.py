@@ -11,6 +11,8 @@ What each function follows (arXiv 2204.13241):
   form_factor, amplitude_species, intensity_species
                           Sec. 2.1: per-atom form factors f_i(q), each a sum
                           of Gaussians in |q| for its species.
+  ewald_points            the spherical detector slice |k_f| = |k_i| (Fig. 5,
+                          Sec. 4.5), as reciprocal-lattice points.
   g2                      Sec. 2.3 Eq. g2_def (XPCS autocorrelation).
   ring_index, xsvs_contrast
                           Sec. 2.3 Eqs. inte_Iq and bq_Iq (finite-exposure
@@ -172,6 +174,50 @@ def intensity_species(pos, f, species, coef, box, miller, threads: int = 0) -> n
     """|S|^2 of :func:`amplitude_species`, float64 [T][P]."""
     s = amplitude_species(pos, f, species, coef, box, miller, threads)
     return s.real ** 2 + s.imag ** 2
+
+
+# ----------------------------------------------------------------------------
+# detector pixels on the Ewald sphere
+# ----------------------------------------------------------------------------
+
+def ewald_points(box: np.ndarray, k_in, nx0: int, nx: int, ny0: int, ny: int
+                 ) -> tuple[np.ndarray, np.ndarray]:
+    """Reciprocal-lattice points on the Ewald sphere for a detector window of
+    (n_x, n_y) (the spherical slice of Fig. 5: |k_f| = |k_i| with
+    k_f = k_i + q).  For each (n_x, n_y), q(n_z) = 2 pi h^-T (n_x, n_y, n_z) is
+    a line in n_z; it meets the sphere |q + k_i| = |k_i| at the real roots of
+    |q + k_i|^2 = |k_i|^2.  The root nearer n_z = 0 is kept, and of the two
+    integers around it the one whose q lies closer to the sphere (ties: the
+    smaller |n_z|).  Returns (miller int32 [nx*ny][3], x fastest, and valid
+    bool [nx*ny]; a line that misses the sphere is invalid)."""
+    h = np.asarray(box, dtype=np.float64).reshape(3, 3)
+    Ht = 2.0 * math.pi * np.linalg.inv(h).T          # q = Ht n
+    k = np.asarray(k_in, dtype=np.float64).reshape(3)
+    kk = float(k @ k)
+    yy, xx = np.meshgrid(np.arange(ny0, ny0 + ny), np.arange(nx0, nx0 + nx), indexing="ij")
+    xx, yy = xx.ravel(), yy.ravel()
+    q0 = np.stack([xx, yy, np.zeros_like(xx)], axis=1).astype(np.float64) @ Ht.T
+    d = Ht[:, 2]
+    A = float(d @ d)
+    B = 2.0 * (q0 @ d + float(d @ k))
+    C = (q0 * q0).sum(axis=1) + 2.0 * (q0 @ k)
+    disc = B * B - 4.0 * A * C
+    valid = disc >= 0.0
+    sq = np.sqrt(np.where(valid, disc, 0.0))
+    r1 = (-B + sq) / (2.0 * A)
+    r2 = (-B - sq) / (2.0 * A)
+    root = np.where(np.abs(r1) <= np.abs(r2), r1, r2)
+
+    def dist(nz):
+        q = q0 + nz[:, None] * d[None, :]
+        return np.abs(np.sqrt(((q + k) ** 2).sum(axis=1)) - math.sqrt(kk))
+
+    lo, hi = np.floor(root), np.ceil(root)
+    dl, dh = dist(lo), dist(hi)
+    pick = np.where((dl < dh) | ((dl == dh) & (np.abs(lo) <= np.abs(hi))), lo, hi)
+    nz = np.where(valid, pick, 0.0).astype(np.int64)
+    m = np.stack([xx, yy, nz], axis=1).astype(np.int32)
+    return m, valid
 
 
 # ----------------------------------------------------------------------------
