@@ -132,6 +132,38 @@ XS_API xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, cons
                                void* cuda_stream);
 
 /*
+ * Intensity at an arbitrary list of reciprocal-lattice points n (Miller
+ * indices), I(n,t) = |sum_j f_j exp(+i q.r_j(t))|^2 with q = 2 pi h^-T n (the
+ * same sum as xs_intensity; Sec. 3.1, Algorithm 1 over a pixel set that is not
+ * a box, such as the Ewald-sphere slice of xs_ewald_points).
+ *   XS_PREC_FP32_DIRECT   the FP32 direct kernel on the points
+ *   XS_PREC_SPLIT_*       the points are grouped by n_z; every 128 x 128 tile
+ *                         of a plane's bounding box that holds a point goes
+ *                         through the tensor-core kernel (one batched launch)
+ *                         and the points are gathered from the tiles
+ *   miller   HOST int32 [P][3]
+ *   traj     device positions (pos_on_host = 0)
+ *   I_out    device float32 [T][P]; amp_out device float32 [T][P][2] or NULL
+ * Uses context workspace for the records and, on the tensor path, the tiles.
+ */
+XS_API xs_status xs_intensity_points(xs_context* ctx, const xs_traj* traj, const int32_t* miller, int64_t P,
+                                     xs_precision prec, float* I_out, float* amp_out, void* cuda_stream);
+
+/*
+ * Host-side helper (no GPU work): the detector slice on the Ewald sphere
+ * (Fig. 5: |k_f| = |k_i| with k_f = k_i + q) as reciprocal-lattice points.
+ * For each (n_x, n_y) of the window, q(n_z) = 2 pi h^-T (n_x, n_y, n_z) is a
+ * line that meets the sphere |q + k_in| = |k_in| where A n_z^2 + B n_z + C = 0;
+ * the root nearer n_z = 0 is kept and, of the two integers around it, the one
+ * whose q lies nearer the sphere (ties: the smaller |n_z|).
+ *   k_in        incident wave vector, 1/A (|k_in| = 2 pi / lambda)
+ *   miller_out  HOST int32 [nx*ny][3], x fastest; n_z = 0 where invalid
+ *   valid_out   HOST uint8 [nx*ny] (1: the line meets the sphere), or NULL
+ */
+XS_API xs_status xs_ewald_points(const xs_box* box, const double* k_in, int32_t nx0, int32_t nx, int32_t ny0,
+                                 int32_t ny, int32_t* miller_out, uint8_t* valid_out);
+
+/*
  * Intensity with q-dependent form factors of several atom species (Sec. 2.1:
  * f_i(q), each species' form factor a sum of Gaussians in |q|):
  *   S(q,t) = sum_j f_j F_{s_j}(q) exp(+i q.r_j(t)),   I = |S|^2,

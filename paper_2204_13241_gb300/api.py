@@ -177,6 +177,35 @@ def intensity_species(pos: torch.Tensor, f: torch.Tensor, species, coef, box, gr
     return (out, amp) if want_amp else out
 
 
+def intensity_points(pos: torch.Tensor, f: torch.Tensor, box, miller, precision: str = "fp16",
+                     want_amp: bool = False):
+    """I at arbitrary reciprocal-lattice points `miller` int [P][3] (host),
+    for every frame: returns I [T][P] (and the amplitude [T][P][2])."""
+    tr, host = _traj(pos, f, box)
+    if host:
+        raise ValueError("the point path takes device positions")
+    m = np.ascontiguousarray(np.asarray(miller, dtype=np.int32).reshape(-1, 3))
+    shape = (int(tr.n_frames), m.shape[0])
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    amp = torch.empty(shape + (2,), dtype=torch.float32, device="cuda") if want_amp else None
+    ctx = Context.get()
+    nat.check(ctx.lib.xs_intensity_points(ctx.handle, ctypes.byref(tr), m.ctypes.data_as(ctypes.c_void_p),
+                                          m.shape[0], nat.PRECISIONS[precision], _ptr(out), _ptr(amp), _stream()))
+    return (out, amp) if want_amp else out
+
+
+def ewald_points(box, k_in, nx0: int, nx: int, ny0: int, ny: int):
+    """Reciprocal-lattice points of the Ewald-sphere slice over a detector
+    window (host helper of the library): (miller int32 [nx*ny][3], valid bool)."""
+    b = _box(box)
+    k = np.ascontiguousarray(np.asarray(k_in, dtype=np.float64).reshape(3))
+    m = np.zeros((nx * ny, 3), dtype=np.int32)
+    v = np.zeros(nx * ny, dtype=np.uint8)
+    nat.check(nat.load().xs_ewald_points(ctypes.byref(b), k.ctypes.data_as(ctypes.c_void_p), nx0, nx, ny0, ny,
+                                         m.ctypes.data_as(ctypes.c_void_p), v.ctypes.data_as(ctypes.c_void_p)))
+    return m, v.astype(bool)
+
+
 def intensity_batched(trajs: Sequence[tuple], grids: Sequence, precision: str = "bf16",
                       outs: Optional[Sequence[torch.Tensor]] = None):
     """Many trajectories (pos, f, box) on their own grids in one call."""

@@ -113,10 +113,10 @@ __device__ __forceinline__ void pixel_miller(int64_t p, const GridDesc& g, uint3
 // grid: x = pixel blocks, y = frame, z = atom split
 __global__ void __launch_bounds__(kDirectThreads)
 direct_kernel(const AtomRec* __restrict__ rec, int64_t n_pad, int64_t n_frames, GridDesc g,
-              int64_t atoms_per_split, double2* __restrict__ partial, float* __restrict__ I,
-              float* __restrict__ amp) {
+              const int32_t* __restrict__ pts, int64_t atoms_per_split, double2* __restrict__ partial,
+              float* __restrict__ I, float* __restrict__ amp) {
     __shared__ uint4 s_rec[kAtomTile];
-    const int64_t P = g.pixels();
+    const int64_t P = g.pixels();  // with a point list: nx = the number of points
     const int t = blockIdx.y;
     const int split = blockIdx.z;
     const int64_t a0 = (int64_t)split * atoms_per_split;
@@ -129,7 +129,13 @@ direct_kernel(const AtomRec* __restrict__ rec, int64_t n_pad, int64_t n_frames, 
     for (int i = 0; i < kDirectPX; ++i) {
         pix[i] = ((int64_t)blockIdx.x * kDirectPX + i) * kDirectThreads + threadIdx.x;
         const int64_t pc = pix[i] < P ? pix[i] : P - 1;
-        pixel_miller(pc, g, nx[i], ny[i], nz[i]);
+        if (pts) {
+            nx[i] = (uint32_t)pts[3 * pc];
+            ny[i] = (uint32_t)pts[3 * pc + 1];
+            nz[i] = (uint32_t)pts[3 * pc + 2];
+        } else {
+            pixel_miller(pc, g, nx[i], ny[i], nz[i]);
+        }
     }
     float re[kDirectPX], im[kDirectPX], cre[kDirectPX], cim[kDirectPX];
     double dre[kDirectPX], dim[kDirectPX];
@@ -250,7 +256,7 @@ DirectPlan plan_direct(int64_t n_pad, int64_t n_frames, const GridDesc& g, int n
 
 cudaError_t launch_direct(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g,
                           const DirectPlan& plan, void* partial, float* I, float* amp,
-                          cudaStream_t st) {
+                          cudaStream_t st, const int32_t* pts) {
     const int64_t P = g.pixels();
     if (P == 0 || n_frames == 0) return cudaSuccess;
     const int64_t pix_blocks = (P + kDirectThreads * kDirectPX - 1) / (kDirectThreads * kDirectPX);
@@ -258,7 +264,8 @@ cudaError_t launch_direct(const AtomRec* rec, int64_t n_pad, int64_t n_frames, c
     dim3 grid((unsigned)pix_blocks, (unsigned)n_frames, (unsigned)plan.splits);
     double2* part = plan.splits > 1 ? static_cast<double2*>(partial) : nullptr;
     ++tl_kernel_launches;
-    direct_kernel<<<grid, kDirectThreads, 0, st>>>(rec, n_pad, n_frames, g, plan.atoms_per_split, part, I, amp);
+    direct_kernel<<<grid, kDirectThreads, 0, st>>>(rec, n_pad, n_frames, g, pts, plan.atoms_per_split, part, I,
+                                                   amp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || plan.splits == 1) return e;
     const int64_t items = n_frames * P;

@@ -6,6 +6,8 @@
 //   ff_table_kernel      F_s(|q_p|) for every species and pixel, FP64
 //   species_acc_kernel   acc[t][p] (+)= F_s(q_p) S_s[t][p], FP64 complex
 //   species_finish_kernel I = |acc|^2 and the amplitude, FP32
+// and the gather of arbitrary lattice points out of the planes that hold them
+// (points_gather_kernel).
 #include <cmath>
 
 #include "xs_internal.h"
@@ -67,7 +69,31 @@ __global__ void species_finish_kernel(const double2* __restrict__ acc, int64_t n
     }
 }
 
+// out[t][p] = tmp[src[p] + t * stride[p]] (and the amplitude), one thread per (t, p)
+__global__ void points_gather_kernel(const float* __restrict__ tmp, const float* __restrict__ tmp_amp,
+                                     const int64_t* __restrict__ src, const int64_t* __restrict__ stride,
+                                     int64_t P, int64_t nf, float* __restrict__ I, float* __restrict__ amp) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nf * P) return;
+    const int64_t t = i / P, p = i - t * P;
+    const int64_t o = src[p] + t * stride[p];
+    I[i] = tmp[o];
+    if (amp) {
+        amp[2 * i] = tmp_amp[2 * o];
+        amp[2 * i + 1] = tmp_amp[2 * o + 1];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_points_gather(const float* tmp, const float* tmp_amp, const int64_t* d_src, const int64_t* d_stride,
+                                 int64_t P, int64_t nf, float* I, float* amp, cudaStream_t st) {
+    const int64_t n = nf * P;
+    if (n == 0) return cudaSuccess;
+    ++tl_kernel_launches;
+    points_gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tmp, tmp_amp, d_src, d_stride, P, nf, I, amp);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_ff_table(const double* d_coef, int n_species, const GridDesc& g, const Mat3& hinv, double* table,
                             cudaStream_t st) {

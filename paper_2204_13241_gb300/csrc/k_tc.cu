@@ -883,21 +883,28 @@ size_t tc_scratch_bytes(int n_pairs) { return (size_t)(2 * n_pairs) * 256 * 128 
 
 void tc_build_lists(const std::vector<TcTraj>& trajs, int n_pairs, std::vector<int4>& units,
                     std::vector<int>& pair_start) {
-    // longest-processing-time first: units sorted by cost (stages), each given
-    // to the least loaded pair; ties keep trajectory, frame and tile order
-    struct Item {
-        int64_t cost;
-        int4 u;
-    };
-    std::vector<Item> items;
+    std::vector<int4> all;
     for (size_t i = 0; i < trajs.size(); ++i) {
         const TcTraj& t = trajs[i];
         for (int f = 0; f < t.n_frames; ++f)
             for (int z = 0; z < t.nz; ++z)
                 for (int ty = 0; ty < t.tiles_y; ++ty)
-                    for (int tx = 0; tx < t.tiles_x; ++tx)
-                        items.push_back({t.n_stages, make_int4((int)i, f, z, tx | (ty << 16))});
+                    for (int tx = 0; tx < t.tiles_x; ++tx) all.push_back(make_int4((int)i, f, z, tx | (ty << 16)));
     }
+    tc_deal_units(trajs, all, n_pairs, units, pair_start);
+}
+
+void tc_deal_units(const std::vector<TcTraj>& trajs, const std::vector<int4>& all, int n_pairs,
+                   std::vector<int4>& units, std::vector<int>& pair_start) {
+    // longest-processing-time first: units sorted by cost (stages), each given
+    // to the least loaded pair; ties keep the given order
+    struct Item {
+        int64_t cost;
+        int4 u;
+    };
+    std::vector<Item> items;
+    items.reserve(all.size());
+    for (const int4& u : all) items.push_back({trajs[(size_t)u.x].n_stages, u});
     std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.cost > b.cost; });
     using Load = std::pair<int64_t, int>;
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;

@@ -542,6 +542,236 @@ xs_status xs_intensity(xs_context* ctx, const xs_traj* traj, const xs_qgrid* gri
 }
 
 // --------------------------------------------------------------------------
+// arbitrary lattice points, and the Ewald-sphere detector slice
+// --------------------------------------------------------------------------
+
+xs_status xs_ewald_points(const xs_box* box, const double* k_in, int32_t nx0, int32_t nx, int32_t ny0, int32_t ny,
+                          int32_t* miller_out, uint8_t* valid_out) {
+    if (!box || !k_in || (!miller_out && (int64_t)nx * ny > 0)) return fail(XS_ERR_INVALID_ARG, "missing argument");
+    if (nx < 0 || ny < 0) return fail(XS_ERR_INVALID_ARG, "negative window");
+    double hinv[9];
+    if (!invert3(box->h, hinv)) return fail(XS_ERR_INVALID_ARG, "singular or non-finite cell matrix");
+    const double two_pi = 6.283185307179586476925286766559;
+    // q = Ht n with Ht = 2 pi h^-T: column c of Ht is 2 pi (row c of h^-1)
+    double Ht[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) Ht[a][c] = two_pi * hinv[c * 3 + a];
+    const double k[3] = {k_in[0], k_in[1], k_in[2]};
+    const double kn = std::sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+    if (!(kn > 0.0) || !std::isfinite(kn)) return fail(XS_ERR_INVALID_ARG, "k_in must be finite and non-zero");
+    const double d[3] = {Ht[0][2], Ht[1][2], Ht[2][2]};
+    const double A = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    auto sphere_dist = [&](const double* q0, double nz) {
+        double s2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double v = q0[a] + nz * d[a] + k[a];
+            s2 += v * v;
+        }
+        return std::fabs(std::sqrt(s2) - kn);
+    };
+    int64_t p = 0;
+    for (int32_t iy = 0; iy < ny; ++iy)
+        for (int32_t ix = 0; ix < nx; ++ix, ++p) {
+            const double n0 = (double)(nx0 + ix), n1 = (double)(ny0 + iy);
+            double q0[3];
+            for (int a = 0; a < 3; ++a) q0[a] = Ht[a][0] * n0 + Ht[a][1] * n1;
+            // |q0 + n d + k|^2 = |k|^2:  A n^2 + B n + C = 0
+            const double B = 2.0 * (q0[0] * d[0] + q0[1] * d[1] + q0[2] * d[2] + d[0] * k[0] + d[1] * k[1] + d[2] * k[2]);
+            const double C = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2] + 2.0 * (q0[0] * k[0] + q0[1] * k[1] + q0[2] * k[2]);
+            const double disc = B * B - 4.0 * A * C;
+            int64_t nz = 0;
+            const bool ok = disc >= 0.0;
+            if (ok) {
+                const double sq = std::sqrt(disc);
+                const double r1 = (-B + sq) / (2.0 * A), r2 = (-B - sq) / (2.0 * A);
+                const double root = std::fabs(r1) <= std::fabs(r2) ? r1 : r2;
+                const double lo = std::floor(root), hi = std::ceil(root);
+                const double dl = sphere_dist(q0, lo), dh = sphere_dist(q0, hi);
+                nz = (int64_t)((dl < dh || (dl == dh && std::fabs(lo) <= std::fabs(hi))) ? lo : hi);
+                if (nz < INT32_MIN || nz > INT32_MAX) return fail(XS_ERR_INVALID_ARG, "n_z out of the int32 range");
+            }
+            miller_out[3 * p] = nx0 + ix;
+            miller_out[3 * p + 1] = ny0 + iy;
+            miller_out[3 * p + 2] = ok ? (int32_t)nz : 0;
+            if (valid_out) valid_out[p] = ok ? 1 : 0;
+        }
+    return XS_OK;
+}
+
+xs_status xs_intensity_points(xs_context* ctx, const xs_traj* traj, const int32_t* miller, int64_t P,
+                              xs_precision prec, float* I_out, float* amp_out, void* cuda_stream) {
+    if (!ctx || !traj || (P > 0 && (!miller || !I_out))) return fail(XS_ERR_INVALID_ARG, "missing argument");
+    if (prec != XS_PREC_FP32_DIRECT && prec != XS_PREC_SPLIT_FP16 && prec != XS_PREC_SPLIT_BF16)
+        return fail(XS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (P < 0 || P > INT32_MAX) return fail(XS_ERR_INVALID_ARG, "point count outside [0, 2^31)");
+    if (traj->n_atoms < 0 || traj->n_frames < 0) return fail(XS_ERR_INVALID_ARG, "negative atom or frame count");
+    if (traj->n_atoms > (int64_t)1 << 31) return fail(XS_ERR_INVALID_ARG, "more than 2^31 atoms");
+    if (traj->pos_on_host) return fail(XS_ERR_INVALID_ARG, "the point path takes device positions");
+    if (traj->n_atoms > 0 && traj->n_frames > 0 && (!traj->pos || !traj->f))
+        return fail(XS_ERR_INVALID_ARG, "positions or form factors are NULL");
+    double hinv[9];
+    if (!invert3(traj->box.h, hinv)) return fail(XS_ERR_INVALID_ARG, "singular or non-finite cell matrix");
+    const int64_t T = traj->n_frames, N = traj->n_atoms;
+    if (P == 0 || T == 0) return XS_OK;
+    if (!is_device_ptr(I_out) || (amp_out && !is_device_ptr(amp_out)))
+        return fail(XS_ERR_INVALID_ARG, "the point path writes device outputs");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (N == 0) {
+        XS_CUDA(cudaMemsetAsync(I_out, 0, (size_t)T * P * sizeof(float), st));
+        if (amp_out) XS_CUDA(cudaMemsetAsync(amp_out, 0, (size_t)T * P * 2 * sizeof(float), st));
+        return XS_OK;
+    }
+    const bool use_tc = prec != XS_PREC_FP32_DIRECT;
+    const int64_t n_pad = round_up(N, 64);
+    Mat3 hm;
+    for (int i = 0; i < 9; ++i) hm.a[i] = hinv[i];
+    PhaseOpts popt;
+    popt.ortho = is_ortho(hinv);
+    popt.need_z = false;
+    for (int64_t p = 0; p < P; ++p)
+        if (miller[3 * p + 2] != 0) popt.need_z = true;
+    popt.perm_mul = use_tc ? coprime_stride(n_pad) : 1;
+
+    // tensor cores: the points grouped by n_z plane, each plane's bounding box
+    // tiled; only tiles that hold a point are computed
+    struct Plane {
+        int32_t z, x0, x1, y0, y1;
+        int64_t off;  // offset of the plane's box in a frame of the temporary buffer
+    };
+    std::vector<Plane> planes;
+    std::vector<int32_t> plane_of((size_t)P);
+    int64_t per_frame = 0;
+    if (use_tc) {
+        std::map<int32_t, size_t> index;
+        for (int64_t p = 0; p < P; ++p) {
+            const int32_t x = miller[3 * p], y = miller[3 * p + 1], z = miller[3 * p + 2];
+            auto it = index.find(z);
+            if (it == index.end()) {
+                it = index.emplace(z, planes.size()).first;
+                planes.push_back(Plane{z, x, x, y, y, 0});
+            }
+            Plane& pl = planes[it->second];
+            pl.x0 = std::min(pl.x0, x);
+            pl.x1 = std::max(pl.x1, x);
+            pl.y0 = std::min(pl.y0, y);
+            pl.y1 = std::max(pl.y1, y);
+            plane_of[(size_t)p] = (int32_t)it->second;
+        }
+        for (Plane& pl : planes) {
+            pl.off = per_frame;
+            per_frame += (int64_t)(pl.x1 - pl.x0 + 1) * (pl.y1 - pl.y0 + 1);
+        }
+    }
+    // frames per chunk
+    const size_t bytes_frame = (size_t)n_pad * sizeof(AtomRec) +
+                               (size_t)per_frame * (sizeof(float) + (amp_out ? 2 * sizeof(float) : 0));
+    int64_t fchunk = std::max<int64_t>(1, std::min<int64_t>(T, (int64_t)(((size_t)4 << 30) / bytes_frame)));
+    if (fchunk > 65535) fchunk = 65535;
+    const GridDesc gpts{0, (int32_t)P, 0, 1, 0, 1};
+    int tc_pairs = 0;
+    DirectPlan dplan{};
+    if (use_tc)
+        tc_pairs = tc_pair_capacity(ctx->num_sms);
+    else
+        dplan = plan_direct(n_pad, fchunk, gpts, ctx->num_sms);
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        size_t o = round_up((int64_t)off, 256);
+        off = o + bytes;
+        return o;
+    };
+    const size_t o_rec = carve((size_t)fchunk * n_pad * sizeof(AtomRec));
+    const size_t o_part = carve(use_tc ? tc_scratch_bytes(tc_pairs) : dplan.partial_bytes);
+    const size_t o_tmp = carve(use_tc ? (size_t)fchunk * per_frame * sizeof(float) : 0);
+    const size_t o_tamp = carve(use_tc && amp_out ? (size_t)fchunk * per_frame * 2 * sizeof(float) : 0);
+    xs_status s = ensure_ws(ctx, off + 256);
+    if (s != XS_OK) return s;
+    char* ws = static_cast<char*>(ctx->ws);
+    AtomRec* rec = reinterpret_cast<AtomRec*>(ws + o_rec);
+
+    for (int64_t t0 = 0; t0 < T; t0 += fchunk) {
+        const int64_t nf = std::min(fchunk, T - t0);
+        const float* pos_c = traj->pos + (size_t)t0 * N * 3;
+        XS_CUDA(traced(ctx, "phase", st,
+                       [&] { return launch_phase(pos_c, traj->f, N, nf, n_pad, hm, popt, rec, ctx->d_err, st); }));
+        float* Ic = I_out + (size_t)t0 * P;
+        float* Ac = amp_out ? amp_out + (size_t)t0 * P * 2 : nullptr;
+        if (!use_tc) {
+            std::vector<char> blob;
+            const size_t o_pts = push(blob, miller, (size_t)P * 3);
+            void* d = nullptr;
+            s = upload_const(ctx, "points", blob, st, &d);
+            if (s != XS_OK) return s;
+            const int32_t* d_pts = reinterpret_cast<const int32_t*>(static_cast<char*>(d) + o_pts);
+            const DirectPlan pc = plan_direct(n_pad, nf, gpts, ctx->num_sms);
+            XS_CUDA(traced(ctx, "direct", st,
+                           [&] { return launch_direct(rec, n_pad, nf, gpts, pc, ws + o_part, Ic, Ac, st, d_pts); }));
+            continue;
+        }
+        float* tmp = reinterpret_cast<float*>(ws + o_tmp);
+        float* tamp = amp_out ? reinterpret_cast<float*>(ws + o_tamp) : nullptr;
+        std::vector<TcTraj> trs;
+        for (const Plane& pl : planes) {
+            GridDesc g{pl.x0, pl.x1 - pl.x0 + 1, pl.y0, pl.y1 - pl.y0 + 1, pl.z, 1};
+            TcTraj tr = tc_traj(rec, n_pad, nf, g, nullptr, nullptr);
+            // each plane writes its own [nf][box] block of the temporary buffer
+            tr.I = tmp + (size_t)nf * pl.off;
+            tr.amp = tamp ? tamp + (size_t)nf * pl.off * 2 : nullptr;
+            trs.push_back(tr);
+        }
+        // occupied tiles, once per frame
+        std::vector<int4> occupied;
+        {
+            std::vector<std::vector<uint8_t>> used(planes.size());
+            for (size_t i = 0; i < planes.size(); ++i) used[i].assign((size_t)trs[i].tiles_x * trs[i].tiles_y, 0);
+            for (int64_t p = 0; p < P; ++p) {
+                const size_t i = (size_t)plane_of[(size_t)p];
+                const int tx = (miller[3 * p] - planes[i].x0) / 128, ty = (miller[3 * p + 1] - planes[i].y0) / 128;
+                used[i][(size_t)ty * trs[i].tiles_x + tx] = 1;
+            }
+            for (int64_t f = 0; f < nf; ++f)
+                for (size_t i = 0; i < planes.size(); ++i)
+                    for (int ty = 0; ty < trs[i].tiles_y; ++ty)
+                        for (int tx = 0; tx < trs[i].tiles_x; ++tx)
+                            if (used[i][(size_t)ty * trs[i].tiles_x + tx])
+                                occupied.push_back(make_int4((int)i, (int)f, 0, tx | (ty << 16)));
+        }
+        const int n_pairs = (int)std::min<int64_t>(tc_pairs, (int64_t)occupied.size());
+        std::vector<int4> units;
+        std::vector<int> pair_start;
+        tc_deal_units(trs, occupied, n_pairs, units, pair_start);
+        // gather map: frame-0 offset and frame stride of every point
+        std::vector<int64_t> src((size_t)P), stride((size_t)P);
+        for (int64_t p = 0; p < P; ++p) {
+            const Plane& pl = planes[(size_t)plane_of[(size_t)p]];
+            const int64_t w = pl.x1 - pl.x0 + 1, area = w * (pl.y1 - pl.y0 + 1);
+            src[(size_t)p] = nf * pl.off + (int64_t)(miller[3 * p + 1] - pl.y0) * w + (miller[3 * p] - pl.x0);
+            stride[(size_t)p] = area;
+        }
+        std::vector<char> blob;
+        const size_t o_tr = push(blob, trs.data(), trs.size());
+        const size_t o_units = push(blob, units.data(), units.size());
+        const size_t o_ps = push(blob, pair_start.data(), pair_start.size());
+        const size_t o_src = push(blob, src.data(), src.size());
+        const size_t o_stride = push(blob, stride.data(), stride.size());
+        void* d = nullptr;
+        s = upload_const(ctx, "points_tc", blob, st, &d);
+        if (s != XS_OK) return s;
+        char* dc = static_cast<char*>(d);
+        XS_CUDA(traced(ctx, "tc", st, [&] {
+            return launch_tc_batch(reinterpret_cast<const TcTraj*>(dc + o_tr), reinterpret_cast<const int4*>(dc + o_units),
+                                   reinterpret_cast<const int*>(dc + o_ps), n_pairs, 32, prec == XS_PREC_SPLIT_BF16,
+                                   reinterpret_cast<double*>(ws + o_part), ctx->d_err, ctx->timeout_ns, st);
+        }));
+        XS_CUDA(traced(ctx, "points", st, [&] {
+            return launch_points_gather(tmp, tamp, reinterpret_cast<const int64_t*>(dc + o_src),
+                                        reinterpret_cast<const int64_t*>(dc + o_stride), P, nf, Ic, Ac, st);
+        }));
+    }
+    return XS_OK;
+}
+
+// --------------------------------------------------------------------------
 // several species with q-dependent form factors
 // --------------------------------------------------------------------------
 

@@ -46,9 +46,11 @@ struct DirectPlan {
     size_t partial_bytes;  // workspace for the partial amplitudes
 };
 DirectPlan plan_direct(int64_t n_pad, int64_t n_frames, const GridDesc& g, int num_sms);
+// pts (optional, device int32 [P][3]): Miller indices of P arbitrary points;
+// g then only gives P as g.nx with ny = nz = 1
 cudaError_t launch_direct(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g,
                           const DirectPlan& plan, void* partial, float* I, float* amp,
-                          cudaStream_t st);
+                          cudaStream_t st, const int32_t* pts = nullptr);
 
 // ---- tensor-core split-precision contraction ----------------------------
 // One trajectory of a launch: phase records [n_frames][n_pad] (slot order of
@@ -70,6 +72,9 @@ TcTraj tc_traj(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDe
 int64_t tc_units(const TcTraj& t);  // frames x planes x tiles
 size_t tc_scratch_bytes(int n_pairs);
 // per-pair unit lists (traj, frame, plane, tile_x | tile_y << 16), longest first
+// longest-processing-time dealing of explicit units (traj, frame, plane, tile_x | tile_y << 16)
+void tc_deal_units(const std::vector<TcTraj>& trajs, const std::vector<int4>& all, int n_pairs,
+                   std::vector<int4>& units, std::vector<int>& pair_start);
 void tc_build_lists(const std::vector<TcTraj>& trajs, int n_pairs, std::vector<int4>& units,
                     std::vector<int>& pair_start);
 // dealing of a single trajectory's units over the pairs: `full` whole waves,
@@ -97,6 +102,8 @@ struct XsvsLayout {
     int n_chunks;         // (ring, pixel range) chunks
     int64_t n_kw;         // sum over K of floor(T/K)
 };
+cudaError_t launch_points_gather(const float* tmp, const float* tmp_amp, const int64_t* d_src, const int64_t* d_stride,
+                                 int64_t P, int64_t nf, float* I, float* amp, cudaStream_t st);
 cudaError_t launch_ff_table(const double* d_coef, int n_species, const GridDesc& g, const Mat3& hinv, double* table,
                             cudaStream_t st);
 cudaError_t launch_species_acc(const float* S, const double* ff, int64_t nf, int64_t P, bool first, double* acc,

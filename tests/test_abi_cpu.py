@@ -101,3 +101,17 @@ def test_triclinic_ring_layout_matches_oracle(lib):
     assert lib.xs_ring_index(ctypes.byref(g), ctypes.byref(b), 1.0, 9, out.ctypes.data_as(ctypes.c_void_p)) == 0
     ref = oracle.ring_index(box, grid.miller(), 1.0, 9)
     assert np.array_equal(out, ref)
+
+
+def test_ewald_points_host_helper_matches_oracle():
+    # host-side library helper (no GPU work) against the oracle's selection
+    import math
+    from paper_2204_13241_gb300 import api as xs
+    cases = [(np.eye(3) * 40.0, [0.0, 0.0, 2 * math.pi / 1.3], (-40, 80, -36, 72)),
+             (np.array([[30.0, 4.0, -2.0], [0.0, 27.0, 3.0], [0.0, 0.0, 33.0]]), [0.3, -0.2, 8.0], (-20, 40, -24, 48)),
+             (np.eye(3) * 25.0, [1.0, 0.0, 0.0], (-8, 16, -8, 16))]
+    for box, k, win in cases:
+        m1, v1 = xs.ewald_points(box, k, *win)
+        m2, v2 = oracle.ewald_points(box, k, *win)
+        assert np.array_equal(v1, v2)
+        assert np.array_equal(m1[v1], m2[v2])
