@@ -36,12 +36,12 @@ import numpy as np  # noqa: E402
 METRIC = "atom*pixel*frames/s"
 FALLBACK_PEAK = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0}
 
-# DRAM bytes (read + write) of one tc_kernel launch per frame of the 256,000-atom
-# workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
-# of a 160-frame launch of this exact kernel source: 656.25 MB + 11.98 MB.
-# The records streamed are proportional to the frames, so a launch over T
-# frames moves T times this.  Reported only while k_tc.cu is unchanged.
-TC_TRAFFIC = {"k_tc_sha256_prefix": "22ff0289144ae001", "bytes_per_frame": (656.251904e6 + 11.979264e6) / 160}
+# DRAM bytes (read + write) of one tc_kernel launch of the 1,000-frame
+# workload, from an ncu capture of that launch (dram__bytes_read.sum +
+# dram__bytes_write.sum, one pass): 4.11 GB + 101.5 MB.  Reported only while
+# k_tc.cu is unchanged; other frame counts scale it by frames (records and
+# outputs are per frame; the split-piece partials are not, a few percent).
+TC_TRAFFIC = {"k_tc_sha256_prefix": "940e85acb2178a66", "bytes": 4.11e9 + 101.5e6, "frames": 1000}
 
 
 def _args():
@@ -68,7 +68,7 @@ def _tc_traffic(frames: int):
         return None
     if not sha.startswith(TC_TRAFFIC["k_tc_sha256_prefix"]):
         return None
-    return TC_TRAFFIC["bytes_per_frame"] * frames
+    return TC_TRAFFIC["bytes"] * frames / TC_TRAFFIC["frames"]
 
 
 def _peaks():
@@ -287,7 +287,7 @@ def run_ours(args):
     achieved = alg_flops / (tc_launch_ms * 1e-3) / 1e12
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": _tc_traffic(T),
-                "traffic_note": "ncu DRAM bytes of a 160-frame capture scaled by frames; "
+                "traffic_note": "ncu DRAM bytes (read + write) of the 1,000-frame launch; "
                                 "algorithmic bytes per launch = T x (N x 16 B records + P x 4 B)",
                 "algorithmic_bytes": float(T) * (N * 16.0 + P * 4.0),
                 "kernel": "tc_kernel (split-FP16 contraction)", "kernel_ms_per_launch": tc_launch_ms,
