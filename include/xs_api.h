@@ -132,6 +132,25 @@ XS_API xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, cons
                                void* cuda_stream);
 
 /*
+ * The paper's FFT-based method (Sec. 3.2, Algorithm 2), as a cross-check of the
+ * direct method: each atom's Gaussian (standard deviation eta, in A) is added
+ * on the k nearest grid points per axis of an n_grid^3 grid over the
+ * orthorhombic cell (periodic), the grid is Fourier transformed (FFT kernels
+ * of this library, FP64), and p^eta is divided by the transform of one
+ * truncated Gaussian at the origin; I = |p^e|^2 on `grid`.  The method's own
+ * errors (grid aliasing, cut-off) are small when eta spans about two grid
+ * steps and the cut-off +-5 eta.
+ *   n_grid   power of two in [8, 1024]; Miller indices of `grid` must lie in
+ *            [-n_grid/2, n_grid/2)
+ *   k_cut    grid points per axis around each atom (<= 64), or <= 0 for the
+ *            smallest integer above 10 eta in grid steps
+ *   I_out    device float32 [T][nz][ny][nx]; amp_out device [...][2] or NULL
+ * Uses n_grid^3 complex FP64 of context workspace; frames run one by one.
+ */
+XS_API xs_status xs_intensity_fft(xs_context* ctx, const xs_traj* traj, int32_t n_grid, double eta, int32_t k_cut,
+                                  const xs_qgrid* grid, float* I_out, float* amp_out, void* cuda_stream);
+
+/*
  * Intensity at an arbitrary list of reciprocal-lattice points n (Miller
  * indices), I(n,t) = |sum_j f_j exp(+i q.r_j(t))|^2 with q = 2 pi h^-T n (the
  * same sum as xs_intensity; Sec. 3.1, Algorithm 1 over a pixel set that is not

@@ -194,6 +194,23 @@ def intensity_points(pos: torch.Tensor, f: torch.Tensor, box, miller, precision:
     return (out, amp) if want_amp else out
 
 
+def intensity_fft(pos: torch.Tensor, f: torch.Tensor, box, grid, n_grid: int, eta: float, k_cut: int = 0,
+                  want_amp: bool = False):
+    """I by the FFT-based method (Sec. 3.2, Algorithm 2) on an n_grid^3 grid,
+    reported on `grid`; a cross-check of the direct method."""
+    tr, host = _traj(pos, f, box)
+    if host:
+        raise ValueError("the FFT path takes device positions")
+    g = _grid(grid)
+    shape = (int(tr.n_frames), g.nz, g.ny, g.nx)
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    amp = torch.empty(shape + (2,), dtype=torch.float32, device="cuda") if want_amp else None
+    ctx = Context.get()
+    nat.check(ctx.lib.xs_intensity_fft(ctx.handle, ctypes.byref(tr), int(n_grid), float(eta), int(k_cut),
+                                       ctypes.byref(g), out.data_ptr(), _ptr(amp), _stream()))
+    return (out, amp) if want_amp else out
+
+
 def ewald_points(box, k_in, nx0: int, nx: int, ny0: int, ny: int):
     """Reciprocal-lattice points of the Ewald-sphere slice over a detector
     window (host helper of the library): (miller int32 [nx*ny][3], valid bool)."""

@@ -67,8 +67,24 @@ phase_kernel(const float* __restrict__ pos, const float* __restrict__ f, int64_t
         r.ux = r.uy = r.uz = 0u;
         r.f = 0.0f;
         if (real) {
-            const float* p = pos + (t * stride + a) * 3;
-            const float x = p[0], y = p[1], z = p[2];
+            const int64_t idx = t * stride + a;
+            const float* p = pos + idx * 3;
+            float x, y, z;
+            if (opt.pos8) {
+                // with `pos` 8-byte aligned, the 12-byte position is one aligned
+                // 8-byte load and one 4-byte load: (x, y) + z at an even index,
+                // x + (y, z) at an odd one
+                const int odd = (int)(idx & 1);
+                const float2 v2 = *reinterpret_cast<const float2*>(p + odd);
+                const float v1 = p[odd ? 0 : 2];
+                x = odd ? v1 : v2.x;
+                y = odd ? v2.x : v2.y;
+                z = odd ? v2.y : v1;
+            } else {
+                x = p[0];
+                y = p[1];
+                z = p[2];
+            }
             // NaN and Inf fail these comparisons too
             bool ok = isfinite(fj);
             if (opt.ortho) {
@@ -221,6 +237,7 @@ cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int6
     Mat3 hs;
     for (int i = 0; i < 9; ++i) hs.a[i] = hinv.a[i] * 4294967296.0;
     PhaseOpts o = opt;
+    o.pos8 = ((uintptr_t)pos & 7u) == 0;
     // atom of slot k = k * a mod n_pad; the products stay below 2^64
     if (o.perm_mul != 1 && n_pad >= ((int64_t)1 << 32)) return cudaErrorInvalidValue;
     // orthorhombic cells: |x| < lim_x keeps |hs_xx x| below 2^50 (the FP32

@@ -102,7 +102,6 @@ struct TcArgs {
     int chunk_stages;
     double* scratch;        // [gridDim.x][256][128] running totals as FP32 pairs (hi, lo)
     double2* partial;       // split units: [rem][parts][128 x][128 y] partial amplitudes
-    int* counters;          // split units: [rem][2] finished epilogue warps per CTA half (start at 0)
     int* err;
     int64_t timeout_ns;
 };
@@ -404,29 +403,29 @@ __device__ __forceinline__ int64_t units_of_pair(const TcArgs& a, int64_t pair, 
     return a.pair_start[pair + 1] - a.pair_start[pair];
 }
 
-// Sum of the pieces of a split unit for the rows of CTA half `rank` (64 x
-// slots by 128 y), in part order, and I = |S|^2; one warp.
-__device__ __noinline__ void finish_split(const TcArgs& a, const Unit& up, int rank, int lane) {
-    const double2* base = a.partial + (size_t)up.split * a.parts * (kTile * kTile);
-    for (int idx = lane; idx < kHalf * kTile; idx += 32) {
-        const int x_slot = idx / kTile, yi = idx - x_slot * kTile;
-        float f;
-        const int xi = up.centred ? centred_index(x_slot, rank, f) : kHalf * rank + x_slot;
-        double re = 0.0, im = 0.0;
-        for (int q = 0; q < a.parts; ++q) {
-            const double2 v = __ldcg(base + (size_t)q * (kTile * kTile) + (size_t)xi * kTile + yi);
-            re += v.x;
-            im += v.y;
-        }
-        const int ix = up.tx * kTile + xi, iy = up.ty * kTile + yi;
-        if (ix < up.nx && iy < up.ny) {
-            const int64_t o = (((int64_t)up.t * up.nz + up.iz) * up.ny + iy) * up.nx + ix;
-            up.I[o] = (float)(re * re + im * im);
-            if (up.amp) {
-                up.amp[2 * o] = (float)re;
-                up.amp[2 * o + 1] = (float)im;
-            }
-        }
+// Pieces of the split units of a single-trajectory launch: one thread per
+// pixel of the tile sums the parts' FP64 partial amplitudes in part order and
+// writes I (and the amplitude).  Runs after tc_kernel on the same stream.
+__global__ void split_finish_kernel(TcArgs a, int64_t n_pairs) {
+    const int64_t r = blockIdx.y;  // split unit
+    const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= kTile * kTile) return;
+    const int xi = pix / kTile, yi = pix - xi * kTile;
+    const Unit up = single_unit(a.single, a.full * n_pairs + r);
+    const int ix = up.tx * kTile + xi, iy = up.ty * kTile + yi;
+    if (ix >= up.nx || iy >= up.ny) return;
+    const double2* base = a.partial + (size_t)r * a.parts * (kTile * kTile) + pix;
+    double re = 0.0, im = 0.0;
+    for (int q = 0; q < a.parts; ++q) {
+        const double2 v = base[(size_t)q * (kTile * kTile)];
+        re += v.x;
+        im += v.y;
+    }
+    const int64_t o = (((int64_t)up.t * up.nz + up.iz) * up.ny + iy) * up.nx + ix;
+    up.I[o] = (float)(re * re + im * im);
+    if (up.amp) {
+        up.amp[2 * o] = (float)re;
+        up.amp[2 * o + 1] = (float)im;
     }
 }
 
@@ -797,21 +796,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive_cluster(acc_empty_c0 + (uint32_t)b * 8u);
-                if (last && up.split >= 0) {
-                    // the last of the 4 x parts epilogue warps to finish this CTA's
-                    // half of a split unit adds the pieces in part order
-                    __threadfence();
-                    __syncwarp();
-                    int done = 0;
-                    if (lane == 0) done = atomicAdd(&args.counters[up.split * 2 + (int)rank], 1);
-                    done = __shfl_sync(0xffffffffu, done, 0);
-                    if (done == kEpiWarps * args.parts - 1) {
-                        __threadfence();
-                        finish_split(args, up, (int)rank, lane);
-                        __syncwarp();
-                        if (lane == 0) args.counters[up.split * 2 + (int)rank] = 0;
-                    }
-                }
             }
         }
     }
@@ -970,8 +954,7 @@ TcSplit tc_split_plan(int64_t units, int n_pairs, int n_stages, int chunk_stages
 
 size_t tc_split_bytes(const TcSplit& sp) {
     if (sp.parts <= 1) return 0;
-    const size_t partial = (size_t)sp.rem * sp.parts * kTile * kTile * sizeof(double2);
-    return partial + (size_t)sp.rem * 2 * sizeof(int) + 256;
+    return (size_t)sp.rem * sp.parts * kTile * kTile * sizeof(double2);
 }
 
 cudaError_t launch_tc_single(const TcTraj& tr, int n_pairs, const TcSplit& sp, int chunk_stages, bool bf16,
@@ -992,14 +975,27 @@ cudaError_t launch_tc_single(const TcTraj& tr, int n_pairs, const TcSplit& sp, i
     if (sp.parts > 1) {
         if (!split_buf) return cudaErrorInvalidValue;
         a.partial = static_cast<double2*>(split_buf);
-        a.counters = reinterpret_cast<int*>(static_cast<char*>(split_buf) +
-                                            (size_t)sp.rem * sp.parts * kTile * kTile * sizeof(double2));
-        const cudaError_t e = cudaMemsetAsync(a.counters, 0, (size_t)sp.rem * 2 * sizeof(int), st);
-        if (e != cudaSuccess) return e;
     }
     const int64_t pieces = sp.full * n_pairs + sp.rem * sp.parts;
     n_pairs = (int)std::min<int64_t>(n_pairs, pieces);
     return launch(a, n_pairs, bf16, st);
+}
+
+cudaError_t launch_tc_split_finish(const TcTraj& tr, int n_pairs, const TcSplit& sp, void* split_buf,
+                                   cudaStream_t st) {
+    if (sp.parts <= 1 || sp.rem == 0) return cudaSuccess;
+    if (!split_buf) return cudaErrorInvalidValue;
+    TcArgs a{};
+    a.single = tr;
+    a.full = sp.full;
+    a.rem = sp.rem;
+    a.parts = sp.parts;
+    a.partial = static_cast<double2*>(split_buf);
+    const int64_t pieces = sp.full * n_pairs + sp.rem * sp.parts;
+    n_pairs = (int)std::min<int64_t>(n_pairs, pieces);  // as in launch_tc_single
+    ++tl_kernel_launches;
+    split_finish_kernel<<<dim3(kTile * kTile / 256, (unsigned)sp.rem), 256, 0, st>>>(a, n_pairs);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tc_batch(const TcTraj* d_trajs, const int4* d_units, const int* d_pair_start, int n_pairs,

@@ -518,6 +518,8 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
                                             reinterpret_cast<double*>(ws + o_part), ws + o_split, ctx->d_err,
                                             ctx->timeout_ns, st);
                 }));
+                XS_CUDA(traced(ctx, "split_finish", st,
+                               [&] { return launch_tc_split_finish(tr, tc_pairs, sp, ws + o_split, st); }));
             } else {
                 DirectPlan pc = plan_direct(n_pad, nf, g, ctx->num_sms);
                 if (pc.partial_bytes > dplan.partial_bytes) return fail(XS_ERR_CUDA, "internal: partial plan grew");
@@ -539,6 +541,87 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
 xs_status xs_intensity(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, xs_precision prec,
                        float* I_out, float* amp_out, void* cuda_stream) {
     return intensity_impl(ctx, traj, grid, prec, I_out, amp_out, static_cast<cudaStream_t>(cuda_stream), 0);
+}
+
+// --------------------------------------------------------------------------
+// the FFT-based method (Algorithm 2), a cross-check
+// --------------------------------------------------------------------------
+
+xs_status xs_intensity_fft(xs_context* ctx, const xs_traj* traj, int32_t n_grid, double eta, int32_t k_cut,
+                           const xs_qgrid* grid, float* I_out, float* amp_out, void* cuda_stream) {
+    if (!ctx || !traj || !I_out) return fail(XS_ERR_INVALID_ARG, "context, trajectory and I_out are required");
+    xs_status s = check_grid(grid);
+    if (s != XS_OK) return s;
+    if (n_grid < 8 || n_grid > 1024 || (n_grid & (n_grid - 1)) != 0)
+        return fail(XS_ERR_INVALID_ARG, "n_grid must be a power of two in [8, 1024]");
+    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(XS_ERR_INVALID_ARG, "eta must be finite and > 0");
+    if (traj->n_atoms < 0 || traj->n_frames < 0) return fail(XS_ERR_INVALID_ARG, "negative atom or frame count");
+    if (traj->pos_on_host) return fail(XS_ERR_INVALID_ARG, "the FFT path takes device positions");
+    if (traj->n_atoms > 0 && traj->n_frames > 0 && (!traj->pos || !traj->f))
+        return fail(XS_ERR_INVALID_ARG, "positions or form factors are NULL");
+    const double* h = traj->box.h;
+    if (h[1] != 0.0 || h[2] != 0.0 || h[3] != 0.0 || h[5] != 0.0 || h[6] != 0.0 || h[7] != 0.0 ||
+        !(h[0] > 0.0) || !(h[4] > 0.0) || !(h[8] > 0.0))
+        return fail(XS_ERR_UNSUPPORTED, "the FFT path takes an orthorhombic cell");
+    const int half = n_grid / 2;
+    if (grid->nx0 < -half || grid->nx0 + grid->nx > half || grid->ny0 < -half || grid->ny0 + grid->ny > half ||
+        grid->nz0 < -half || grid->nz0 + grid->nz > half)
+        return fail(XS_ERR_INVALID_ARG, "Miller indices outside [-n_grid/2, n_grid/2) of the FFT grid");
+    const GridDesc g = to_desc(grid);
+    const int64_t P = g.pixels(), T = traj->n_frames, N = traj->n_atoms;
+    if (P == 0 || T == 0) return XS_OK;
+    if (!is_device_ptr(I_out) || (amp_out && !is_device_ptr(amp_out)))
+        return fail(XS_ERR_INVALID_ARG, "the FFT path writes device outputs");
+    FftGrid fg;
+    fg.n = n_grid;
+    fg.inv_2eta2 = 1.0 / (2.0 * eta * eta);
+    const double Ls[3] = {h[0], h[4], h[8]};
+    for (int a = 0; a < 3; ++a) {
+        fg.h[a] = Ls[a] / n_grid;
+        // k <= 0: the smallest integer above 10 eta in grid steps (+-5 eta)
+        fg.k[a] = k_cut > 0 ? k_cut : (int)std::floor(10.0 * eta / fg.h[a]) + 1;
+        if (fg.k[a] > 64 || fg.k[a] > n_grid)
+            return fail(XS_ERR_INVALID_ARG, "Gaussian cut-off of %d grid points above min(64, n_grid)", fg.k[a]);
+    }
+    // G_a(m) = sum_j w_j exp(-2 pi i m x_j / n) of the truncated Gaussian at the origin
+    std::vector<double> G((size_t)3 * n_grid * 2);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int a = 0; a < 3; ++a) {
+        const int64_t s0 = (int64_t)std::ceil(-0.5 * fg.k[a]);
+        for (int m = 0; m < n_grid; ++m) {
+            double re = 0.0, im = 0.0;
+            for (int j = 0; j < fg.k[a]; ++j) {
+                const int64_t idx = s0 + j;
+                const double d = (double)idx * fg.h[a];
+                const double w = std::exp(-d * d / (2.0 * eta * eta));
+                const int64_t e = ((idx % n_grid) + n_grid) % n_grid;
+                const double ang = -two_pi * (double)((m * e) % n_grid) / n_grid;
+                re += w * std::cos(ang);
+                im += w * std::sin(ang);
+            }
+            G[((size_t)a * n_grid + m) * 2] = re;
+            G[((size_t)a * n_grid + m) * 2 + 1] = im;
+        }
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<char> blob;
+    const size_t o_G = push(blob, G.data(), G.size());
+    void* d = nullptr;
+    s = upload_const(ctx, "fft", blob, st, &d);
+    if (s != XS_OK) return s;
+    const double2* d_G = reinterpret_cast<const double2*>(static_cast<char*>(d) + o_G);
+    s = ensure_ws(ctx, (size_t)n_grid * n_grid * n_grid * sizeof(double2) + 256);
+    if (s != XS_OK) return s;
+    double2* fgrid = static_cast<double2*>(ctx->ws);
+    for (int64_t t = 0; t < T; ++t) {
+        const float* pos_t = traj->pos + (size_t)t * N * 3;
+        float* It = I_out + (size_t)t * P;
+        float* At = amp_out ? amp_out + (size_t)t * P * 2 : nullptr;
+        XS_CUDA(traced(ctx, "fft", st, [&] {
+            return launch_fft_frame(pos_t, traj->f, N, fg, fgrid, g, d_G, It, At, ctx->d_err, st);
+        }));
+    }
+    return XS_OK;
 }
 
 // --------------------------------------------------------------------------
@@ -906,6 +989,8 @@ xs_status xs_intensity_species(xs_context* ctx, const xs_traj* traj, const int32
                                             reinterpret_cast<double*>(ws + o_part), ws + o_split, ctx->d_err,
                                             ctx->timeout_ns, st);
                 }));
+                XS_CUDA(traced(ctx, "split_finish", st,
+                               [&] { return launch_tc_split_finish(tr, tc_pairs, spl, ws + o_split, st); }));
             } else {
                 const DirectPlan pc = plan_direct(n_pad, nf, g, ctx->num_sms);
                 if (pc.partial_bytes > dmax.partial_bytes) return fail(XS_ERR_CUDA, "internal: partial plan grew");

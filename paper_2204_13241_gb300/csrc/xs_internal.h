@@ -34,6 +34,7 @@ struct PhaseOpts {
     float lim[3] = {0.0f, 0.0f, 0.0f};  // set by launch_phase
     const int32_t* index = nullptr;      // optional device [n_atoms]: atoms of the frames to use
     int64_t pos_atoms = 0;               // atoms per frame of `pos` when `index` is given
+    bool pos8 = false;                   // set by launch_phase: `pos` is 8-byte aligned
 };
 cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int64_t n_frames,
                          int64_t n_pad, const Mat3& hinv, const PhaseOpts& opt, AtomRec* rec, int* err,
@@ -88,6 +89,10 @@ TcSplit tc_split_plan(int64_t units, int n_pairs, int n_stages, int chunk_stages
 size_t tc_split_bytes(const TcSplit& sp);  // partial amplitudes and counters of the pieces
 cudaError_t launch_tc_single(const TcTraj& tr, int n_pairs, const TcSplit& sp, int chunk_stages, bool bf16,
                              double* scratch, void* split_buf, int* err, int64_t timeout_ns, cudaStream_t st);
+// sums the pieces of the split units of a launch_tc_single launch (same
+// arguments) into I; run after it on the same stream
+cudaError_t launch_tc_split_finish(const TcTraj& tr, int n_pairs, const TcSplit& sp, void* split_buf,
+                                   cudaStream_t st);
 cudaError_t launch_tc_batch(const TcTraj* d_trajs, const int4* d_units, const int* d_pair_start, int n_pairs,
                             int chunk_stages, bool bf16, double* scratch, int* err, int64_t timeout_ns,
                             cudaStream_t st);
@@ -102,6 +107,16 @@ struct XsvsLayout {
     int n_chunks;         // (ring, pixel range) chunks
     int64_t n_kw;         // sum over K of floor(T/K)
 };
+// Algorithm 2 grid: n^3 points of an orthorhombic cell, spacing h[a], k[a]
+// Gaussian weights per axis around each atom
+struct FftGrid {
+    int n;
+    double h[3];
+    int k[3];
+    double inv_2eta2;  // 1 / (2 eta^2)
+};
+cudaError_t launch_fft_frame(const float* pos, const float* f, int64_t n_atoms, const FftGrid& fg, double2* grid,
+                             const GridDesc& g, const double2* d_G, float* I, float* amp, int* err, cudaStream_t st);
 cudaError_t launch_points_gather(const float* tmp, const float* tmp_amp, const int64_t* d_src, const int64_t* d_stride,
                                  int64_t P, int64_t nf, float* I, float* amp, cudaStream_t st);
 cudaError_t launch_ff_table(const double* d_coef, int n_species, const GridDesc& g, const Mat3& hinv, double* table,
