@@ -1,11 +1,15 @@
 // Correlation stages on the intensity series I[t][p]:
 //   g2 (Sec. 2.3, Eq. g2_def) and the XSVS contrast (Eqs. inte_Iq, bq_Iq).
 //
-// g2_kernel: one thread per pixel and a group of up to kTauGroup delays.  The
-//   block walks t in order; I[t][p] and I[t+tau][p] are coalesced across the
-//   pixels of a warp.  Products are summed with compensated (Kahan) FP32
-//   updates over blocks of 64 frames, the block sums are added in FP64; the
-//   mean is summed in FP64 directly.
+// g2_kernel: one thread per pixel, group of up to kTauGroup delays and
+//   segment of frames (blockIdx.z).  The block walks its frames t in order;
+//   I[t][p] and I[t+tau][p] are coalesced across the pixels of a warp.
+//   Products are summed with compensated (Kahan) FP32 updates over blocks of
+//   64 frames and the block sums are added in FP64; the mean is summed in
+//   FP64 directly.  Each segment writes FP64 partial sums; g2_finish_kernel
+//   adds the segments in order and divides.  The segments (up to 8, each a
+//   whole number of 64-frame blocks) give the kernel enough warps to hide the
+//   load latency.
 //
 // XSVS: pixels are first permuted ring by ring (host-built permutation), then
 //   prefix_kernel   C[t][p'] = sum_{t'<t} I[t'][perm[p']]       (FP64, [T+1][P'])
@@ -36,7 +40,7 @@ constexpr int kFlush = 64;
 
 __global__ void __launch_bounds__(kG2Threads)
 g2_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __restrict__ taus,
-          int n_tau, double* __restrict__ g2, double* __restrict__ mean_out) {
+          int n_tau, int64_t seg_len, double* __restrict__ part, double* __restrict__ mpart) {
     __shared__ int s_tau[kTauGroup];
     const int g0 = blockIdx.y * kTauGroup;
     const int nt = min(kTauGroup, n_tau - g0);
@@ -55,8 +59,9 @@ g2_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __re
         dacc[k] = 0.0;
     }
     double dmean = 0.0;
-    for (int64_t t0 = 0; t0 < T; t0 += kFlush) {
-        const int64_t t1 = min(T, t0 + kFlush);
+    const int64_t seg0 = (int64_t)blockIdx.z * seg_len, seg1 = min(T, seg0 + seg_len);
+    for (int64_t t0 = seg0; t0 < seg1; t0 += kFlush) {
+        const int64_t t1 = min(seg1, t0 + kFlush);
         for (int64_t t = t0; t < t1; ++t) {
             const float x = I[t * P + p];
             dmean += (double)x;
@@ -76,12 +81,30 @@ g2_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __re
             acc[k] = comp[k] = 0.0f;
         }
     }
-    const double m = dmean / (double)T;
-    if (blockIdx.y == 0 && mean_out) mean_out[p] = m;
+    const int64_t seg = blockIdx.z;
+    if (blockIdx.y == 0) mpart[seg * P + p] = dmean;
 #pragma unroll
     for (int k = 0; k < kTauGroup; ++k) {
-        if (k < nt) g2[(int64_t)(g0 + k) * P + p] = (dacc[k] / (double)(T - tau[k])) / (m * m);
+        if (k < nt) part[(seg * n_tau + g0 + k) * P + p] = dacc[k];
     }
+}
+
+// one thread per (delay, pixel): segments added in order
+__global__ void g2_finish_kernel(const double* __restrict__ part, const double* __restrict__ mpart, int n_seg,
+                                 int64_t T, int64_t P, const int32_t* __restrict__ taus, int n_tau,
+                                 double* __restrict__ g2, double* __restrict__ mean_out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_tau * P) return;
+    const int k = (int)(i / P);
+    const int64_t p = i - (int64_t)k * P;
+    double msum = 0.0, sum = 0.0;
+    for (int s = 0; s < n_seg; ++s) {
+        msum += mpart[(int64_t)s * P + p];
+        sum += part[((int64_t)s * n_tau + k) * P + p];
+    }
+    const double m = msum / (double)T;
+    if (k == 0 && mean_out) mean_out[p] = m;
+    g2[i] = (sum / (double)(T - taus[k])) / (m * m);
 }
 
 constexpr int kIsfGroup = 8;
@@ -279,12 +302,33 @@ __global__ void finalize_kernel(const double2* __restrict__ partial, int n_chunk
 
 }  // namespace
 
+int g2_segments(int64_t T) {
+    const int64_t blocks = (T + kFlush - 1) / kFlush;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(8, blocks));
+}
+
+size_t g2_workspace_bytes(int64_t T, int64_t P, int n_tau) {
+    return (size_t)g2_segments(T) * (size_t)(n_tau + 1) * (size_t)P * sizeof(double);
+}
+
 cudaError_t launch_g2(const float* I, int64_t T, int64_t P, const int32_t* d_taus, int n_tau,
-                      double* g2, double* mean, cudaStream_t st) {
+                      double* g2, double* mean, void* ws, cudaStream_t st) {
     if (P == 0 || n_tau == 0) return cudaSuccess;
-    dim3 grid((unsigned)((P + kG2Threads - 1) / kG2Threads), (unsigned)((n_tau + kTauGroup - 1) / kTauGroup));
+    const int n_seg = g2_segments(T);
+    const int64_t blocks = (T + kFlush - 1) / kFlush;
+    const int64_t seg_len = (blocks + n_seg - 1) / n_seg * kFlush;
+    double* part = static_cast<double*>(ws);
+    double* mpart = part + (size_t)n_seg * n_tau * P;
+    dim3 grid((unsigned)((P + kG2Threads - 1) / kG2Threads), (unsigned)((n_tau + kTauGroup - 1) / kTauGroup),
+              (unsigned)n_seg);
     ++tl_kernel_launches;
-    g2_kernel<<<grid, kG2Threads, 0, st>>>(I, T, P, d_taus, n_tau, g2, mean);
+    g2_kernel<<<grid, kG2Threads, 0, st>>>(I, T, P, d_taus, n_tau, seg_len, part, mpart);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t items = (int64_t)n_tau * P;
+    ++tl_kernel_launches;
+    g2_finish_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(part, mpart, n_seg, T, P, d_taus, n_tau, g2,
+                                                                       mean);
     return cudaGetLastError();
 }
 

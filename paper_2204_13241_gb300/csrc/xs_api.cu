@@ -1234,7 +1234,10 @@ xs_status xs_g2(xs_context* ctx, const float* I, int64_t T, int64_t P, const int
     xs_status s = upload_const(ctx, "g2", blob, st, &d);
     if (s != XS_OK) return s;
     const int32_t* d_taus = reinterpret_cast<const int32_t*>(static_cast<char*>(d) + o_tau);
-    XS_CUDA(traced(ctx, "g2", st, [&] { return launch_g2(I, T, P, d_taus, n_tau, g2_out, mean_out, st); }));
+    s = ensure_ws(ctx, g2_workspace_bytes(T, P, n_tau) + 256);
+    if (s != XS_OK) return s;
+    void* ws = ctx->ws;
+    XS_CUDA(traced(ctx, "g2", st, [&] { return launch_g2(I, T, P, d_taus, n_tau, g2_out, mean_out, ws, st); }));
     return XS_OK;
 }
 

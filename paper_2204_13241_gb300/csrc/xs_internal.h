@@ -98,8 +98,10 @@ cudaError_t launch_tc_batch(const TcTraj* d_trajs, const int4* d_units, const in
                             cudaStream_t st);
 
 // ---- g2 -----------------------------------------------------------------
+int g2_segments(int64_t T);
+size_t g2_workspace_bytes(int64_t T, int64_t P, int n_tau);  // FP64 partial sums per frame segment
 cudaError_t launch_g2(const float* I, int64_t T, int64_t P, const int32_t* d_taus, int n_tau,
-                      double* g2, double* mean, cudaStream_t st);
+                      double* g2, double* mean, void* ws, cudaStream_t st);
 
 // ---- XSVS contrast --------------------------------------------------------
 struct XsvsLayout {
