@@ -55,6 +55,7 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -271,7 +272,14 @@ def run_ours(args):
     barrier()
     launches = ctx.launch_count() - launches0
     tc_ms, tc_n = ctx.profile_read("tc")
+    # per-stage device time per step (library events around each stage's launches)
+    breakdown = {"tc_kernel": tc_ms / args.steps}
+    for tag in ("split_finish", "phase", "g2", "xsvs"):
+        t_ms, _ = ctx.profile_read(tag)
+        breakdown[tag] = t_ms / args.steps
     all_ms, all_n = ctx.profile_read("")
+    breakdown["other"] = all_ms / args.steps
+    all_ms += sum(v for k, v in breakdown.items() if k not in ("tc_kernel", "other")) * args.steps
     ctx.profile(False)
     ctx.sync_status()
     ms = ev0.elapsed_time(ev1) / args.steps
@@ -304,7 +312,8 @@ def run_ours(args):
                        "n_tau": len(taus), "window_lengths": Ks, "rings": R,
                        "l2": "inputs larger than L2 (3.1 GB positions + 4.1 GB phase records read per step)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "gpu_launches": launches, "clocks": clocks}
+            "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
+            "stage_ms_per_step": {k: round(v, 4) for k, v in breakdown.items()}}
 
     # ---- end to end through the public API with host buffers ------------------
     if not args.no_e2e:
@@ -351,6 +360,34 @@ def run_ours(args):
         ours_rate = units / (tc_launch_ms * 1e-3)
         line["fp32_direct"] = {"value": rate32, "unit": METRIC, "frames": nf,
                                "tc_kernel_rate": ours_rate, "speedup_tc_vs_fp32": ours_rate / rate32}
+
+    # ---- the batched workload: 64 ideal-gas trajectories in one persistent launch
+    if not args.no_batched and rank == 0:
+        del pos_d
+        torch.cuda.empty_cache()
+        params = wl.config2_params()
+        trajs, grids = [], []
+        for prm in params:
+            trajs.append(wl.gas_on_device(prm, "cuda"))
+            grids.append(wl.centered_plane(prm["side"]))
+        outs = [torch.empty((prm["n_frames"], 1, prm["side"], prm["side"]), dtype=torch.float32, device="cuda")
+                for prm in params]
+        b_units = float(sum(prm["n_atoms"] * prm["n_frames"] * prm["side"] ** 2 for prm in params))
+        xs.intensity_batched(trajs, grids, "bf16", outs)     # builds and captures the graph
+        ctx.sync_status()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            xs.intensity_batched(trajs, grids, "bf16", outs)  # graph replay
+        e1.record(stream)
+        e1.synchronize()
+        ctx.sync_status()
+        b_ms = e0.elapsed_time(e1) / 2
+        line["batched"] = {"workload": "64 ideal-gas trajectories, N log-uniform 2e3-5e5, T 100-2000, "
+                                       "planes 64^2-256^2, split BF16, one persistent launch per call",
+                           "units": b_units, "ms_per_call": b_ms, "value": b_units / (b_ms * 1e-3), "unit": METRIC}
+        del trajs, outs
+        torch.cuda.empty_cache()
 
     # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N = 1) ----
     if not args.no_cpu_baseline and rank == 0 and world == 1:
