@@ -268,6 +268,34 @@ XS_API xs_status xs_contrast_from_isf(xs_context* ctx, const double* Fhat, int64
                                       void* cuda_stream);
 
 /*
+ * XSVS over pixel shards (one GPU per shard): the sums that the contrast of
+ * xs_xsvs_contrast is made of, for the shard's pixels.  For window length
+ * Ks[k] and window w (0 <= w < T / Ks[k]) the row is kw = sum_{k'<k} T / Ks[k']
+ * + w, and
+ *   sums_out[kw][r - 1] = (sum_p I_K(p,w), sum_p I_K(p,w)^2) over the pixels p
+ *   of the shard in ring r,   I_K(p,w) = sum_{t=wK}^{wK+K-1} I(t,p)
+ * Adding the shards' sums and counts (an all-reduce) and passing them to
+ * xs_xsvs_finalize gives the contrast of all pixels.
+ *   I          device float32 [T][P] (the shard's pixels)
+ *   ring       HOST int32 [P]: ring of each pixel, 1..n_rings, 0 for none (as
+ *              from xs_ring_index on the full grid)
+ *   sums_out   device float64 [n_kw][n_rings][2]
+ *   count_out  HOST int64 [n_rings] pixels per ring in the shard, or NULL
+ */
+XS_API xs_status xs_xsvs_partial(xs_context* ctx, const float* I, int64_t T, int64_t P, const int32_t* ring,
+                                 int32_t n_rings, const int32_t* Ks, int32_t n_K, double* sums_out,
+                                 int64_t* count_out, void* cuda_stream);
+
+/*
+ * Host-side (no GPU work): beta_K(r) from summed shard sums and counts (HOST
+ * arrays laid out as in xs_xsvs_partial), with the per-window contrast of Eq.
+ * bq_Iq averaged over windows; NaN for an empty ring.  beta_out HOST float64
+ * [n_K][n_rings].
+ */
+XS_API xs_status xs_xsvs_finalize(const double* sums, const int64_t* counts, int64_t T, const int32_t* Ks,
+                                  int32_t n_K, int32_t n_rings, double* beta_out);
+
+/*
  * Host-side helper (no GPU work): the ring of every pixel of `grid` as used by
  * xs_xsvs_contrast, ring_out HOST int32 [nx*ny*nz], 0 for pixels in no ring.
  */

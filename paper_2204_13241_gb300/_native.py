@@ -20,7 +20,7 @@ EXPORTS = ["xs_context_create", "xs_context_destroy", "xs_intensity", "xs_intens
            "xs_xsvs_contrast", "xs_ring_index", "xs_intensity_backward", "xs_tune", "xs_last_error",
            "xs_sync_status", "xs_set_wait_timeout_ns", "xs_version", "xs_profile_enable", "xs_profile_read",
            "xs_launch_count", "xs_intensity_fp32_static", "xs_isf", "xs_contrast_from_isf", "xs_intensity_species",
-           "xs_intensity_points", "xs_ewald_points", "xs_intensity_fft"]
+           "xs_intensity_points", "xs_ewald_points", "xs_intensity_fft", "xs_xsvs_partial", "xs_xsvs_finalize"]
 
 
 class XsError(RuntimeError):
@@ -89,6 +89,8 @@ def load() -> ctypes.CDLL:
         "xs_isf": ([P, P, I64, I64, P, I32, D, P, P, P], st),
         "xs_intensity_points": ([P, ctypes.POINTER(Traj), P, I64, st, P, P, P], st),
         "xs_intensity_fft": ([P, ctypes.POINTER(Traj), I32, D, I32, ctypes.POINTER(QGrid), P, P, P], st),
+        "xs_xsvs_partial": ([P, P, I64, I64, P, I32, P, I32, P, P, P], st),
+        "xs_xsvs_finalize": ([P, P, I64, P, I32, I32, P], st),
         "xs_ewald_points": ([ctypes.POINTER(Box), P, I32, I32, I32, I32, P, P], st),
         "xs_intensity_species": ([P, ctypes.POINTER(Traj), P, I32, P, ctypes.POINTER(QGrid), st, P, P, P], st),
         "xs_contrast_from_isf": ([P, P, I64, ctypes.POINTER(QGrid), ctypes.POINTER(Box), P, I32, D, I32, P, P, P],

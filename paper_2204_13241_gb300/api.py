@@ -322,6 +322,41 @@ def contrast_from_isf(Fhat: torch.Tensor, grid, box, Ks: Sequence[int], n_rings:
     return out, counts
 
 
+def xsvs_partial(I: torch.Tensor, ring, n_rings: int, Ks: Sequence[int]):
+    """Per-(K, window, ring) sums (sum I_K, sum I_K^2) over the pixels of a
+    shard, I [T][P_shard], ring int [P_shard] (host); returns (sums float64
+    [n_kw][n_rings][2] on the device, counts int64 [n_rings] on the host)."""
+    _need(I, "I")
+    T = I.shape[0]
+    P = I.numel() // max(T, 1)
+    rg = np.ascontiguousarray(np.asarray(ring, dtype=np.int32).reshape(-1))
+    if rg.size != P:
+        raise ValueError("one ring label per pixel")
+    k = np.ascontiguousarray(np.asarray(Ks, dtype=np.int32))
+    n_kw = int(sum(T // int(K) for K in k))
+    sums = torch.zeros((n_kw, n_rings, 2), dtype=torch.float64, device=I.device)
+    counts = np.zeros(n_rings, dtype=np.int64)
+    ctx = Context.get()
+    nat.check(ctx.lib.xs_xsvs_partial(ctx.handle, I.data_ptr(), T, P, rg.ctypes.data_as(ctypes.c_void_p), int(n_rings),
+                                      k.ctypes.data_as(ctypes.c_void_p), k.size, sums.data_ptr() if sums.numel() else None,
+                                      counts.ctypes.data_as(ctypes.c_void_p), _stream()))
+    return sums, counts
+
+
+def xsvs_finalize(sums, counts, T: int, Ks: Sequence[int]) -> np.ndarray:
+    """beta_K(r) from summed shard sums (host or device array [n_kw][n_rings][2])
+    and counts [n_rings] (host, library routine without GPU work)."""
+    sm = np.ascontiguousarray(np.asarray(sums.cpu() if hasattr(sums, "cpu") else sums, dtype=np.float64))
+    ct = np.ascontiguousarray(np.asarray(counts, dtype=np.int64))
+    k = np.ascontiguousarray(np.asarray(Ks, dtype=np.int32))
+    n_rings = ct.size
+    out = np.zeros((k.size, n_rings), dtype=np.float64)
+    nat.check(nat.load().xs_xsvs_finalize(sm.ctypes.data_as(ctypes.c_void_p), ct.ctypes.data_as(ctypes.c_void_p),
+                                          int(T), k.ctypes.data_as(ctypes.c_void_p), k.size, n_rings,
+                                          out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
 def ring_index(grid, box, ring_width: float, n_rings: int) -> np.ndarray:
     """Ring of every pixel as used by xsvs_contrast (host computation)."""
     g = _grid(grid)

@@ -265,6 +265,22 @@ __global__ void window_kernel(const double* __restrict__ C, int64_t n_in, const 
     }
 }
 
+// one warp per ((K,w), ring): the ring's chunk partials added in chunk order
+__global__ void ring_sums_kernel(const double2* __restrict__ partial, int n_chunks, int64_t n_kw,
+                                 const int32_t* __restrict__ ring_first_chunk, int n_rings, double2* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_kw * n_rings) return;
+    const int64_t kw = i / n_rings;
+    const int r = (int)(i - kw * n_rings);
+    const double2* row = partial + kw * n_chunks;
+    double s1 = 0.0, s2 = 0.0;
+    for (int c = ring_first_chunk[r]; c < ring_first_chunk[r + 1]; ++c) {
+        s1 += row[c].x;
+        s2 += row[c].y;
+    }
+    out[i] = make_double2(s1, s2);
+}
+
 // one warp per (K, ring): lanes take windows w = lane, lane + 32, ...; the
 // per-lane sums of beta_w are reduced by a fixed shuffle tree (deterministic)
 __global__ void finalize_kernel(const double2* __restrict__ partial, int n_chunks,
@@ -329,6 +345,32 @@ cudaError_t launch_g2(const float* I, int64_t T, int64_t P, const int32_t* d_tau
     ++tl_kernel_launches;
     g2_finish_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(part, mpart, n_seg, T, P, d_taus, n_tau, g2,
                                                                        mean);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xsvs_partial(const float* I, int64_t T, int64_t P, const int32_t* d_perm, const int4* d_chunks,
+                               int n_chunks, int64_t n_in_rings, const int32_t* d_K, const int64_t* d_kw_off, int n_K,
+                               int64_t n_kw, const int32_t* d_ring_first_chunk, int n_rings, double* prefix,
+                               double2* partial, double* sums, cudaStream_t st) {
+    if (n_in_rings > 0) {
+        ++tl_kernel_launches;
+        prefix_kernel<<<(unsigned)((n_in_rings + 127) / 128), 128, 0, st>>>(I, T, P, d_perm, n_in_rings, prefix);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        int64_t slice = 64;
+        if ((n_kw + slice - 1) / slice > 65535) slice = (n_kw + 65534) / 65535;
+        const dim3 wgrid((unsigned)n_chunks, (unsigned)std::max<int64_t>(1, (n_kw + slice - 1) / slice));
+        ++tl_kernel_launches;
+        window_kernel<<<wgrid, 256, 0, st>>>(prefix, n_in_rings, d_chunks, n_chunks, d_K, d_kw_off, n_K, n_kw, slice,
+                                             partial);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t items = n_kw * n_rings;
+    if (items == 0) return cudaSuccess;
+    ++tl_kernel_launches;
+    ring_sums_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(partial, n_chunks, n_kw, d_ring_first_chunk,
+                                                                       n_rings, reinterpret_cast<double2*>(sums));
     return cudaGetLastError();
 }
 

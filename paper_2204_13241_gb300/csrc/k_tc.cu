@@ -39,6 +39,10 @@
 // symmetry of the factors, E(-n) = conj E(n) and w(-n) = conj w(n) for real
 // f: each CTA holds n in [32r, 32r + 32) and their negatives, builds 33 base
 // values per operand instead of 64 and stores each twice (see centred_index).
+// Units (frame x plane x tile) are dealt round-robin to the pairs.  When the
+// last wave is partial, its units are cut along the atoms into pieces; each
+// piece leaves its FP64 partial amplitude, and split_finish_kernel adds the
+// pieces in part order after the launch.
 // The atoms arrive in a coprime-stride permuted order (see the phase kernel),
 // so the partial sums over a chunk behave like random walks even for ordered
 // crystals and the FP32 accumulator never sums a coherent run of terms.

@@ -1315,6 +1315,115 @@ static xs_status ring_layout(const xs_qgrid* grid, const xs_box* box, double rin
     return XS_OK;
 }
 
+// --------------------------------------------------------------------------
+// XSVS over pixel shards: partial sums on the device, finalize on the host
+// --------------------------------------------------------------------------
+
+xs_status xs_xsvs_partial(xs_context* ctx, const float* I, int64_t T, int64_t P, const int32_t* ring, int32_t n_rings,
+                          const int32_t* Ks, int32_t n_K, double* sums_out, int64_t* count_out, void* cuda_stream) {
+    if (!ctx || (P > 0 && (!I || !ring)) || (n_K > 0 && !Ks)) return fail(XS_ERR_INVALID_ARG, "missing argument");
+    if (T < 1 || P < 0 || n_K < 0 || n_rings < 0) return fail(XS_ERR_INVALID_ARG, "need T >= 1, P, n_K, n_rings >= 0");
+    if (P > INT32_MAX) return fail(XS_ERR_INVALID_ARG, "more than 2^31 pixels");
+    for (int32_t k = 0; k < n_K; ++k)
+        if (Ks[k] < 1 || Ks[k] > T) return fail(XS_ERR_INVALID_ARG, "window length %d outside [1, T]", Ks[k]);
+    std::vector<int32_t> count((size_t)n_rings, 0);
+    for (int64_t p = 0; p < P; ++p) {
+        if (ring[p] < 0 || ring[p] > n_rings) return fail(XS_ERR_INVALID_ARG, "pixel %lld has ring %d", (long long)p, ring[p]);
+        if (ring[p] > 0) ++count[(size_t)ring[p] - 1];
+    }
+    if (count_out)
+        for (int r = 0; r < n_rings; ++r) count_out[r] = count[(size_t)r];
+    std::vector<int64_t> kw_off((size_t)n_K + 1, 0);
+    for (int k = 0; k < n_K; ++k) kw_off[(size_t)k + 1] = kw_off[(size_t)k] + T / Ks[k];
+    const int64_t n_kw = kw_off[(size_t)n_K];
+    if (n_kw == 0 || n_rings == 0) return XS_OK;
+    if (!sums_out) return fail(XS_ERR_INVALID_ARG, "sums_out is required");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<int64_t> start((size_t)n_rings + 1, 0);
+    for (int r = 0; r < n_rings; ++r) start[(size_t)r + 1] = start[(size_t)r] + count[(size_t)r];
+    const int64_t n_in = start[(size_t)n_rings];
+    std::vector<int32_t> perm((size_t)std::max<int64_t>(n_in, 1), 0);
+    {
+        std::vector<int64_t> fill(start.begin(), start.end() - 1);
+        for (int64_t p = 0; p < P; ++p)
+            if (ring[p] > 0) perm[(size_t)fill[(size_t)ring[p] - 1]++] = (int32_t)p;
+    }
+    constexpr int kChunk = 128;
+    std::vector<int32_t> chunks, first((size_t)n_rings + 1, 0);
+    for (int r = 0; r < n_rings; ++r) {
+        first[(size_t)r] = (int32_t)(chunks.size() / 4);
+        for (int64_t a = start[(size_t)r]; a < start[(size_t)r + 1]; a += kChunk) {
+            chunks.push_back(r + 1);
+            chunks.push_back((int32_t)a);
+            chunks.push_back((int32_t)std::min<int64_t>(kChunk, start[(size_t)r + 1] - a));
+            chunks.push_back(0);
+        }
+    }
+    const int n_chunks = (int)(chunks.size() / 4);
+    first[(size_t)n_rings] = n_chunks;
+    if (chunks.empty()) chunks.assign(4, 0);
+    std::vector<char> blob;
+    const int64_t key[2] = {T, P};
+    push(blob, key, 2);
+    const size_t o_perm = push(blob, perm.data(), perm.size());
+    const size_t o_chunks = push(blob, chunks.data(), chunks.size());
+    const size_t o_K = push(blob, Ks, (size_t)n_K);
+    const size_t o_kw = push(blob, kw_off.data(), kw_off.size());
+    const size_t o_first = push(blob, first.data(), first.size());
+    void* d = nullptr;
+    xs_status s = upload_const(ctx, "xsvs_partial", blob, st, &d);
+    if (s != XS_OK) return s;
+    char* dc = static_cast<char*>(d);
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        size_t o = round_up((int64_t)off, 256);
+        off = o + bytes;
+        return o;
+    };
+    const size_t o_prefix = carve((size_t)(T + 1) * std::max<int64_t>(n_in, 1) * sizeof(double));
+    const size_t o_partial = carve((size_t)n_kw * std::max(n_chunks, 1) * sizeof(double2));
+    s = ensure_ws(ctx, off + 256);
+    if (s != XS_OK) return s;
+    char* ws = static_cast<char*>(ctx->ws);
+    if (n_chunks == 0) {  // no pixel in any ring: zero sums
+        XS_CUDA(cudaMemsetAsync(sums_out, 0, (size_t)n_kw * n_rings * 2 * sizeof(double), st));
+        return XS_OK;
+    }
+    XS_CUDA(traced(ctx, "xsvs", st, [&] {
+        return launch_xsvs_partial(I, T, P, reinterpret_cast<const int32_t*>(dc + o_perm),
+                                   reinterpret_cast<const int4*>(dc + o_chunks), n_chunks, n_in,
+                                   reinterpret_cast<const int32_t*>(dc + o_K), reinterpret_cast<const int64_t*>(dc + o_kw),
+                                   n_K, n_kw, reinterpret_cast<const int32_t*>(dc + o_first), n_rings,
+                                   reinterpret_cast<double*>(ws + o_prefix), reinterpret_cast<double2*>(ws + o_partial),
+                                   sums_out, st);
+    }));
+    return XS_OK;
+}
+
+xs_status xs_xsvs_finalize(const double* sums, const int64_t* counts, int64_t T, const int32_t* Ks, int32_t n_K,
+                           int32_t n_rings, double* beta_out) {
+    if ((n_K > 0 && (!Ks || !beta_out)) || (n_rings > 0 && !counts) || T < 1 || n_K < 0 || n_rings < 0)
+        return fail(XS_ERR_INVALID_ARG, "bad arguments");
+    int64_t kw0 = 0;
+    for (int32_t k = 0; k < n_K; ++k) {
+        if (Ks[k] < 1 || Ks[k] > T) return fail(XS_ERR_INVALID_ARG, "window length %d outside [1, T]", Ks[k]);
+        const int64_t W = T / Ks[k];
+        if (W > 0 && n_rings > 0 && !sums) return fail(XS_ERR_INVALID_ARG, "sums are required");
+        for (int32_t r = 0; r < n_rings; ++r) {
+            const double n = (double)counts[r];
+            double acc = 0.0;
+            for (int64_t w = 0; w < W; ++w) {
+                const double* v = sums + ((kw0 + w) * n_rings + r) * 2;
+                const double m1 = v[0] / n, m2 = v[1] / n;
+                acc += (m2 - m1 * m1) / (m1 * m1);
+            }
+            beta_out[(int64_t)k * n_rings + r] = counts[r] > 0 ? acc / (double)W : std::nan("");
+        }
+        kw0 += W;
+    }
+    return XS_OK;
+}
+
 xs_status xs_xsvs_contrast(xs_context* ctx, const float* I, int64_t T, const xs_qgrid* grid, const xs_box* box,
                            const int32_t* Ks, int32_t n_K, double ring_width, int32_t n_rings, double* beta_out,
                            int32_t* ring_count_out, void* cuda_stream) {

@@ -86,7 +86,7 @@ struct TcSplit {
     int parts = 1;
 };
 TcSplit tc_split_plan(int64_t units, int n_pairs, int n_stages, int chunk_stages);
-size_t tc_split_bytes(const TcSplit& sp);  // partial amplitudes and counters of the pieces
+size_t tc_split_bytes(const TcSplit& sp);  // FP64 partial amplitudes of the pieces
 cudaError_t launch_tc_single(const TcTraj& tr, int n_pairs, const TcSplit& sp, int chunk_stages, bool bf16,
                              double* scratch, void* split_buf, int* err, int64_t timeout_ns, cudaStream_t st);
 // sums the pieces of the split units of a launch_tc_single launch (same
@@ -126,6 +126,11 @@ cudaError_t launch_ff_table(const double* d_coef, int n_species, const GridDesc&
 cudaError_t launch_species_acc(const float* S, const double* ff, int64_t nf, int64_t P, bool first, double* acc,
                                cudaStream_t st);
 cudaError_t launch_species_finish(const double* acc, int64_t n, float* I, float* amp, cudaStream_t st);
+// XSVS window sums per ring for a pixel subset: sums [n_kw][n_rings] of (sum x, sum x^2)
+cudaError_t launch_xsvs_partial(const float* I, int64_t T, int64_t P, const int32_t* d_perm, const int4* d_chunks,
+                               int n_chunks, int64_t n_in_rings, const int32_t* d_K, const int64_t* d_kw_off, int n_K,
+                               int64_t n_kw, const int32_t* d_ring_first_chunk, int n_rings, double* prefix,
+                               double2* partial, double* sums, cudaStream_t st);
 cudaError_t launch_isf(const float* amp, int64_t T, int64_t P, const int32_t* d_taus, int n_tau, double inv_sum_f2,
                        double* F, double* Fhat, cudaStream_t st);
 cudaError_t launch_isf_contrast(const double* Fhat, int64_t Kmax, int64_t P, const int32_t* d_perm, int64_t n_in,

@@ -1,11 +1,16 @@
-"""The multi-rank path of the benchmark on CPU: two gloo ranks on 127.0.0.1
-agree on the slowest rank's time, and the whole-job value counts every rank's
-replica (weak scaling); the reference arm does no work on ranks other than 0."""
+"""Multi-rank paths on the CPU with two gloo ranks on 127.0.0.1:
+  * the benchmark: the ranks agree on the slowest rank's time, and the
+    whole-job value counts every rank's replica (weak scaling); the reference
+    arm does no work on ranks other than 0;
+  * XSVS over pixel shards: each rank's window sums per ring, all-reduced, go
+    through the library's xs_xsvs_finalize and give the contrast of all pixels
+    (the exchange of the sharded design, Sec. 2.3 Eq. bq_Iq)."""
 import os
 import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 import torch
 import torch.distributed as dist
@@ -58,3 +63,56 @@ def test_reference_arm_is_silent_on_other_ranks():
                         "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def _shard_sums(I, ring, n_rings, Ks):
+    # window sums per ring of one shard's pixels, laid out as xs_xsvs_partial writes them
+    T = I.shape[0]
+    rows = []
+    for K in Ks:
+        for w in range(T // K):
+            x = I[w * K:(w + 1) * K].sum(axis=0)
+            rows.append([[x[ring == r].sum(), (x[ring == r] ** 2).sum()] for r in range(1, n_rings + 1)])
+    counts = np.array([(ring == r).sum() for r in range(1, n_rings + 1)], dtype=np.int64)
+    return np.array(rows, dtype=np.float64), counts
+
+
+def _xsvs_rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_2204_13241_gb300 import api as xs
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        rng = np.random.default_rng(5)                       # every rank draws the same series
+        T, P, n_rings, Ks = 40, 300, 6, [1, 3, 8, 40]
+        I = rng.exponential(size=(T, P))
+        ring = rng.integers(0, n_rings + 1, P).astype(np.int32)
+        mine = np.arange(P) % world == rank                   # pixel shard of this rank
+        sums, counts = _shard_sums(I[:, mine], ring[mine], n_rings, Ks)
+        ts, tc = torch.from_numpy(sums), torch.from_numpy(counts)
+        dist.all_reduce(ts)
+        dist.all_reduce(tc)
+        beta = xs.xsvs_finalize(ts.numpy(), tc.numpy(), T, Ks)
+        ref, cref = oracle.xsvs_contrast(I, Ks, ring, n_rings)
+        ok = bool(np.array_equal(tc.numpy(), cref) and np.allclose(beta, ref, rtol=1e-12, atol=0, equal_nan=True))
+        q.put((rank, ok))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_shard_pixels_for_xsvs_and_finalize_in_the_library():
+    from paper_2204_13241_gb300 import build as xbuild
+    xbuild.build()
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_xsvs_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert all(ok for _, ok in out), out

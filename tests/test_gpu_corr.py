@@ -109,3 +109,29 @@ def test_config0_end_to_end_fp32(xs):
     ok = counts >= 8
     e_b = np.max(np.abs(beta.cpu().numpy()[:, ok] - bref[:, ok]) / np.abs(bref[:, ok]))
     assert e_b <= 1e-6, e_b
+
+
+def test_xsvs_over_pixel_shards_matches_the_whole(xs):
+    # two shards of one plane (emulated ranks on one GPU): partial sums added,
+    # as an all-reduce would, then finalized on the host
+    import oracle as _oracle
+    T, grid, box = 300, wl.centered_plane(48), np.eye(3) * 30.0
+    n_rings = wl.rings_for_plane(grid)
+    m = grid.miller()
+    rings = _oracle.ring_index(box, m, 1.0, n_rings)
+    g = torch.Generator(device="cuda").manual_seed(11)
+    I = torch.rand((T, m.shape[0]), generator=g, device="cuda") + 0.1
+    Ks = [1, 2, 5, 10, 50, 300]
+    whole, counts = xs.xsvs_contrast(I.view(T, 1, grid.ny, grid.nx), grid, box, Ks, n_rings)
+    sums, cnt = None, None
+    for shard in (np.arange(m.shape[0]) % 3 == 0, np.arange(m.shape[0]) % 3 != 0):
+        idx = torch.from_numpy(np.flatnonzero(shard)).cuda()
+        s, c = xs.xsvs_partial(I[:, idx].contiguous(), rings[shard], n_rings, Ks)
+        sums = s if sums is None else sums + s
+        cnt = c if cnt is None else cnt + c
+    xs.Context.get().sync_status()
+    beta = xs.xsvs_finalize(sums, cnt, T, Ks)
+    assert np.array_equal(cnt, counts)
+    assert np.allclose(beta, whole.cpu().numpy(), rtol=1e-12, atol=0, equal_nan=True)
+    ref, _ = _oracle.xsvs_contrast(I.cpu().numpy(), Ks, rings, n_rings)
+    assert np.allclose(beta, ref, rtol=1e-9, atol=1e-12, equal_nan=True)
