@@ -407,6 +407,20 @@ def run_ours(args):
                                 "sample": f"frame 0, {sel.size} of {m.shape[0]} pixels (every 2nd), "
                                           f"{traj.n_atoms} atoms, {dt:.1f} s"}
         line["accuracy"] = {"e_I_frame0": e_I, "against": "oracle on the cpu_baseline sample"}
+        # one host core on a smaller sample, and the 4,000-atom workload in full
+        sel1 = np.arange(0, m.shape[0], 32)
+        t0 = time.perf_counter()
+        oracle.intensity(traj.pos[:1], traj.f, traj.box, m[sel1], threads=1)
+        dt1 = time.perf_counter() - t0
+        line["cpu_baseline"]["single_core"] = {"value": traj.n_atoms * sel1.size / dt1, "unit": METRIC,
+                                               "sample": f"frame 0, {sel1.size} pixels (every 32nd)"}
+        t0c, g0 = wl.config0()
+        t0 = time.perf_counter()
+        oracle.intensity(t0c.pos, t0c.f, t0c.box, g0.miller())
+        dt0 = time.perf_counter() - t0
+        line["cpu_baseline"]["config_4000_atoms_full"] = {
+            "value": t0c.n_atoms * g0.n_pixels * t0c.pos.shape[0] / dt0, "unit": METRIC, "seconds": dt0,
+            "workload": "4,000 atoms, 10 frames, 64^2 plane, all host cores"}
 
     if rank == 0:
         print(json.dumps(line), flush=True)
