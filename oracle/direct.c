@@ -88,8 +88,9 @@ int oracle_amplitude(const float* pos, int64_t n_atoms, int64_t n_frames, const 
     /* small fixed-size path keeps this file free of allocation helpers */
     enum { QCHUNK = 1024 };
     double qbuf[QCHUNK * 3];
+    /* n_threads > 0 applies to this call only (no global OpenMP setting) */
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
+    const int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
 #else
     (void)n_threads;
 #endif
@@ -98,7 +99,7 @@ int oracle_amplitude(const float* pos, int64_t n_atoms, int64_t n_frames, const 
         if (!oracle_qvectors(h, miller + 3 * q0, nq, qbuf)) return 0;
         q = qbuf;
         int64_t total = n_frames * nq;
-#pragma omp parallel for schedule(dynamic, 16)
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
         for (int64_t w = 0; w < total; ++w) {
             int64_t t = w / nq, p = w % nq;
             const double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
