@@ -38,10 +38,10 @@ FALLBACK_PEAK = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gb
 
 # DRAM bytes (read + write) of one tc_kernel launch of the 1,000-frame
 # workload, from an ncu capture of that launch (dram__bytes_read.sum +
-# dram__bytes_write.sum, one pass): 4.11 GB + 75.35 MB.  Reported only while
+# dram__bytes_write.sum, one pass; 64-stage chunks): 4.11 GB + 77.2 MB.  Reported only while
 # k_tc.cu is unchanged; other frame counts scale it by frames (records and
 # outputs are per frame; the split-piece partials are not, a few percent).
-TC_TRAFFIC = {"k_tc_sha256_prefix": "4c877d58ca21e375", "bytes": 4.11e9 + 75.35e6, "frames": 1000}
+TC_TRAFFIC = {"k_tc_sha256_prefix": "4c877d58ca21e375", "bytes": 4.11e9 + 77.23e6, "frames": 1000}
 
 
 def _args():

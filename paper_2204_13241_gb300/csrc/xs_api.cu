@@ -426,7 +426,7 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
 
     DirectPlan dplan{};
     int tc_pairs = 0;
-    int chunk_stages = 32;
+    int chunk_stages = kDefaultChunkStages;
     if (use_tc) {
         auto key = std::make_tuple(n_pad, g.nx, g.ny, g.nz, (int)prec);
         auto it = ctx->tuned_chunk.find(key);
@@ -843,7 +843,7 @@ xs_status xs_intensity_points(xs_context* ctx, const xs_traj* traj, const int32_
         char* dc = static_cast<char*>(d);
         XS_CUDA(traced(ctx, "tc", st, [&] {
             return launch_tc_batch(reinterpret_cast<const TcTraj*>(dc + o_tr), reinterpret_cast<const int4*>(dc + o_units),
-                                   reinterpret_cast<const int*>(dc + o_ps), n_pairs, 32, prec == XS_PREC_SPLIT_BF16,
+                                   reinterpret_cast<const int*>(dc + o_ps), n_pairs, kDefaultChunkStages, prec == XS_PREC_SPLIT_BF16,
                                    reinterpret_cast<double*>(ws + o_part), ctx->d_err, ctx->timeout_ns, st);
         }));
         XS_CUDA(traced(ctx, "points", st, [&] {
@@ -915,7 +915,7 @@ xs_status xs_intensity_species(xs_context* ctx, const xs_traj* traj, const int32
     const size_t per_frame = (size_t)n_pad_max * sizeof(AtomRec) + (size_t)P * (2 * sizeof(float) + sizeof(float) + 2 * sizeof(double));
     int64_t fchunk = std::max<int64_t>(1, std::min<int64_t>(T, (int64_t)(((size_t)6 << 30) / per_frame)));
     if (fchunk > 65535) fchunk = 65535;
-    int tc_pairs = 0, chunk_stages = 32;
+    int tc_pairs = 0, chunk_stages = kDefaultChunkStages;
     DirectPlan dmax{};
     if (use_tc) {
         tc_pairs = tc_pair_capacity(ctx->num_sms);
@@ -1099,7 +1099,7 @@ xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qg
     s = upload_const(ctx, "tc_batch", blob, st, &d);
     if (s != XS_OK) return s;
     char* dc = static_cast<char*>(d);
-    int chunk = 32;
+    int chunk = kDefaultChunkStages;
     {
         auto it = ctx->tuned_chunk.find(std::make_tuple(trs[trs.size() / 2].n_pad, trs[trs.size() / 2].nx,
                                                         trs[trs.size() / 2].ny, trs[trs.size() / 2].nz, (int)prec));

@@ -78,6 +78,12 @@ void tc_deal_units(const std::vector<TcTraj>& trajs, const std::vector<int4>& al
                    std::vector<int4>& units, std::vector<int>& pair_start);
 void tc_build_lists(const std::vector<TcTraj>& trajs, int n_pairs, std::vector<int4>& units,
                     std::vector<int>& pair_start);
+// stages (of 64 atoms) per FP32 tensor-core accumulation before the epilogue
+// adds the chunk into its TwoSum totals.  The tensor core's FP32 accumulation
+// is biased, so the error grows with the chunk: on the 256,000-atom crystal
+// e_I is 1.4e-5 at 32 stages and 2.9e-5 at 64, which runs 5% faster.
+constexpr int kDefaultChunkStages = 64;
+
 // dealing of a single trajectory's units over the pairs: `full` whole waves,
 // then `rem` units cut into `parts` pieces along the atoms (parts = 1: plain
 // round-robin of all units, full = 0)
