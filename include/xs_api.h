@@ -9,7 +9,12 @@
  *   - the XPCS autocorrelation g2(q,tau)             (Sec. 2.3, Eq. g2_def),
  *   - the XSVS contrast of K-frame exposures         (Sec. 2.3, Eqs. inte_Iq, bq_Iq),
  *   - the gradient of a loss L(I) with respect to the atomic positions
- *     (the adjoint of Eq. pe_ri).
+ *     (the adjoint of Eq. pe_ri),
+ * and, beyond that path: the intermediate scattering function and the
+ * contrast it predicts (Eqs. Fq_pq, norm_Fq, beta_alt_int), intensities at
+ * point lists and on the Ewald-sphere slice (Fig. 5), per-species
+ * q-dependent form factors (Sec. 2.1), the FFT-based method (Sec. 3.2,
+ * Algorithm 2) as a cross-check, and XSVS over pixel shards.
  * Sign convention: the paper writes p^e = sum f exp(-i q.r); this library's
  * amplitude S is its complex conjugate.  I, g2 and the contrast are identical.
  *
@@ -115,9 +120,9 @@ XS_API xs_status xs_context_destroy(xs_context* ctx);
  *   I_out   float32 [n_frames][nz][ny][nx]
  *   amp_out float32 [n_frames][nz][ny][nx][2] = (Re S, Im S), or NULL
  * Outputs may be device or host memory (detected per pointer); host outputs
- * make the call wait for the stream.  XS_PREC_SPLIT_* need nx, ny <= 4096 and
- * the 128-aligned tiles described in the design notes; every grid works
- * with XS_PREC_FP32_DIRECT.
+ * make the call wait for the stream.  XS_PREC_SPLIT_* work in 128 x 128 tiles
+ * of (n_x, n_y) per plane (a partial tile is computed whole and cut); any grid
+ * size works with every precision.
  */
 XS_API xs_status xs_intensity(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid,
                        xs_precision prec, float* I_out, float* amp_out, void* cuda_stream);
