@@ -30,9 +30,8 @@ What each function follows (arXiv 2204.13241):
   grad_fd                 central finite differences of a caller loss, with an
                           exact incremental update of S per displaced atom.
 
-Readings taken where the paper leaves a choice (listed with the rest in the
-design notes): S uses exp(+i q.r) (the paper's p^e is its conjugate; I is
-the same); g2's numerator averages the T - tau available products and its
+Readings taken where the paper leaves a choice: S uses exp(+i q.r) (the
+paper's p^e is its conjugate; I is the same); g2's numerator averages the T - tau available products and its
 denominator is the square of the mean over all T frames; a ring r holds the
 pixels with r - w/2 <= |q|/Delta < r + w/2, Delta = 2 pi / det(h)^(1/3);
 windows are the floor(T/K) non-overlapping blocks of K frames and beta is the
