@@ -56,6 +56,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-table1", action="store_true")
     return ap.parse_args()
 
 
@@ -360,6 +361,47 @@ def run_ours(args):
         ours_rate = units / (tc_launch_ms * 1e-3)
         line["fp32_direct"] = {"value": rate32, "unit": METRIC, "frames": nf,
                                "tc_kernel_rate": ours_rate, "speedup_tc_vs_fp32": ours_rate / rate32}
+
+    # ---- the paper's own timing setting (Table 1): 4,000 atoms in a
+    # 59.19 A box, one q, an 81^2 slice and an 81^3 grid per frame, and the FFT
+    # method on a 512^3 grid (the next power of two above the paper's 400)
+    if not args.no_table1 and rank == 0:
+        rng = np.random.default_rng(wl.SEED_BASE + 7)
+        Lar, Nar, Tar = 59.19, 4000, 4
+        pos_ar = torch.from_numpy((rng.random((Tar, Nar, 3)) * Lar).astype(np.float32)).cuda()
+        f_ar = torch.ones(Nar, device="cuda")
+        box_ar = np.eye(3) * Lar
+
+        def per_frame(fn, reps=3):
+            fn()
+            torch.cuda.synchronize()
+            ctx.sync_status()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            ctx.sync_status()
+            return e0.elapsed_time(e1) / reps / Tar * 1e-3
+
+        g1 = wl.QGrid(5, 1, 3, 1, 0, 1)
+        g81 = wl.QGrid(-40, 81, -40, 81, 0, 1)
+        v81 = wl.QGrid(-40, 81, -40, 81, -40, 81)
+        t_q = per_frame(lambda: xs.intensity(pos_ar, f_ar, box_ar, g1, "fp32"))
+        t_s = per_frame(lambda: xs.intensity(pos_ar, f_ar, box_ar, g81, "fp16"))
+        t_v = per_frame(lambda: xs.intensity(pos_ar, f_ar, box_ar, v81, "fp16"))
+        t_f = per_frame(lambda: xs.intensity_fft(pos_ar, f_ar, box_ar, g81, 512, 2.0 * Lar / 512), reps=1)
+        line["paper_table1"] = {
+            "workload": "4,000 atoms uniform in a 59.19 A box (synthetic stand-in for the paper's Ar frame), f = 1",
+            "seconds_per_frame": {"direct_single_q_fp32": t_q, "direct_81x81_slice_split_fp16": t_s,
+                                  "direct_81x81x81_grid_split_fp16": t_v,
+                                  "fft_method_512^3_fp64_eta_2_grid_steps": t_f},
+            "paper_seconds_per_frame_32_cpus": {"direct_single_q": 0.0015, "direct_81x81_slice": 4.1836,
+                                                "direct_81x81x81_grid": 416.8243, "fft_method_n400": 0.4527},
+            "note": "paper: Table 1, 32 CPUs (model unstated), its own Ar frames; context, not a like-for-like ratio"}
+        del pos_ar
+        torch.cuda.empty_cache()
 
     # ---- the batched workload: 64 ideal-gas trajectories in one persistent launch
     if not args.no_batched and rank == 0:
