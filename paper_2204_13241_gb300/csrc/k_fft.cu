@@ -3,9 +3,13 @@
 //   spread_kernel    each atom adds f_i g_x g_y g_z (1D Gaussian weights on
 //                    the k_a grid points nearest it, periodic) into a complex
 //                    FP64 grid with atomics
-//   fft_lines_kernel radix-2 decimation-in-time FFT of one grid line per
-//                    block in shared memory (twiddles exp(-2 pi i j / len)
-//                    from sincospi), run once per axis, FP64
+//   fft_lines_kernel radix-2 decimation-in-time FFT of a group of grid lines
+//                    per block in shared memory, run once per axis, FP64,
+//                    coalesced; the n/2 twiddles exp(-2 pi i m / n) are built
+//                    once per block with sincospi (GB300's FP64 pipe is
+//                    narrow: a sincospi per butterfly had cost ten times the
+//                    butterflies themselves), and the first two stages, whose
+//                    twiddles are 1 and -i, multiply nothing
 //   fft_gather_kernel P(n) / (G_x(n_x) G_y(n_y) G_z(n_z)) at the requested
 //                    Miller indices, with G_a the 1D DFT of the truncated
 //                    Gaussian centred at the origin (the transform of one
@@ -62,33 +66,62 @@ __global__ void spread_kernel(const float* __restrict__ pos, const float* __rest
     }
 }
 
-// one block per line; lines are indexed by L in [0, n^2): element j of line L
-// sits at (L / n) * s_hi + (L % n) * s_lo + j * s_el
-__global__ void fft_lines_kernel(double2* __restrict__ data, int n, int log2n, int64_t s_el, int64_t s_lo,
+// one block per `lb` lines; lines are indexed by L in [0, n^2): element j of
+// line L sits at (L / n) * s_hi + (L % n) * s_lo + j * s_el.  Along x (s_el =
+// 1) a line is contiguous and threads walk j; along y and z consecutive lines
+// are consecutive x (s_lo = 1) and threads walk the lines, so the loads and
+// stores are coalesced either way.  Shared memory: [lb][n] values, then the
+// n/2 twiddles.
+__global__ void fft_lines_kernel(double2* __restrict__ data, int n, int log2n, int lb, int64_t s_el, int64_t s_lo,
                                  int64_t s_hi) {
     extern __shared__ double2 buf[];
-    const int64_t L = blockIdx.x;
-    double2* line = data + (L / n) * s_hi + (L % n) * s_lo;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    double2* tw = buf + (size_t)lb * n;
+    const int half_n = n >> 1;
+    for (int m = threadIdx.x; m < half_n; m += blockDim.x) {
+        double s, c;
+        sincospi(-2.0 * (double)m / (double)n, &s, &c);
+        tw[m] = make_double2(c, s);
+    }
+    const int64_t L0 = (int64_t)blockIdx.x * lb;
+    const bool j_fast = s_el == 1;
+    const int total = lb * n;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int l = j_fast ? idx / n : idx % lb;
+        const int j = j_fast ? idx % n : idx / lb;
+        const int64_t L = L0 + l;
+        const double2* line = data + (L / n) * s_hi + (L % n) * s_lo;
         const int r = (int)(__brev((unsigned)j) >> (32 - log2n));
-        buf[r] = line[(int64_t)j * s_el];
+        buf[l * n + r] = line[(int64_t)j * s_el];
     }
     __syncthreads();
-    for (int len = 2; len <= n; len <<= 1) {
+    for (int len = 2, tw_step = half_n; len <= n; len <<= 1, tw_step >>= 1) {
         const int half = len >> 1;
-        for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) {
-            const int pos = t & (half - 1);
-            const int i0 = (t / half) * len + pos, i1 = i0 + half;
-            double s, c;
-            sincospi(-2.0 * (double)pos / (double)len, &s, &c);
+        for (int t = threadIdx.x; t < lb * half_n; t += blockDim.x) {
+            const int l = t / half_n, bt = t - l * half_n;
+            const int pos = bt & (half - 1);
+            const int i0 = l * n + (bt / half) * len + pos, i1 = i0 + half;
             const double2 u = buf[i0], v = buf[i1];
-            const double2 vw = make_double2(v.x * c - v.y * s, v.x * s + v.y * c);
+            double2 vw;
+            if (len == 2) {
+                vw = v;
+            } else if (len == 4) {  // twiddles 1 and exp(-i pi / 2) = -i
+                vw = pos ? make_double2(v.y, -v.x) : v;
+            } else {
+                const double2 w = tw[pos * tw_step];
+                vw = make_double2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
+            }
             buf[i0] = make_double2(u.x + vw.x, u.y + vw.y);
             buf[i1] = make_double2(u.x - vw.x, u.y - vw.y);
         }
         __syncthreads();
     }
-    for (int j = threadIdx.x; j < n; j += blockDim.x) line[(int64_t)j * s_el] = buf[j];
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int l = j_fast ? idx / n : idx % lb;
+        const int j = j_fast ? idx % n : idx / lb;
+        const int64_t L = L0 + l;
+        double2* line = data + (L / n) * s_hi + (L % n) * s_lo;
+        line[(int64_t)j * s_el] = buf[l * n + j];
+    }
 }
 
 __global__ void fft_gather_kernel(const double2* __restrict__ grid, int n, GridDesc g, const double2* __restrict__ G,
@@ -134,15 +167,20 @@ cudaError_t launch_fft_frame(const float* pos, const float* f, int64_t n_atoms, 
     }
     int log2n = 0;
     while ((1 << log2n) < n) ++log2n;
-    const int threads = std::min(512, std::max(32, n / 2));
-    const size_t smem = (size_t)n * sizeof(double2);
+    // lines per block: 64 KB of values (lb divides n, both powers of two) plus
+    // the twiddles
+    const int lb = std::max(1, std::min(n, 4096 / n));
+    const int threads = 512;
+    const size_t smem = ((size_t)lb * n + n / 2) * sizeof(double2);
+    e = cudaFuncSetAttribute((const void*)fft_lines_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     const int64_t nn = (int64_t)n * n;
     // x lines (stride 1), then y (stride n), then z (stride n^2)
     const int64_t strides[3][3] = {{1, n, nn}, {n, 1, nn}, {nn, 1, n}};
     for (int a = 0; a < 3; ++a) {
         ++tl_kernel_launches;
-        fft_lines_kernel<<<(unsigned)nn, threads, smem, st>>>(grid, n, log2n, strides[a][0], strides[a][1],
-                                                              strides[a][2]);
+        fft_lines_kernel<<<(unsigned)(nn / lb), threads, smem, st>>>(grid, n, log2n, lb, strides[a][0],
+                                                                     strides[a][1], strides[a][2]);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
