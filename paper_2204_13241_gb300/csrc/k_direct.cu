@@ -5,11 +5,13 @@
 //   turn count.  This is the only FP64 work per atom (one multiply per axis
 //   for an orthorhombic cell); every later phase n_x*U_x + n_y*U_y + n_z*U_z
 //   is exact integer arithmetic modulo one turn.  Slots may hold the atoms in
-//   a coprime-stride order (slot k holds atom k*a mod n_pad): summing in that
-//   order turns the coherent partial sums of an ordered crystal into random
-//   walks.  Threads follow the slots: the records are written coalesced and
-//   the positions gathered (scattering 16-byte records from coalesced reads
-//   measured 2.6x slower).
+//   a coprime-stride order of runs of 8 (slot 8q + r holds atom
+//   8 (q*a mod n_pad/8) + r): summing in that order turns the coherent partial
+//   sums of an ordered crystal into random walks, while a run of 8 atoms (two
+//   FCC cells) is too short to add up coherently.  Threads follow the slots:
+//   the records are written coalesced and the positions gathered, a warp
+//   reading four contiguous 96-byte runs (scattering 16-byte records from
+//   coalesced reads measured 2.6x slower).
 //
 // direct_kernel: the plain reference-rate kernel.  A block owns 256*PX pixels
 //   of one frame and a range of atoms; atom records are staged in shared
@@ -54,7 +56,9 @@ phase_kernel(const float* __restrict__ pos, const float* __restrict__ f, int64_t
              int64_t n_pad, Mat3 hs, PhaseOpts opt, AtomRec* __restrict__ rec, int* err) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n_pad) return;
-    const int64_t j = opt.perm_mul == 1 ? k : (int64_t)(((uint64_t)k * (uint64_t)opt.perm_mul) % (uint64_t)n_pad);
+    const int64_t j = opt.perm_mul == 1 ? k
+                                        : (int64_t)(((uint64_t)(k / kPermRun) * (uint64_t)opt.perm_mul) %
+                                                    (uint64_t)(n_pad / kPermRun)) * kPermRun + k % kPermRun;
     const bool real = j < n_atoms;
     // atom j of this call is atom a of the frames (a subset when an index is given)
     const int64_t a = (opt.index && real) ? (int64_t)opt.index[j] : j;
@@ -238,8 +242,9 @@ cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int6
     for (int i = 0; i < 9; ++i) hs.a[i] = hinv.a[i] * 4294967296.0;
     PhaseOpts o = opt;
     o.pos8 = ((uintptr_t)pos & 7u) == 0;
-    // atom of slot k = k * a mod n_pad; the products stay below 2^64
-    if (o.perm_mul != 1 && n_pad >= ((int64_t)1 << 32)) return cudaErrorInvalidValue;
+    // atom of slot k = kPermRun ((k / kPermRun) a mod n_pad / kPermRun) + k mod
+    // kPermRun; the products stay below 2^64
+    if (o.perm_mul != 1 && (n_pad >= ((int64_t)1 << 32) || n_pad % kPermRun != 0)) return cudaErrorInvalidValue;
     // orthorhombic cells: |x| < lim_x keeps |hs_xx x| below 2^50 (the FP32
     // bound is rounded down, so the check is conservative)
     for (int a = 0; a < 3; ++a) {

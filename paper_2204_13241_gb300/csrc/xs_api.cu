@@ -72,8 +72,8 @@ int64_t gcd64(int64_t a, int64_t b) {
     return a;
 }
 
-// odd multiplier near 0.618 n coprime with n: k -> k*a mod n visits the atoms
-// far apart in input order (a bijection on [0, n))
+// odd multiplier near 0.618 n coprime with n: k -> k*a mod n visits the atom
+// runs far apart in input order (a bijection on [0, n))
 int64_t coprime_stride(int64_t n) {
     if (n <= 2) return 1;
     int64_t a = (int64_t)(0.6180339887498949 * (double)n) | 1;
@@ -413,7 +413,7 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
     PhaseOpts popt;
     popt.ortho = is_ortho(hinv);
     popt.need_z = !(g.nz == 1 && g.nz0 == 0);
-    popt.perm_mul = use_tc ? coprime_stride(n_pad) : 1;
+    popt.perm_mul = use_tc ? coprime_stride(n_pad / kPermRun) : 1;
 
     // frames per chunk: records and (for host positions) staged positions
     const size_t rec_per_frame = (size_t)n_pad * sizeof(AtomRec);
@@ -713,7 +713,7 @@ xs_status xs_intensity_points(xs_context* ctx, const xs_traj* traj, const int32_
     popt.need_z = false;
     for (int64_t p = 0; p < P; ++p)
         if (miller[3 * p + 2] != 0) popt.need_z = true;
-    popt.perm_mul = use_tc ? coprime_stride(n_pad) : 1;
+    popt.perm_mul = use_tc ? coprime_stride(n_pad / kPermRun) : 1;
 
     // tensor cores: the points grouped by n_z plane, each plane's bounding box
     // tiled; only tiles that hold a point are computed
@@ -975,7 +975,7 @@ xs_status xs_intensity_species(xs_context* ctx, const xs_traj* traj, const int32
             PhaseOpts popt;
             popt.ortho = is_ortho(hinv);
             popt.need_z = !(g.nz == 1 && g.nz0 == 0);
-            popt.perm_mul = use_tc ? coprime_stride(n_pad) : 1;
+            popt.perm_mul = use_tc ? coprime_stride(n_pad / kPermRun) : 1;
             popt.index = d_index + start[(size_t)sp];
             popt.pos_atoms = N;
             const float* pos_c = traj->pos + (size_t)t0 * N * 3;
@@ -1115,7 +1115,7 @@ xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qg
             PhaseOpts popt;
             popt.ortho = is_ortho(j.hinv);
             popt.need_z = !(j.g.nz == 1 && j.g.nz0 == 0);
-            popt.perm_mul = coprime_stride(j.n_pad);
+            popt.perm_mul = coprime_stride(j.n_pad / kPermRun);
             cudaError_t err = launch_phase(t.pos, t.f, j.N, j.T, j.n_pad, hm, popt,
                                            reinterpret_cast<AtomRec*>(ws + j.rec_off), ctx->d_err, st);
             if (err != cudaSuccess) return err;

@@ -23,14 +23,16 @@ struct GridDesc {
 };
 
 // ---- phase records (fractional coordinates as 32-bit turns) -------------
-// rec [n_frames][n_pad]; slot k of a frame holds atom j = (k * perm_mul) mod
-// n_pad (perm_mul coprime with n_pad; 1 keeps the input order); atoms >=
-// n_atoms get f = 0 and U = 0.  `ortho`: h^-1 is diagonal; `need_z`: U_z is
-// used (otherwise it is left 0).
+// rec [n_frames][n_pad]; the slots hold runs of kPermRun consecutive atoms:
+// slot k of a frame holds atom j = kPermRun ((k / kPermRun) perm_mul mod
+// n_pad / kPermRun) + k mod kPermRun (perm_mul coprime with n_pad / kPermRun;
+// 1 keeps the input order); atoms >= n_atoms get f = 0 and U = 0.  `ortho`:
+// h^-1 is diagonal; `need_z`: U_z is used (otherwise it is left 0).
+constexpr int64_t kPermRun = 8;
 struct PhaseOpts {
     bool ortho = false;
     bool need_z = true;
-    int64_t perm_mul = 1;                // slot k holds atom k * perm_mul mod n_pad
+    int64_t perm_mul = 1;                // permutes the runs of kPermRun atoms
     float lim[3] = {0.0f, 0.0f, 0.0f};  // set by launch_phase
     const int32_t* index = nullptr;      // optional device [n_atoms]: atoms of the frames to use
     int64_t pos_atoms = 0;               // atoms per frame of `pos` when `index` is given
