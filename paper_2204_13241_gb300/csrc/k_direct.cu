@@ -1,10 +1,10 @@
 // Phase records and the plain FP32 direct sum (Algorithm 1, Sec. 3.1).
 //
-// phase_kernel: one thread per (frame, atom slot).  s = h^-1 r in FP64, then
-//   each axis is reduced to its fractional part and quantised to a 32-bit
-//   turn count.  This is the only FP64 work per atom (one multiply per axis
-//   for an orthorhombic cell); every later phase n_x*U_x + n_y*U_y + n_z*U_z
-//   is exact integer arithmetic modulo one turn.  Slots may hold the atoms in
+// phase_kernel: one thread per (frame, atom slot).  s = h^-1 r is reduced
+//   to its fractional part per axis and quantised to a 32-bit turn count: in
+//   exact integer arithmetic for an orthorhombic cell, in FP64 otherwise.
+//   Every later phase n_x*U_x + n_y*U_y + n_z*U_z is exact integer
+//   arithmetic modulo one turn.  Slots may hold the atoms in
 //   a coprime-stride order of runs of 8 (slot 8q + r holds atom
 //   8 (q*a mod n_pad/8) + r): summing in that order turns the coherent partial
 //   sums of an ordered crystal into random walks, while a run of 8 atoms (two
@@ -37,15 +37,46 @@ constexpr int kAtomTile = 256;   // atom records staged per shared-memory tile
 // hs = 2^32 h^-1 (a power-of-two scaling, exact): rint(hs r) mod 2^32 equals
 // rint(frac(h^-1 r) 2^32) mod 2^32.  Adding M = 1.5 * 2^52 to |v| < 2^51 gives
 // M + rint(v) (ties to even) in one FP64 rounding, and the low 32 bits of that
-// sum's encoding are rint(v) mod 2^32; in an FMA the product is not rounded
-// first.  GB300's FP64 pipe is narrow, so this replaces a multiply and a
-// conversion per axis by one FMA.
+// sum's encoding are rint(v) mod 2^32.
 constexpr double kRoundMagic = 6755399441055744.0;      // 1.5 * 2^52
 constexpr double kTurnLimit = 1125899906842624.0;       // 2^50: |v| bound checked
-__device__ __forceinline__ uint32_t turns_fma(double a, double b) {
-    return (uint32_t)__double2loint(fma(a, b, kRoundMagic));
-}
 __device__ __forceinline__ uint32_t turns_of(double v) { return (uint32_t)__double2loint(v + kRoundMagic); }
+
+// The count for an orthorhombic cell in integer arithmetic: x = +-m 2^ex
+// (m the float's 24-bit significand) times c = +-cm 2^ce (cm < 2^53) is the
+// exact product m cm = H 2^32 + L (two 32 x 32 -> 64-bit multiplies, H <
+// 2^45) scaled by 2^-d, d = -(ex + ce).  The turns are bits d.. of m cm,
+// rounded to nearest with ties to even from the bit below (rb) and those
+// under it (sticky), as the FP64 rounding above does.  GB300 issues FP64 at a
+// small fraction of its integer rate, and this was the phase kernel's only
+// FP64 work.
+__device__ __forceinline__ uint32_t turns_int(float x, uint32_t ch, uint32_t cl, int ce, uint32_t cneg) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t E = (b >> 23) & 0xffu;
+    const uint32_t m = E ? ((b & 0x7fffffu) | 0x800000u) : (b & 0x7fffffu);
+    const int d = -((E ? (int)E - 150 : -149) + ce);
+    const uint64_t A = (uint64_t)m * cl;
+    const uint64_t H = (uint64_t)m * ch + (A >> 32);
+    const uint32_t L = (uint32_t)A;
+    uint32_t u;
+    if (d > 32 && d <= 77) {  // the usual case: |x c| < 2^45
+        const int e = d - 32;
+        const uint32_t q = (uint32_t)(H >> e);
+        const uint32_t rb = (uint32_t)(H >> (e - 1)) & 1u;
+        const uint32_t st = ((H & ((1ull << (e - 1)) - 1ull)) != 0ull || L != 0u) ? 1u : 0u;
+        u = q + (rb & (st | (q & 1u)));
+    } else if (d > 77) {
+        u = 0u;  // |x c| < 1/2
+    } else if (d > 0) {
+        const uint32_t q = d == 32 ? (uint32_t)H : (((uint32_t)H << (32 - d)) | (L >> d));
+        const uint32_t rb = (L >> (d - 1)) & 1u;
+        const uint32_t st = (L & ((1u << (d - 1)) - 1u)) != 0u ? 1u : 0u;
+        u = q + (rb & (st | (q & 1u)));
+    } else {
+        u = d <= -32 ? 0u : L << -d;
+    }
+    return ((b >> 31) ^ cneg) ? 0u - u : u;
+}
 
 constexpr int kPhaseFrames = 8;  // frames per block of the phase kernel
 
@@ -94,9 +125,9 @@ phase_kernel(const float* __restrict__ pos, const float* __restrict__ f, int64_t
             if (opt.ortho) {
                 ok = ok && fabsf(x) < opt.lim[0] && fabsf(y) < opt.lim[1] && fabsf(z) < opt.lim[2];
                 if (ok) {
-                    r.ux = turns_fma((double)x, hs.a[0]);
-                    r.uy = turns_fma((double)y, hs.a[4]);
-                    if (opt.need_z) r.uz = turns_fma((double)z, hs.a[8]);
+                    r.ux = turns_int(x, opt.ch[0], opt.cl[0], opt.ce[0], opt.cneg[0]);
+                    r.uy = turns_int(y, opt.ch[1], opt.cl[1], opt.ce[1], opt.cneg[1]);
+                    if (opt.need_z) r.uz = turns_int(z, opt.ch[2], opt.cl[2], opt.ce[2], opt.cneg[2]);
                 }
             } else {
                 const double vx = hs.a[0] * x + hs.a[1] * y + hs.a[2] * z;
@@ -250,6 +281,14 @@ cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int6
     for (int a = 0; a < 3; ++a) {
         const double d = std::fabs(hs.a[4 * a]);
         o.lim[a] = d > 0.0 ? std::nextafter((float)(1125899906842624.0 / d), 0.0f) : 3.0e38f;
+        // d = cm 2^ce with cm < 2^53 an integer (exact: frexp only moves the exponent)
+        int e = 0;
+        const double fr = std::frexp(d, &e);
+        const uint64_t cm = (uint64_t)std::ldexp(fr, 53);
+        o.ch[a] = (uint32_t)(cm >> 32);
+        o.cl[a] = (uint32_t)cm;
+        o.ce[a] = e - 53;
+        o.cneg[a] = hs.a[4 * a] < 0.0 ? 1u : 0u;
     }
     dim3 grid((unsigned)((n_pad + 255) / 256), (unsigned)gy);
     ++tl_kernel_launches;

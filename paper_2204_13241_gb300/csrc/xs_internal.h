@@ -37,6 +37,11 @@ struct PhaseOpts {
     const int32_t* index = nullptr;      // optional device [n_atoms]: atoms of the frames to use
     int64_t pos_atoms = 0;               // atoms per frame of `pos` when `index` is given
     bool pos8 = false;                   // set by launch_phase: `pos` is 8-byte aligned
+    // set by launch_phase for orthorhombic cells: 2^32 h^-1_aa = (-1)^cneg cm 2^ce
+    // with cm = ch 2^32 + cl a 53-bit integer
+    uint32_t ch[3] = {0, 0, 0}, cl[3] = {0, 0, 0};
+    int ce[3] = {0, 0, 0};
+    uint32_t cneg[3] = {0, 0, 0};
 };
 cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int64_t n_frames,
                          int64_t n_pad, const Mat3& hinv, const PhaseOpts& opt, AtomRec* rec, int* err,

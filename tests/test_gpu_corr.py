@@ -25,6 +25,11 @@ def xs():
     (200, 129, list(range(0, 40))),         # more delays than one group
     (1, 5, [0]),
     (1000, 4096, list(wl.log_delays(1000))),
+    # frame segments are whole 64-frame blocks, up to 8: at 577 and 1,100
+    # frames the last segments hold no frame and must still add zeros
+    (577, 200, [0, 1, 3, 64, 576]),
+    (1100, 300, [1, 2, 3, 17, 1099]),
+    (40000, 64, [0, 1, 7, 4095, 4096, 39999]),  # several 4,096-frame FP32 blocks per segment
 ])
 def test_g2_stage_parity(xs, T, P, taus):
     rng = np.random.default_rng(T + P)
