@@ -6,10 +6,13 @@
 //   I[t][p] and I[t+tau][p] are coalesced across the pixels of a warp.
 //   Products are summed with compensated (Kahan) FP32 updates over blocks of
 //   64 frames and the block sums are added in FP64; the mean is summed in
-//   FP64 directly.  Each segment writes FP64 partial sums; g2_finish_kernel
-//   adds the segments in order and divides.  The segments (up to 8, each a
-//   whole number of 64-frame blocks) give the kernel enough warps to hide the
-//   load latency.
+//   FP64 directly, by the blocks of the first delay group.  The kernel is
+//   bound by instruction issue: frames whose delays all stay inside the
+//   series run a loop with one pointer step per frame and a precomputed
+//   offset per delay, without bound checks.  Each segment writes FP64
+//   partial sums; g2_finish_kernel adds the segments in order and divides.
+//   The segments (up to 8, each a whole number of 64-frame blocks) give the
+//   kernel more blocks.
 //
 // XSVS: pixels are first permuted ring by ring (host-built permutation), then
 //   prefix_kernel   C[t][p'] = sum_{t'<t} I[t'][perm[p']]       (FP64, [T+1][P'])
@@ -48,9 +51,15 @@ g2_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __re
     __syncthreads();
     const int64_t p = blockIdx.x * (int64_t)kG2Threads + threadIdx.x;
     if (p >= P) return;
-    int tau[kTauGroup];
+    // offset of I[t + tau_k][p] from I[t][p]; unused delays of a partial
+    // group point at I[t][p] itself and are never written out
+    int64_t off[kTauGroup];
+    int tau_max = 0;
 #pragma unroll
-    for (int k = 0; k < kTauGroup; ++k) tau[k] = s_tau[k];
+    for (int k = 0; k < kTauGroup; ++k) {
+        off[k] = (int64_t)s_tau[k] * P;
+        tau_max = max(tau_max, s_tau[k]);
+    }
     float acc[kTauGroup], comp[kTauGroup];
     double dacc[kTauGroup];
 #pragma unroll
@@ -59,16 +68,34 @@ g2_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __re
         dacc[k] = 0.0;
     }
     double dmean = 0.0;
+    const bool want_mean = blockIdx.y == 0;  // the first delay group sums the mean
     const int64_t seg0 = (int64_t)blockIdx.z * seg_len, seg1 = min(T, seg0 + seg_len);
     for (int64_t t0 = seg0; t0 < seg1; t0 += kFlush) {
         const int64_t t1 = min(seg1, t0 + kFlush);
-        for (int64_t t = t0; t < t1; ++t) {
-            const float x = I[t * P + p];
-            dmean += (double)x;
+        // frames t < T - tau_max have every delay inside the series: the loop
+        // over them carries no bound checks and no index arithmetic but one
+        // pointer step (the kernel is bound by instruction issue)
+        const int64_t tf = max(t0, min(t1, T - (int64_t)tau_max));
+        const float* row = I + t0 * P + p;
+        int64_t t = t0;
+        for (; t < tf; ++t, row += P) {
+            const float x = row[0];
+            if (want_mean) dmean += (double)x;
 #pragma unroll
             for (int k = 0; k < kTauGroup; ++k) {
-                if (k < nt && t + tau[k] < T) {
-                    const float y = fmaf(x, I[(t + tau[k]) * P + p], -comp[k]);
+                const float y = fmaf(x, row[off[k]], -comp[k]);
+                const float s = acc[k] + y;
+                comp[k] = (s - acc[k]) - y;
+                acc[k] = s;
+            }
+        }
+        for (; t < t1; ++t, row += P) {
+            const float x = row[0];
+            if (want_mean) dmean += (double)x;
+#pragma unroll
+            for (int k = 0; k < kTauGroup; ++k) {
+                if (k < nt && t + s_tau[k] < T) {
+                    const float y = fmaf(x, row[off[k]], -comp[k]);
                     const float s = acc[k] + y;
                     comp[k] = (s - acc[k]) - y;
                     acc[k] = s;
@@ -82,7 +109,7 @@ g2_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __re
         }
     }
     const int64_t seg = blockIdx.z;
-    if (blockIdx.y == 0) mpart[seg * P + p] = dmean;
+    if (want_mean) mpart[seg * P + p] = dmean;
 #pragma unroll
     for (int k = 0; k < kTauGroup; ++k) {
         if (k < nt) part[(seg * n_tau + g0 + k) * P + p] = dacc[k];
