@@ -57,6 +57,7 @@ def _args():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-table1", action="store_true")
+    ap.add_argument("--no-next", action="store_true", help="skip the ISF, Ewald-slice and species timings")
     return ap.parse_args()
 
 
@@ -401,6 +402,61 @@ def run_ours(args):
                                                 "direct_81x81x81_grid": 416.8243, "fft_method_n400": 0.4527},
             "note": "paper: Table 1, 32 CPUs (model unstated), its own Ar frames; context, not a like-for-like ratio"}
         del pos_ar
+        torch.cuda.empty_cache()
+
+    # ---- the rows beyond the hot path, on the same crystal: per-species form
+    # factors, the Ewald-sphere slice through the point path, and the
+    # intermediate scattering function with its Siegert contrast
+    if not args.no_next and rank == 0:
+        def ms_per_call(fn, reps=3):
+            fn()
+            torch.cuda.synchronize()
+            ctx.sync_status()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            ctx.sync_status()
+            return e0.elapsed_time(e1) / reps
+
+        nf = min(100, T)
+        sub = pos_d[:nf].contiguous()
+        t_plane = ms_per_call(lambda: xs.intensity(sub, f_d, box, grid, args.precision))
+        plane_units = float(N) * P * nf
+        # two species (alternate atoms) with synthetic four-Gaussian form factors
+        species = np.arange(N, dtype=np.int32) % 2
+        coef = np.array([[8.0, 12.0, 6.0, 1.5, 3.0, 40.0, 1.0, 90.0, 0.5],
+                         [4.0, 20.0, 2.5, 4.0, 1.2, 0.6, 0.8, 60.0, 0.3]], dtype=np.float64)
+        t_sp = ms_per_call(lambda: xs.intensity_species(sub, f_d, species, coef, box, grid, args.precision))
+        # Ewald slice: beam along z, wavelength 1 A, over the 128 x 128 detector window
+        k_in = [0.0, 0.0, 2.0 * math.pi / 1.0]
+        mil, valid = xs.ewald_points(box, k_in, grid.nx0, grid.nx, grid.ny0, grid.ny)
+        mil = mil[valid]
+        t_pt = ms_per_call(lambda: xs.intensity_points(sub, f_d, box, mil, args.precision))
+        # ISF on the amplitudes of the full series, same delays as g2
+        _, amp = xs.intensity(pos_d, f_d, box, grid, args.precision, want_amp=True)
+        sum_f2 = float((traj.f.astype(np.float64) ** 2).sum())
+        t_isf = ms_per_call(lambda: xs.isf(amp, taus, sum_f2))
+        Kmax = max(Ks)
+        _, Fh = xs.isf(amp, list(range(Kmax)), sum_f2)
+        t_cf = ms_per_call(lambda: xs.contrast_from_isf(Fh, grid, box, Ks, R))
+        pairs = float(P) * sum(T - t for t in taus)
+        line["next_rows"] = {
+            "frames": nf,
+            "plane_reference": {"value": plane_units / (t_plane * 1e-3), "unit": METRIC, "ms_per_call": t_plane},
+            "species_form_factors": {"value": plane_units / (t_sp * 1e-3), "unit": METRIC, "ms_per_call": t_sp,
+                                     "species": 2, "coefficients": "synthetic four-Gaussian sums"},
+            "ewald_slice_points": {"value": float(N) * mil.shape[0] * nf / (t_pt * 1e-3),
+                                   "unit": "atom*point*frames/s", "ms_per_call": t_pt,
+                                   "points": int(mil.shape[0]),
+                                   "n_z_planes": int(np.unique(mil[:, 2]).size),
+                                   "beam": "along z, wavelength 1 A, 128 x 128 detector window"},
+            "isf": {"value": pairs / (t_isf * 1e-3), "unit": "pixel*delay*frame products/s",
+                    "ms_per_call": t_isf, "frames": T, "n_tau": len(taus)},
+            "contrast_from_isf": {"ms_per_call": t_cf, "delays": Kmax, "window_lengths": len(Ks)}}
+        del sub, amp, Fh
         torch.cuda.empty_cache()
 
     # ---- the batched workload: 64 ideal-gas trajectories in one persistent launch
