@@ -146,9 +146,15 @@ isf_kernel(const float2* __restrict__ S, int64_t T, int64_t P, const int32_t* __
     __syncthreads();
     const int64_t p = blockIdx.x * (int64_t)kG2Threads + threadIdx.x;
     if (p >= P) return;
-    int tau[kIsfGroup];
+    // offset of S[t + tau_k][p] from S[t][p]; unused delays of a partial group
+    // point at S[t][p] itself and are never written out
+    int64_t off[kIsfGroup];
+    int tau_max = 0;
 #pragma unroll
-    for (int k = 0; k < kIsfGroup; ++k) tau[k] = s_tau[k];
+    for (int k = 0; k < kIsfGroup; ++k) {
+        off[k] = (int64_t)s_tau[k] * P;
+        tau_max = max(tau_max, s_tau[k]);
+    }
     float are[kIsfGroup], cre[kIsfGroup], aim[kIsfGroup], cim[kIsfGroup];
     double dre[kIsfGroup], dim[kIsfGroup];
 #pragma unroll
@@ -157,26 +163,35 @@ isf_kernel(const float2* __restrict__ S, int64_t T, int64_t P, const int32_t* __
         dre[k] = dim[k] = 0.0;
     }
     double dmean = 0.0;
+    // conj(a) b = (a.x b.x + a.y b.y) + i (a.x b.y - a.y b.x), compensated
+    auto add = [&](int k, float2 a, float2 b) {
+        const float yr = fmaf(a.x, b.x, fmaf(a.y, b.y, -cre[k]));
+        const float sr = are[k] + yr;
+        cre[k] = (sr - are[k]) - yr;
+        are[k] = sr;
+        const float yi = fmaf(a.x, b.y, fmaf(-a.y, b.x, -cim[k]));
+        const float si = aim[k] + yi;
+        cim[k] = (si - aim[k]) - yi;
+        aim[k] = si;
+    };
     for (int64_t t0 = 0; t0 < T; t0 += kFlush) {
         const int64_t t1 = min(T, t0 + kFlush);
-        for (int64_t t = t0; t < t1; ++t) {
-            const float2 a = S[t * P + p];
+        // frames whose delays all stay inside the series: no bound checks
+        const int64_t tf = max(t0, min(t1, T - (int64_t)tau_max));
+        const float2* row = S + t0 * P + p;
+        int64_t t = t0;
+        for (; t < tf; ++t, row += P) {
+            const float2 a = row[0];
             dmean = fma((double)a.x, (double)a.x, fma((double)a.y, (double)a.y, dmean));
 #pragma unroll
-            for (int k = 0; k < kIsfGroup; ++k) {
-                if (k < nt && t + tau[k] < T) {
-                    const float2 b = S[(t + tau[k]) * P + p];
-                    // conj(a) b = (a.x b.x + a.y b.y) + i (a.x b.y - a.y b.x)
-                    const float yr = fmaf(a.x, b.x, fmaf(a.y, b.y, -cre[k]));
-                    const float sr = are[k] + yr;
-                    cre[k] = (sr - are[k]) - yr;
-                    are[k] = sr;
-                    const float yi = fmaf(a.x, b.y, fmaf(-a.y, b.x, -cim[k]));
-                    const float si = aim[k] + yi;
-                    cim[k] = (si - aim[k]) - yi;
-                    aim[k] = si;
-                }
-            }
+            for (int k = 0; k < kIsfGroup; ++k) add(k, a, row[off[k]]);
+        }
+        for (; t < t1; ++t, row += P) {
+            const float2 a = row[0];
+            dmean = fma((double)a.x, (double)a.x, fma((double)a.y, (double)a.y, dmean));
+#pragma unroll
+            for (int k = 0; k < kIsfGroup; ++k)
+                if (k < nt && t + s_tau[k] < T) add(k, a, row[off[k]]);
         }
 #pragma unroll
         for (int k = 0; k < kIsfGroup; ++k) {
@@ -189,7 +204,7 @@ isf_kernel(const float2* __restrict__ S, int64_t T, int64_t P, const int32_t* __
 #pragma unroll
     for (int k = 0; k < kIsfGroup; ++k) {
         if (k < nt) {
-            const double n = (double)(T - tau[k]);
+            const double n = (double)(T - s_tau[k]);
             const double re = dre[k] / n, im = dim[k] / n;
             const int64_t o = (int64_t)(g0 + k) * P + p;
             F[o] = make_double2(re * inv_sum_f2, im * inv_sum_f2);
