@@ -8,6 +8,7 @@
 #include <map>
 #include <string>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "xs_api.h"
@@ -423,6 +424,24 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
     if ((size_t)T * rec_per_frame > cap) fchunk = std::max<int64_t>(1, (int64_t)(cap / rec_per_frame));
     if (pos_host) fchunk = std::min<int64_t>(fchunk, std::max<int64_t>(1, (int64_t)((size_t)1 << 30) / std::max<size_t>(pos_per_frame, 1)));
     if (fchunk > 65535) fchunk = 65535;
+    // chunks (first frame, frames).  Streamed host positions on the tensor
+    // path start with about 64 MB and double up to fchunk: only the first copy
+    // is exposed, and each later copy (twice the frames) hides behind the
+    // previous chunk's kernels as long as the host link moves a frame's
+    // positions faster than the kernels take for half a frame
+    std::vector<std::pair<int64_t, int64_t>> chunks;
+    {
+        int64_t nf = fchunk;
+        if (pos_host && use_tc)
+            nf = std::min<int64_t>(fchunk, std::max<int64_t>(1, (int64_t)((size_t)64 << 20) /
+                                                                   std::max<size_t>(pos_per_frame, 1)));
+        for (int64_t t0 = 0; t0 < T;) {
+            const int64_t n = std::min(nf, T - t0);
+            chunks.emplace_back(t0, n);
+            t0 += n;
+            nf = std::min(fchunk, 2 * nf);
+        }
+    }
 
     DirectPlan dplan{};
     int tc_pairs = 0;
@@ -450,9 +469,10 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
         return tc_split_plan(tc_units(tc_traj(nullptr, n_pad, nf, g, nullptr, nullptr)), tc_pairs,
                              (int)(n_pad / tc_atom_multiple()), chunk_stages);
     };
-    const size_t o_split = carve(use_tc ? std::max(tc_split_bytes(split_of(fchunk)),
-                                                   tc_split_bytes(split_of(T - (T - 1) / fchunk * fchunk)))
-                                        : 0);
+    size_t split_bytes = 0;
+    if (use_tc)
+        for (const auto& ch : chunks) split_bytes = std::max(split_bytes, tc_split_bytes(split_of(ch.second)));
+    const size_t o_split = carve(split_bytes);
     const size_t o_pos0 = carve(pos_host ? (size_t)fchunk * pos_per_frame : 0);
     const size_t o_pos1 = carve(pos_host ? (size_t)fchunk * pos_per_frame : 0);
     const size_t o_f = carve(pos_host ? (size_t)N * sizeof(float) : 0);
@@ -469,14 +489,14 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
         f_dev = reinterpret_cast<float*>(ws + o_f);
     }
 
-    const int64_t n_chunks = (T + fchunk - 1) / fchunk;
+    const int64_t n_chunks = (int64_t)chunks.size();
     if (pos_host && N > 0) {
         // the copy stream starts after everything already on the caller's stream
         XS_CUDA(cudaEventRecord(ctx->ev_consumed[0], st));
         XS_CUDA(cudaEventRecord(ctx->ev_consumed[1], st));
     }
     auto issue_copy = [&](int64_t c) -> xs_status {
-        const int64_t t0 = c * fchunk, nf = std::min(fchunk, T - t0);
+        const int64_t t0 = chunks[(size_t)c].first, nf = chunks[(size_t)c].second;
         const int b = (int)(c & 1);
         XS_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_consumed[b], 0));
         XS_CUDA(cudaMemcpyAsync(pos_stage[b], traj->pos + (size_t)t0 * N * 3, (size_t)nf * pos_per_frame,
@@ -489,7 +509,7 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
         if (s != XS_OK) return s;
     }
     for (int64_t c = 0; c < n_chunks; ++c) {
-        const int64_t t0 = c * fchunk, nf = std::min(fchunk, T - t0);
+        const int64_t t0 = chunks[(size_t)c].first, nf = chunks[(size_t)c].second;
         float* Ic = out_dev ? I_out + (size_t)t0 * P : reinterpret_cast<float*>(ws + o_I);
         float* Ac = amp_out ? (out_dev ? amp_out + (size_t)t0 * P * 2 : reinterpret_cast<float*>(ws + o_amp)) : nullptr;
         if (N == 0) {

@@ -121,6 +121,26 @@ def test_host_streamed_positions_match_device(xs):
     assert np.array_equal(host_out.numpy(), dev)
 
 
+def test_host_streaming_over_several_chunks(xs):
+    # 64,000 atoms are 768 kB per frame: host positions are streamed in chunks
+    # that start near 64 MB (87 frames) and double, so 200 frames take two
+    # chunks with their own launches; the output goes to host memory too
+    pos, f, box = _case(13, 64000, 200, 90.0, f_mixed=False)
+    grid = wl.QGrid(-32, 64, -32, 64, 0, 1)
+    dev = _run(xs, pos, f, box, grid, "fp16")
+    hp = torch.from_numpy(pos).pin_memory()
+    hf = torch.from_numpy(f).pin_memory()
+    host_out = xs.intensity(hp, hf, box, grid, "fp16").numpy().reshape(200, -1)
+    m = grid.miller()
+    err, err0 = e_I(host_out, dev.reshape(200, -1), m)
+    assert err <= 1e-4 and err0 <= 1e-6, (err, err0)
+    pix = np.random.default_rng(3).choice(m.shape[0], 48, replace=False)
+    for t in (0, 86, 87, 199):  # both sides of the chunk boundary
+        ref = oracle.intensity(pos[t:t + 1], f, box, m[pix])
+        e, e0 = e_I(host_out[t:t + 1, pix], ref, m[pix])
+        assert e <= 1e-4 and e0 <= 1e-4, (t, e, e0)
+
+
 def test_nonfinite_position_is_reported(xs):
     from paper_2204_13241_gb300 import _native as nat
     pos, f, box = _case(12, 100, 1, 10.0)
