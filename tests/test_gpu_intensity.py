@@ -154,6 +154,57 @@ def test_nonfinite_position_is_reported(xs):
     xs.Context.get().sync_status()  # cleared
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_periodic_images_give_identical_records(xs, prec):
+    # box 16 and positions on a 2^-8 grid: shifts by up to 2^10 boxes stay
+    # exact in float32, and the turn counts rint(x 2^32 / 16) mod 2^32 of an
+    # atom and of its images agree, so the intensities agree bit for bit
+    rng = np.random.default_rng(21)
+    N, T, L = 3000, 2, 16.0
+    pos = (np.floor(rng.random((T, N, 3)) * L * 256) / 256).astype(np.float32)
+    shift = rng.integers(-1024, 1025, (T, N, 3)).astype(np.float32) * np.float32(L)
+    far = (pos + shift).astype(np.float32)
+    assert np.array_equal(far - shift, pos)
+    f = rng.uniform(0.5, 1.5, N).astype(np.float32)
+    box = np.eye(3) * L
+    grid = wl.QGrid(-40, 80, -40, 80, 0, 1)
+    I0 = _run(xs, pos, f, box, grid, prec)
+    I1 = _run(xs, far, f, box, grid, prec)
+    assert np.array_equal(I0, I1)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_unwrapped_positions_far_from_the_cell(xs, prec):
+    # a box that is no power of two, atoms about 1,000 and 2^17 boxes out
+    # (both signs): the integer turn counts stay exact there
+    rng = np.random.default_rng(22)
+    N, L = 1200, 21.7
+    base = rng.random((N, 3)) * L
+    k = np.where(rng.random((N, 3)) < 0.5, 1000.0, 2.0 ** 17) * np.where(rng.random((N, 3)) < 0.5, 1.0, -1.0)
+    pos = (base + k * L).astype(np.float32)[None]
+    f = rng.uniform(0.5, 1.5, N).astype(np.float32)
+    box = np.eye(3) * L
+    grid = wl.QGrid(-16, 32, -16, 32, -1, 3)
+    I = _run(xs, pos, f, box, grid, prec)
+    ref = oracle.intensity(pos, f, box, grid.miller())
+    err, e0 = e_I(I, ref, grid.miller())
+    assert err <= TOL[prec] and e0 <= TOL[prec], (err, e0)
+
+
+def test_position_beyond_the_turn_range_is_reported(xs):
+    # more than 2^18 cells out: rejected through the error word
+    from paper_2204_13241_gb300 import _native as nat
+    pos, f, box = _case(14, 300, 1, 10.0)
+    pos[0, 5, 0] = np.float32(10.0 * 2.0 ** 19)
+    p = torch.from_numpy(pos).cuda()
+    fd = torch.from_numpy(f).cuda()
+    xs.intensity(p, fd, box, wl.QGrid(-64, 128, -64, 128, 0, 1), "fp16")
+    with pytest.raises(nat.XsError) as ei:
+        xs.Context.get().sync_status()
+    assert ei.value.status == 6
+    xs.Context.get().sync_status()  # cleared
+
+
 def test_bounded_wait_timeout_is_reported_and_context_survives(xs):
     from paper_2204_13241_gb300 import _native as nat
     pos, f, box = _case(13, 4096, 4, 20.0)
