@@ -131,6 +131,13 @@ XS_API xs_status xs_intensity(xs_context* ctx, const xs_traj* traj, const xs_qgr
  * Many independent trajectories in one persistent launch (the batched form
  * of Algorithm 1).  traj[i], grid[i] and I_out[i] as in xs_intensity, with
  * device positions; n_traj >= 1.  `traj`, `grid` and `I_out` are host arrays.
+ * A centred n_z = 0 plane [-nx/2, nx/2) x [-ny/2, ny/2) (even sizes) whose
+ * half n_x <= 0 (with n_y up to +ny/2) needs fewer 128 x 128 tiles, such as
+ * 192 x 192, is computed on that half and filled by I(-q) = I(q), which holds
+ * for the real form factors of this library (the intensity's pair form is a
+ * sum of f_i f_j cos(q.r_ij)); the half lives in the context workspace.
+ * With the split precisions, repeated calls with the same arguments replay
+ * one captured CUDA graph.
  */
 XS_API xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid,
                                int32_t n_traj, xs_precision prec, float* const* I_out,

@@ -7,7 +7,10 @@
 //   species_acc_kernel   acc[t][p] (+)= F_s(q_p) S_s[t][p], FP64 complex
 //   species_finish_kernel I = |acc|^2 and the amplitude, FP32
 // and the gather of arbitrary lattice points out of the planes that hold them
-// (points_gather_kernel).
+// (points_gather_kernel), and the fill of a centred n_z = 0 plane from the
+// half of it that the contraction computed (friedel_plane_kernel: for real
+// form factors S(-q) = conj S(q), so I(-q) = I(q), as the pair form of the
+// intensity, a sum of f_i f_j cos(q.r_ij), shows).
 #include <cmath>
 
 #include "xs_internal.h"
@@ -84,7 +87,49 @@ __global__ void points_gather_kernel(const float* __restrict__ tmp, const float*
     }
 }
 
+// one thread per output pixel of I [T][ny][nx] (grid g, n_z = 0): pixels with
+// n_x <= 0 are read from the half-plane `half` [T][v.ny][v.nx] computed on the
+// grid v, the others from their mirror -n
+__global__ void friedel_plane_kernel(const float* __restrict__ half, int64_t T, GridDesc v, GridDesc g,
+                                     float* __restrict__ I) {
+    const int64_t P = (int64_t)g.nx * g.ny;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= T * P) return;
+    const int64_t t = i / P;
+    const int64_t p = i - t * P;
+    const int iy = (int)(p / g.nx);
+    const int ix = (int)(p - (int64_t)iy * g.nx);
+    int x = g.nx0 + ix, y = g.ny0 + iy;
+    if (x > 0) {
+        x = -x;
+        y = -y;
+    }
+    I[i] = half[(t * v.ny + (y - v.ny0)) * v.nx + (x - v.nx0)];
+}
+
 }  // namespace
+
+bool friedel_half_grid(const GridDesc& g, GridDesc& v) {
+    // a centred n_z = 0 plane [-nx/2, nx/2) x [-ny/2, ny/2) (even sizes) is
+    // covered by n_x in [-nx/2, 0] and n_y in [-ny/2, ny/2] with mirrors; the
+    // half is used where it needs fewer 128 x 128 tiles (a 192^2 plane: 2
+    // instead of 4)
+    if (g.nz != 1 || g.nz0 != 0 || (g.nx & 1) || (g.ny & 1) || g.nx0 != -g.nx / 2 || g.ny0 != -g.ny / 2) return false;
+    v = g;
+    v.nx = g.nx / 2 + 1;
+    v.ny = g.ny + 1;
+    auto tiles = [](const GridDesc& d) { return (int64_t)((d.nx + 127) / 128) * ((d.ny + 127) / 128); };
+    return tiles(v) < tiles(g);
+}
+
+cudaError_t launch_friedel_plane(const float* half, int64_t T, const GridDesc& v, const GridDesc& g, float* I,
+                                 cudaStream_t st) {
+    const int64_t n = T * g.pixels();
+    if (n == 0) return cudaSuccess;
+    ++tl_kernel_launches;
+    friedel_plane_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(half, T, v, g, I);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_points_gather(const float* tmp, const float* tmp_amp, const int64_t* d_src, const int64_t* d_stride,
                                  int64_t P, int64_t nf, float* I, float* amp, cudaStream_t st) {

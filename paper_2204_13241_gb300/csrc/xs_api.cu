@@ -1054,6 +1054,9 @@ xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qg
         double hinv[9];
         GridDesc g;
         size_t rec_off;
+        bool half = false;  // centred plane computed as a half-plane plus mirrors
+        GridDesc v;         // the half-plane's grid
+        size_t half_off = 0;
     };
     std::vector<Job> jobs((size_t)n_traj);
     size_t off = 0;
@@ -1080,6 +1083,10 @@ xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qg
         j.g = to_desc(&grid[i]);
         if (j.T > 65535 * 8) return fail(XS_ERR_INVALID_ARG, "trajectory %d: too many frames", i);
         j.rec_off = carve((size_t)j.T * j.n_pad * sizeof(AtomRec));
+        if (j.N > 0 && j.T > 0 && friedel_half_grid(j.g, j.v)) {
+            j.half = true;
+            j.half_off = carve((size_t)j.T * j.v.pixels() * sizeof(float));
+        }
     }
     const int cap = tc_pair_capacity(ctx->num_sms);
     const size_t o_scratch = carve(tc_scratch_bytes(cap));
@@ -1098,7 +1105,11 @@ xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qg
             empty.push_back(i);
             continue;
         }
-        trs.push_back(tc_traj(reinterpret_cast<AtomRec*>(ws + j.rec_off), j.n_pad, j.T, j.g, I_out[i], nullptr));
+        if (j.half)
+            trs.push_back(tc_traj(reinterpret_cast<AtomRec*>(ws + j.rec_off), j.n_pad, j.T, j.v,
+                                  reinterpret_cast<float*>(ws + j.half_off), nullptr));
+        else
+            trs.push_back(tc_traj(reinterpret_cast<AtomRec*>(ws + j.rec_off), j.n_pad, j.T, j.g, I_out[i], nullptr));
         which.push_back(i);
     }
     for (int i : empty)
@@ -1140,15 +1151,23 @@ xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qg
                                            reinterpret_cast<AtomRec*>(ws + j.rec_off), ctx->d_err, st);
             if (err != cudaSuccess) return err;
         }
-        return launch_tc_batch(reinterpret_cast<const TcTraj*>(dc + o_tr), reinterpret_cast<const int4*>(dc + o_units),
-                               reinterpret_cast<const int*>(dc + o_ps), n_pairs, chunk, bf16,
-                               reinterpret_cast<double*>(ws + o_scratch), ctx->d_err, ctx->timeout_ns, st);
+        cudaError_t err = launch_tc_batch(reinterpret_cast<const TcTraj*>(dc + o_tr),
+                                          reinterpret_cast<const int4*>(dc + o_units),
+                                          reinterpret_cast<const int*>(dc + o_ps), n_pairs, chunk, bf16,
+                                          reinterpret_cast<double*>(ws + o_scratch), ctx->d_err, ctx->timeout_ns, st);
+        for (size_t e = 0; e < trs.size() && err == cudaSuccess; ++e) {
+            const Job& j = jobs[(size_t)which[e]];
+            if (j.half)
+                err = launch_friedel_plane(reinterpret_cast<const float*>(ws + j.half_off), j.T, j.v, j.g,
+                                           I_out[which[e]], st);
+        }
+        return err;
     };
     // the same batch (same tables, inputs, outputs and workspace) replays a
     // captured graph; anything else is captured once and kept
     std::string key(blob.begin(), blob.end());
     for (int32_t i = 0; i < n_traj; ++i) {
-        const void* ptrs[2] = {traj[i].pos, traj[i].f};
+        const void* ptrs[3] = {traj[i].pos, traj[i].f, I_out[i]};
         key.append(reinterpret_cast<const char*>(ptrs), sizeof(ptrs));
         key.append(reinterpret_cast<const char*>(traj[i].box.h), sizeof(traj[i].box.h));
     }
