@@ -103,9 +103,14 @@ def test_large_crystal_plane_streamed_from_host(xs, crystal4):
     pos_d = pos_h.cuda()
     I_d = xs.intensity(pos_d, f_h.cuda(), traj.box, grid, "fp16")
     xs.Context.get().sync_status()
-    assert torch.equal(I_h, I_d.cpu())
-    del pos_d, I_d
     m = grid.miller()
+    # streamed from host, the 16 frames (38 MB each) run as launches of 1, 2,
+    # 4, 8 and 1 frames, whose last waves are cut along the atoms elsewhere
+    # than in the single device launch: the FP32 accumulation groups differ,
+    # so the two agree to the method's tolerance, not bit for bit
+    e, e0 = e_I(I_h.reshape(16, -1).numpy(), I_d.reshape(16, -1).cpu().numpy().astype(np.float64), m)
+    assert e <= 1e-4 and e0 <= 1e-6, (e, e0)
+    del pos_d, I_d
     pix = _sample_pixels(m, 512, 41)
     frames = [0, 15]
     ref = oracle.intensity(traj.pos[frames], traj.f, traj.box, m[pix])
