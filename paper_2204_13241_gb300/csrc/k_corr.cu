@@ -266,7 +266,22 @@ __global__ void prefix_kernel(const float* __restrict__ I, int64_t T, int64_t P,
     const int64_t p = perm[q];
     double acc = 0.0;
     C[q] = 0.0;
-    for (int64_t t = 0; t < T; ++t) {
+    // eight frames' loads in flight per thread (the kernel has one thread per
+    // in-ring pixel, too few to hide load latency otherwise); the sums keep
+    // their sequential order
+    constexpr int kAhead = 8;
+    int64_t t = 0;
+    for (; t + kAhead <= T; t += kAhead) {
+        float x[kAhead];
+#pragma unroll
+        for (int k = 0; k < kAhead; ++k) x[k] = I[(t + k) * P + p];
+#pragma unroll
+        for (int k = 0; k < kAhead; ++k) {
+            acc += (double)x[k];
+            C[(t + k + 1) * n_in + q] = acc;
+        }
+    }
+    for (; t < T; ++t) {
         acc += (double)I[t * P + p];
         C[(t + 1) * n_in + q] = acc;
     }
@@ -274,6 +289,24 @@ __global__ void prefix_kernel(const float* __restrict__ I, int64_t T, int64_t P,
 
 // block = one chunk (ring, start, count) and a slice of `kw_slice` entries of
 // the (K,w) list; its warps stride over the slice
+// One warp takes 8 consecutive (K, w) entries: every lane sums x and x^2 over
+// its pixels of the chunk for all 8, then one transposed butterfly reduces
+// the 8 pairs together (lanes split the values in half at offsets 16, 8 and
+// 4, then add at 2 and 1), 9 FP64 additions per lane and sum instead of 40;
+// the kernel is bound by the FP64 pipe.  Lane 4j holds the totals of entry j.
+constexpr int kKwGroup = 8;
+
+__device__ __forceinline__ double halve(double* v, int n, int lane, int off) {
+    // v[0 .. 2n) -> v[0 .. n): lanes with the `off` bit keep the upper half
+    const bool up = (lane & off) != 0;
+    for (int k = 0; k < n; ++k) {
+        const double send = up ? v[k] : v[k + n];
+        const double keep = up ? v[k + n] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+    return v[0];
+}
+
 __global__ void window_kernel(const double* __restrict__ C, int64_t n_in, const int4* __restrict__ chunks,
                               int n_chunks, const int32_t* __restrict__ Ks, const int64_t* __restrict__ kw_off,
                               int n_K, int64_t n_kw, int64_t kw_slice, double2* __restrict__ partial) {
@@ -284,26 +317,40 @@ __global__ void window_kernel(const double* __restrict__ C, int64_t n_in, const 
     const int64_t kw0 = (int64_t)blockIdx.y * kw_slice;
     const int64_t kw1 = min(n_kw, kw0 + kw_slice);
     int ik = 0;
-    for (int64_t kw = kw0 + warp; kw < kw1; kw += nwarps) {
-        while (ik + 1 < n_K && kw >= kw_off[ik + 1]) ++ik;
-        while (ik > 0 && kw < kw_off[ik]) --ik;
-        const int64_t K = Ks[ik];
-        const int64_t w = kw - kw_off[ik];
-        const double* c0 = C + (w * K) * n_in;
-        const double* c1 = C + ((w + 1) * K) * n_in;
-        double s1 = 0.0, s2 = 0.0;
-        for (int i = lane; i < ch.z; i += 32) {
-            const int64_t q = ch.y + i;
-            const double x = c1[q] - c0[q];
-            s1 += x;
-            s2 = fma(x, x, s2);
-        }
+    for (int64_t base = kw0 + (int64_t)warp * kKwGroup; base < kw1; base += (int64_t)nwarps * kKwGroup) {
+        double s1[kKwGroup], s2[kKwGroup];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        for (int j = 0; j < kKwGroup; ++j) {
+            s1[j] = s2[j] = 0.0;
+            const int64_t kw = base + j;
+            if (kw >= kw1) continue;
+            while (ik + 1 < n_K && kw >= kw_off[ik + 1]) ++ik;
+            while (ik > 0 && kw < kw_off[ik]) --ik;
+            const int64_t K = Ks[ik];
+            const int64_t w = kw - kw_off[ik];
+            const double* c0 = C + (w * K) * n_in;
+            const double* c1 = C + ((w + 1) * K) * n_in;
+            for (int i = lane; i < ch.z; i += 32) {
+                const int64_t q = ch.y + i;
+                const double x = c1[q] - c0[q];
+                s1[j] += x;
+                s2[j] = fma(x, x, s2[j]);
+            }
         }
-        if (lane == 0) partial[kw * n_chunks + blockIdx.x] = make_double2(s1, s2);
+        halve(s1, 4, lane, 16);
+        halve(s1, 2, lane, 8);
+        double t1 = halve(s1, 1, lane, 4);
+        halve(s2, 4, lane, 16);
+        halve(s2, 2, lane, 8);
+        double t2 = halve(s2, 1, lane, 4);
+        t1 += __shfl_xor_sync(0xffffffffu, t1, 2);
+        t2 += __shfl_xor_sync(0xffffffffu, t2, 2);
+        t1 += __shfl_xor_sync(0xffffffffu, t1, 1);
+        t2 += __shfl_xor_sync(0xffffffffu, t2, 1);
+        // lane bits 16, 8, 4 chose the upper halves: entry j = 4 b16 + 2 b8 + b4
+        const int j = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        const int64_t kw = base + j;
+        if ((lane & 3) == 0 && kw < kw1) partial[kw * n_chunks + blockIdx.x] = make_double2(t1, t2);
     }
 }
 
