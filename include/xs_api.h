@@ -122,7 +122,14 @@ XS_API xs_status xs_context_destroy(xs_context* ctx);
  * Outputs may be device or host memory (detected per pointer); host outputs
  * make the call wait for the stream.  XS_PREC_SPLIT_* work in 128 x 128 tiles
  * of (n_x, n_y) per plane (a partial tile is computed whole and cut); any grid
- * size works with every precision.
+ * size works with every precision.  With device outputs, the split path
+ * contracts only half of a grid that is (nearly) symmetric under n -> -n when
+ * that needs fewer tiles, and fills the rest by S(-q) = conj S(q), which holds
+ * for the real form factors of this library: the half n_x <= 0 of a plane at
+ * n_z = 0, or the planes n_z <= 0 of a volume (the other axes widened to the
+ * hull of their range and its mirror).  A 192 x 192 centred plane takes 2
+ * tiles instead of 4 and the volume [-40, 40]^3 41 instead of 81; the half
+ * lives in the context workspace.
  */
 XS_API xs_status xs_intensity(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid,
                        xs_precision prec, float* I_out, float* amp_out, void* cuda_stream);
@@ -131,13 +138,11 @@ XS_API xs_status xs_intensity(xs_context* ctx, const xs_traj* traj, const xs_qgr
  * Many independent trajectories in one persistent launch (the batched form
  * of Algorithm 1).  traj[i], grid[i] and I_out[i] as in xs_intensity, with
  * device positions; n_traj >= 1.  `traj`, `grid` and `I_out` are host arrays.
- * A centred n_z = 0 plane [-nx/2, nx/2) x [-ny/2, ny/2) (even sizes) whose
- * half n_x <= 0 (with n_y up to +ny/2) needs fewer 128 x 128 tiles, such as
- * 192 x 192, is computed on that half and filled by I(-q) = I(q), which holds
- * for the real form factors of this library (the intensity's pair form is a
- * sum of f_i f_j cos(q.r_ij)); the half lives in the context workspace.
- * With the split precisions, repeated calls with the same arguments replay
- * one captured CUDA graph.
+ * Grids are contracted as halves filled by I(-q) = I(q) where that saves
+ * tiles, as in xs_intensity (the intensity's pair form is a sum of
+ * f_i f_j cos(q.r_ij), even in q for real form factors).  With the split
+ * precisions, repeated calls with the same arguments replay one captured
+ * CUDA graph.
  */
 XS_API xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid,
                                int32_t n_traj, xs_precision prec, float* const* I_out,

@@ -7,10 +7,11 @@
 //   species_acc_kernel   acc[t][p] (+)= F_s(q_p) S_s[t][p], FP64 complex
 //   species_finish_kernel I = |acc|^2 and the amplitude, FP32
 // and the gather of arbitrary lattice points out of the planes that hold them
-// (points_gather_kernel), and the fill of a centred n_z = 0 plane from the
-// half of it that the contraction computed (friedel_plane_kernel: for real
-// form factors S(-q) = conj S(q), so I(-q) = I(q), as the pair form of the
-// intensity, a sum of f_i f_j cos(q.r_ij), shows).
+// (points_gather_kernel), and the fill of a grid from the half of it that the
+// contraction computed (friedel_kernel: for real form factors S(-q) =
+// conj S(q), so I(-q) = I(q), as the pair form of the intensity, a sum of
+// f_i f_j cos(q.r_ij), shows).
+#include <algorithm>
 #include <cmath>
 
 #include "xs_internal.h"
@@ -87,47 +88,78 @@ __global__ void points_gather_kernel(const float* __restrict__ tmp, const float*
     }
 }
 
-// one thread per output pixel of I [T][ny][nx] (grid g, n_z = 0): pixels with
-// n_x <= 0 are read from the half-plane `half` [T][v.ny][v.nx] computed on the
-// grid v, the others from their mirror -n
-__global__ void friedel_plane_kernel(const float* __restrict__ half, int64_t T, GridDesc v, GridDesc g,
-                                     float* __restrict__ I) {
-    const int64_t P = (int64_t)g.nx * g.ny;
+// one thread per output pixel of I [T][nz][ny][nx] (grid g): pixels whose
+// coordinate on the split axis is <= 0 are read from the half-grid `half`
+// [T][v.nz][v.ny][v.nx], the others from their mirror -n (the amplitude is
+// conjugated there)
+__global__ void friedel_kernel(const float* __restrict__ half, const float* __restrict__ half_amp, int64_t T,
+                               GridDesc v, GridDesc g, int axis, float* __restrict__ I, float* __restrict__ amp) {
+    const int64_t P = g.pixels();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= T * P) return;
     const int64_t t = i / P;
     const int64_t p = i - t * P;
-    const int iy = (int)(p / g.nx);
-    const int ix = (int)(p - (int64_t)iy * g.nx);
-    int x = g.nx0 + ix, y = g.ny0 + iy;
-    if (x > 0) {
-        x = -x;
-        y = -y;
+    const int64_t plane = (int64_t)g.nx * g.ny;
+    const int iz = (int)(p / plane);
+    const int64_t rem = p - (int64_t)iz * plane;
+    const int iy = (int)(rem / g.nx);
+    const int ix = (int)(rem - (int64_t)iy * g.nx);
+    int n[3] = {g.nx0 + ix, g.ny0 + iy, g.nz0 + iz};
+    const bool mirror = n[axis] > 0;
+    if (mirror) {
+        n[0] = -n[0];
+        n[1] = -n[1];
+        n[2] = -n[2];
     }
-    I[i] = half[(t * v.ny + (y - v.ny0)) * v.nx + (x - v.nx0)];
+    const int64_t o = ((t * v.nz + (n[2] - v.nz0)) * v.ny + (n[1] - v.ny0)) * v.nx + (n[0] - v.nx0);
+    I[i] = half[o];
+    if (amp) {
+        amp[2 * i] = half_amp[2 * o];
+        amp[2 * i + 1] = mirror ? -half_amp[2 * o + 1] : half_amp[2 * o + 1];
+    }
 }
 
 }  // namespace
 
-bool friedel_half_grid(const GridDesc& g, GridDesc& v) {
-    // a centred n_z = 0 plane [-nx/2, nx/2) x [-ny/2, ny/2) (even sizes) is
-    // covered by n_x in [-nx/2, 0] and n_y in [-ny/2, ny/2] with mirrors; the
-    // half is used where it needs fewer 128 x 128 tiles (a 192^2 plane: 2
-    // instead of 4)
-    if (g.nz != 1 || g.nz0 != 0 || (g.nx & 1) || (g.ny & 1) || g.nx0 != -g.nx / 2 || g.ny0 != -g.ny / 2) return false;
+int friedel_half_grid(const GridDesc& g, GridDesc& v) {
+    // For real form factors I(-n) = I(n): the pixels of g whose coordinate on
+    // the split axis (n_x for a plane at n_z = 0, n_z otherwise) is positive
+    // are read from their mirrors.  The half-grid v keeps the split axis from
+    // min(lo, 1 - hi) to 0 and widens the other two to the hull of their
+    // range and its mirror.  It is used where it needs fewer 128 x 128 tiles
+    // (planes of 192^2: 2 instead of 4; the volume n in [-40, 40]^3: 41
+    // instead of 81).
+    const int axis = (g.nz == 1 && g.nz0 == 0) ? 0 : 2;
+    int lo[3] = {g.nx0, g.ny0, g.nz0}, n[3] = {g.nx, g.ny, g.nz};
+    int vlo[3], vn[3];
+    for (int a = 0; a < 3; ++a) {
+        const int hi = lo[a] + n[a];  // exclusive
+        if (a == axis) {
+            if (hi <= 1) return -1;  // nothing positive to mirror
+            vlo[a] = std::min(lo[a], 1 - hi);
+            vn[a] = 1 - vlo[a];      // up to 0 inclusive
+        } else {
+            vlo[a] = std::min(lo[a], 1 - hi);
+            vn[a] = std::max(hi, 1 - lo[a]) - vlo[a];
+        }
+    }
     v = g;
-    v.nx = g.nx / 2 + 1;
-    v.ny = g.ny + 1;
-    auto tiles = [](const GridDesc& d) { return (int64_t)((d.nx + 127) / 128) * ((d.ny + 127) / 128); };
-    return tiles(v) < tiles(g);
+    v.nx0 = vlo[0];
+    v.nx = vn[0];
+    v.ny0 = vlo[1];
+    v.ny = vn[1];
+    v.nz0 = vlo[2];
+    v.nz = vn[2];
+    auto tiles = [](const GridDesc& d) { return (int64_t)d.nz * ((d.nx + 127) / 128) * ((d.ny + 127) / 128); };
+    return tiles(v) < tiles(g) ? axis : -1;
 }
 
-cudaError_t launch_friedel_plane(const float* half, int64_t T, const GridDesc& v, const GridDesc& g, float* I,
-                                 cudaStream_t st) {
+cudaError_t launch_friedel(const float* half, const float* half_amp, int64_t T, const GridDesc& v, const GridDesc& g,
+                           int axis, float* I, float* amp, cudaStream_t st) {
     const int64_t n = T * g.pixels();
     if (n == 0) return cudaSuccess;
     ++tl_kernel_launches;
-    friedel_plane_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(half, T, v, g, I);
+    friedel_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(half, half_amp, T, v, g, axis, I, amp);
     return cudaGetLastError();
 }
 

@@ -411,9 +411,14 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
     for (int i = 0; i < 9; ++i) hm.a[i] = hinv[i];
     const int64_t N = traj->n_atoms;
     const int64_t n_pad = round_up(N > 0 ? N : 1, 64);
+    // with device outputs the tensor path may contract a half grid and fill
+    // the rest by I(-q) = I(q) (real form factors), where that needs fewer tiles
+    GridDesc gh = g;
+    const int half_axis = (use_tc && out_dev && N > 0) ? friedel_half_grid(g, gh) : -1;
+    const GridDesc gc = half_axis >= 0 ? gh : g;  // the contraction's grid
     PhaseOpts popt;
     popt.ortho = is_ortho(hinv);
-    popt.need_z = !(g.nz == 1 && g.nz0 == 0);
+    popt.need_z = !(gc.nz == 1 && gc.nz0 == 0);
     popt.perm_mul = use_tc ? coprime_stride(n_pad / kPermRun) : 1;
 
     // frames per chunk: records and (for host positions) staged positions
@@ -466,7 +471,7 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
     const size_t o_rec = carve((size_t)fchunk * rec_per_frame);
     const size_t o_part = carve(use_tc ? tc_scratch_bytes(tc_pairs) : dplan.partial_bytes);
     auto split_of = [&](int64_t nf) {
-        return tc_split_plan(tc_units(tc_traj(nullptr, n_pad, nf, g, nullptr, nullptr)), tc_pairs,
+        return tc_split_plan(tc_units(tc_traj(nullptr, n_pad, nf, gc, nullptr, nullptr)), tc_pairs,
                              (int)(n_pad / tc_atom_multiple()), chunk_stages);
     };
     size_t split_bytes = 0;
@@ -478,6 +483,8 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
     const size_t o_f = carve(pos_host ? (size_t)N * sizeof(float) : 0);
     const size_t o_I = carve(out_dev ? 0 : (size_t)fchunk * P * sizeof(float));
     const size_t o_amp = carve(out_dev || !amp_out ? 0 : (size_t)fchunk * P * 2 * sizeof(float));
+    const size_t o_half = carve(half_axis >= 0 ? (size_t)fchunk * gh.pixels() * sizeof(float) : 0);
+    const size_t o_half_amp = carve(half_axis >= 0 && amp_out ? (size_t)fchunk * gh.pixels() * 2 * sizeof(float) : 0);
     s = ensure_ws(ctx, off + 256);
     if (s != XS_OK) return s;
     char* ws = static_cast<char*>(ctx->ws);
@@ -531,7 +538,9 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
             XS_CUDA(traced(ctx, "phase", st, [&] { return launch_phase(pos_c, f_dev, N, nf, n_pad, hm, popt, rec, ctx->d_err, st); }));
             if (pos_host) XS_CUDA(cudaEventRecord(ctx->ev_consumed[c & 1], st));
             if (use_tc) {
-                const TcTraj tr = tc_traj(rec, n_pad, nf, g, Ic, Ac);
+                float* Ih = half_axis >= 0 ? reinterpret_cast<float*>(ws + o_half) : Ic;
+                float* Ah = half_axis >= 0 ? (Ac ? reinterpret_cast<float*>(ws + o_half_amp) : nullptr) : Ac;
+                const TcTraj tr = tc_traj(rec, n_pad, nf, gc, Ih, Ah);
                 const TcSplit sp = split_of(nf);
                 XS_CUDA(traced(ctx, "tc", st, [&] {
                     return launch_tc_single(tr, tc_pairs, sp, chunk_stages, prec == XS_PREC_SPLIT_BF16,
@@ -540,6 +549,9 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
                 }));
                 XS_CUDA(traced(ctx, "split_finish", st,
                                [&] { return launch_tc_split_finish(tr, tc_pairs, sp, ws + o_split, st); }));
+                if (half_axis >= 0)
+                    XS_CUDA(traced(ctx, "friedel", st,
+                                   [&] { return launch_friedel(Ih, Ah, nf, gh, g, half_axis, Ic, Ac, st); }));
             } else {
                 DirectPlan pc = plan_direct(n_pad, nf, g, ctx->num_sms);
                 if (pc.partial_bytes > dplan.partial_bytes) return fail(XS_ERR_CUDA, "internal: partial plan grew");
@@ -1054,8 +1066,8 @@ xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qg
         double hinv[9];
         GridDesc g;
         size_t rec_off;
-        bool half = false;  // centred plane computed as a half-plane plus mirrors
-        GridDesc v;         // the half-plane's grid
+        int half_axis = -1;  // >= 0: computed on the half grid v, the rest by mirrors
+        GridDesc v;
         size_t half_off = 0;
     };
     std::vector<Job> jobs((size_t)n_traj);
@@ -1083,9 +1095,9 @@ xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qg
         j.g = to_desc(&grid[i]);
         if (j.T > 65535 * 8) return fail(XS_ERR_INVALID_ARG, "trajectory %d: too many frames", i);
         j.rec_off = carve((size_t)j.T * j.n_pad * sizeof(AtomRec));
-        if (j.N > 0 && j.T > 0 && friedel_half_grid(j.g, j.v)) {
-            j.half = true;
-            j.half_off = carve((size_t)j.T * j.v.pixels() * sizeof(float));
+        if (j.N > 0 && j.T > 0 && j.g.pixels() > 0) {
+            j.half_axis = friedel_half_grid(j.g, j.v);
+            if (j.half_axis >= 0) j.half_off = carve((size_t)j.T * j.v.pixels() * sizeof(float));
         }
     }
     const int cap = tc_pair_capacity(ctx->num_sms);
@@ -1105,7 +1117,7 @@ xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qg
             empty.push_back(i);
             continue;
         }
-        if (j.half)
+        if (j.half_axis >= 0)
             trs.push_back(tc_traj(reinterpret_cast<AtomRec*>(ws + j.rec_off), j.n_pad, j.T, j.v,
                                   reinterpret_cast<float*>(ws + j.half_off), nullptr));
         else
@@ -1145,7 +1157,8 @@ xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qg
             for (int k = 0; k < 9; ++k) hm.a[k] = j.hinv[k];
             PhaseOpts popt;
             popt.ortho = is_ortho(j.hinv);
-            popt.need_z = !(j.g.nz == 1 && j.g.nz0 == 0);
+            const GridDesc& gc = j.half_axis >= 0 ? j.v : j.g;
+            popt.need_z = !(gc.nz == 1 && gc.nz0 == 0);
             popt.perm_mul = coprime_stride(j.n_pad / kPermRun);
             cudaError_t err = launch_phase(t.pos, t.f, j.N, j.T, j.n_pad, hm, popt,
                                            reinterpret_cast<AtomRec*>(ws + j.rec_off), ctx->d_err, st);
@@ -1157,9 +1170,9 @@ xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qg
                                           reinterpret_cast<double*>(ws + o_scratch), ctx->d_err, ctx->timeout_ns, st);
         for (size_t e = 0; e < trs.size() && err == cudaSuccess; ++e) {
             const Job& j = jobs[(size_t)which[e]];
-            if (j.half)
-                err = launch_friedel_plane(reinterpret_cast<const float*>(ws + j.half_off), j.T, j.v, j.g,
-                                           I_out[which[e]], st);
+            if (j.half_axis >= 0)
+                err = launch_friedel(reinterpret_cast<const float*>(ws + j.half_off), nullptr, j.T, j.v, j.g,
+                                     j.half_axis, I_out[which[e]], nullptr, st);
         }
         return err;
     };

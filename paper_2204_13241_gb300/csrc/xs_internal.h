@@ -132,12 +132,14 @@ struct FftGrid {
 };
 cudaError_t launch_fft_frame(const float* pos, const float* f, int64_t n_atoms, const FftGrid& fg, double2* grid,
                              const GridDesc& g, const double2* d_G, float* I, float* amp, int* err, cudaStream_t st);
-// centred n_z = 0 planes computed as a half-plane plus mirrors (real form
-// factors: I(-q) = I(q)); true when v (the half) needs fewer tiles than g
-bool friedel_half_grid(const GridDesc& g, GridDesc& v);
-// I [T][g.ny][g.nx] from the half-plane [T][v.ny][v.nx]
-cudaError_t launch_friedel_plane(const float* half, int64_t T, const GridDesc& v, const GridDesc& g, float* I,
-                                 cudaStream_t st);
+// grids computed as a half plus mirrors (real form factors: I(-q) = I(q)):
+// returns the split axis (0: n_x for planes at n_z = 0, 2: n_z) and the half
+// grid v when v needs fewer 128 x 128 tiles than g, else -1
+int friedel_half_grid(const GridDesc& g, GridDesc& v);
+// I [T][g] (and amp, conjugated where mirrored; NULL to skip) from the half
+// [T][v]
+cudaError_t launch_friedel(const float* half, const float* half_amp, int64_t T, const GridDesc& v, const GridDesc& g,
+                           int axis, float* I, float* amp, cudaStream_t st);
 cudaError_t launch_points_gather(const float* tmp, const float* tmp_amp, const int64_t* d_src, const int64_t* d_stride,
                                  int64_t P, int64_t nf, float* I, float* amp, cudaStream_t st);
 cudaError_t launch_ff_table(const double* d_coef, int n_species, const GridDesc& g, const Mat3& hinv, double* table,

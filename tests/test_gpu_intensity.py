@@ -95,6 +95,41 @@ def test_triclinic_cell(xs, prec):
     assert err <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_symmetric_volume_from_half_and_mirrors(xs, prec):
+    # n in [-6, 6]^3 maps onto itself under n -> -n: the tensor path contracts
+    # the planes n_z <= 0 and reads the others from their mirrors, using
+    # S(-q) = conj S(q) for real form factors; the amplitude checks the
+    # conjugation
+    pos, f, box = _case(31, 900, 2, 19.0)
+    grid = wl.QGrid(-6, 13, -6, 13, -6, 13)
+    I, A = _run(xs, pos, f, box, grid, prec, amp=True)
+    ref = oracle.amplitude(pos, f, box, grid.miller())
+    assert amp_err(A, ref) <= TOL[prec]
+    e, e0 = e_I(I.reshape(2, -1), np.abs(ref) ** 2, grid.miller())
+    assert e <= TOL[prec] and e0 <= TOL[prec], (e, e0)
+
+
+@pytest.mark.parametrize("grid", [
+    wl.QGrid(-40, 81, -40, 81, -40, 81),   # the 81^3 grid of the paper's Table 1: 41 planes contracted
+    wl.centered_plane(192),                # two tiles instead of four
+])
+def test_half_grid_against_oracle(xs, grid):
+    rng = np.random.default_rng(33)
+    N, L = 4000, 59.19
+    pos = (rng.random((1, N, 3)) * L).astype(np.float32)
+    f = np.ones(N, np.float32)
+    box = np.eye(3) * L
+    I = _run(xs, pos, f, box, grid, "fp16").reshape(1, -1)
+    m = grid.miller()
+    pick = np.unique(np.concatenate([np.flatnonzero(np.all(m == 0, axis=1)),
+                                     np.flatnonzero((m[:, 0] == 1) | (m[:, 2] == 1))[:2000],
+                                     rng.choice(m.shape[0], 3000, replace=False)]))
+    ref = oracle.intensity(pos, f, box, m[pick])
+    e, e0 = e_I(I[:, pick], ref, m[pick])
+    assert e <= 1e-4 and e0 <= 1e-4, (e, e0)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
 def test_edge_cases_single_and_zero_atoms(xs, prec):
     grid = wl.QGrid(-8, 16, -8, 16, 0, 1)
