@@ -35,6 +35,9 @@ import numpy as np  # noqa: E402
 
 METRIC = "atom*pixel*frames/s"
 FALLBACK_PEAK = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0}
+# FP32 SIMT rate from the unit counts and the maximum SM clock (152 SMs x 128
+# FP32 lanes x 2 flops x 2.07 GHz); nominal, the measured peaks carry none
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # DRAM bytes (read + write) of one tc_kernel launch of the 1,000-frame
 # workload, from an ncu capture of that launch (dram__bytes_read.sum +
@@ -58,6 +61,7 @@ def _args():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-table1", action="store_true")
     ap.add_argument("--no-next", action="store_true", help="skip the ISF, Ewald-slice and species timings")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing on its own workload")
     return ap.parse_args()
 
 
@@ -407,20 +411,20 @@ def run_ours(args):
     # ---- the rows beyond the hot path, on the same crystal: per-species form
     # factors, the Ewald-sphere slice through the point path, and the
     # intermediate scattering function with its Siegert contrast
-    if not args.no_next and rank == 0:
-        def ms_per_call(fn, reps=3):
+    def ms_per_call(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
             fn()
-            torch.cuda.synchronize()
-            ctx.sync_status()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps):
-                fn()
-            e1.record(stream)
-            e1.synchronize()
-            ctx.sync_status()
-            return e0.elapsed_time(e1) / reps
+        e1.record(stream)
+        e1.synchronize()
+        ctx.sync_status()
+        return e0.elapsed_time(e1) / reps
 
+    if not args.no_next and rank == 0:
         nf = min(100, T)
         sub = pos_d[:nf].contiguous()
         t_plane = ms_per_call(lambda: xs.intensity(sub, f_d, box, grid, args.precision))
@@ -457,6 +461,35 @@ def run_ours(args):
                     "ms_per_call": t_isf, "frames": T, "n_tau": len(taus)},
             "contrast_from_isf": {"ms_per_call": t_cf, "delays": Kmax, "window_lengths": len(Ks)}}
         del sub, amp, Fh
+        torch.cuda.empty_cache()
+
+    # ---- the adjoint on its own workload: 100,000 atoms, a 256^2 plane, one
+    # frame, L = sum_q w_q (I - I_target)^2 with w_q = 1 / (1 + |q|^2)
+    if not args.no_adjoint and rank == 0:
+        traj3, target3, grid3 = wl.config3()
+        p3 = torch.from_numpy(traj3.pos[0]).cuda()
+        f3 = torch.from_numpy(traj3.f).cuda()
+        It = xs.intensity(torch.from_numpy(target3[0]).cuda(), f3, traj3.box, grid3, "fp32").reshape(-1)
+        q2 = ((2.0 * math.pi / traj3.L) ** 2) * (grid3.miller().astype(np.float64) ** 2).sum(axis=1)
+        w3 = torch.from_numpy((1.0 / (1.0 + q2)).astype(np.float32)).cuda()
+        I3, A3 = xs.intensity(p3, f3, traj3.box, grid3, "fp32", want_amp=True)
+        G3 = (2.0 * w3 * (I3.reshape(-1) - It)).contiguous()
+        A3 = A3.reshape(-1, 2).contiguous()
+        t_b = ms_per_call(lambda: xs.intensity_backward(p3, f3, traj3.box, grid3, A3, G3))
+        t_f32 = ms_per_call(lambda: xs.intensity(p3, f3, traj3.box, grid3, "fp32", want_amp=True))
+        t_f16 = ms_per_call(lambda: xs.intensity(p3, f3, traj3.box, grid3, args.precision, want_amp=True))
+        units3 = float(traj3.n_atoms) * grid3.n_pixels
+        fp32_peak = FP32_PEAK_TFLOPS
+        achieved3 = 16.0 * units3 / (t_b * 1e-3) / 1e12
+        line["adjoint"] = {
+            "workload": "100,000 atoms U[0,120)^3, 256^2 plane, one frame",
+            "backward_ms": t_b, "value": units3 / (t_b * 1e-3), "unit": "atom*pixel/s",
+            "forward_fp32_with_amp_ms": t_f32, f"forward_split_{args.precision}_with_amp_ms": t_f16,
+            "roofline": {"bound": "fp32", "achieved": achieved3, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved3 / fp32_peak,
+                         "note": "16 FP32 flops per atom*pixel (two complex multiply-adds); peak = 152 SMs x 128 "
+                                 "FP32 lanes x 2 flops x 2.07 GHz (nominal, not measured)"}}
+        del p3, f3, It, I3, A3, G3
         torch.cuda.empty_cache()
 
     # ---- the batched workload: 64 ideal-gas trajectories in one persistent launch

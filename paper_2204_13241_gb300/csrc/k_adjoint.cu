@@ -24,7 +24,7 @@ namespace {
 constexpr int kAdjAtoms = 64;
 constexpr int kAdjThreads = 256;
 constexpr int kAdjWarps = kAdjThreads / 32;
-constexpr int kAdjYChunk = 256;
+constexpr int kAdjYChunk = 128;  // n_y rows of E_y per shared-memory chunk (64 KB: three blocks per SM)
 
 __global__ void h_kernel(const float* __restrict__ amp, const float* __restrict__ G, int64_t P,
                          float2* __restrict__ H) {
