@@ -80,9 +80,12 @@ adjoint_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, GridDesc g, Mat
 #pragma unroll
                     for (int k = 0; k < 2; ++k) Z[r][k] = Zy[r][k] = make_float2(0.f, 0.f);
                 float fny = (float)(g.ny0 + cy0);
-                for (int iy = 0; iy < ncy; ++iy, fny += 1.0f) {
-                    const float2 hv0 = h0[(int64_t)iy * g.nx];
-                    const float2 hv1 = has1 ? h1[(int64_t)iy * g.nx] : make_float2(0.f, 0.f);
+                // h1 aliases h0 when the warp has no second row; its sums are
+                // then never used.  Pointer steps, no index products.
+#pragma unroll 2
+                for (int iy = 0; iy < ncy; ++iy, fny += 1.0f, h0 += g.nx, h1 += g.nx) {
+                    const float2 hv0 = *h0;
+                    const float2 hv1 = *h1;
                     const float2 hy0 = make_float2(fny * hv0.x, fny * hv0.y);
                     const float2 hy1 = make_float2(fny * hv1.x, fny * hv1.y);
 #pragma unroll

@@ -4,9 +4,9 @@
 // g2_kernel: one thread per pixel, group of up to kTauGroup delays and
 //   segment of frames (blockIdx.z).  The block walks its frames t in order;
 //   I[t][p] and I[t+tau][p] are coalesced across the pixels of a warp.
-//   Products are summed with compensated (Kahan) FP32 updates over blocks of
-//   64 frames and the block sums are added in FP64; the mean is summed in
-//   FP64 directly, by the blocks of the first delay group.  The kernel is
+//   Products and the mean (summed by the blocks of the first delay group)
+//   are summed with compensated (Kahan) FP32 updates over blocks of up to 256
+//   frames, and the block sums are added in FP64.  The kernel is
 //   bound by instruction issue: frames whose delays all stay inside the
 //   series run a loop with one pointer step per frame and a precomputed
 //   offset per delay, without bound checks.  Each segment writes FP64
@@ -40,6 +40,10 @@ namespace {
 constexpr int kTauGroup = 16;
 constexpr int kG2Threads = 128;
 constexpr int kFlush = 64;
+// frames per compensated FP32 block of g2_kernel before its FP64 totals: the
+// FP64 pipe is narrow on GB300, and a compensated sum of up to 256
+// non-negative terms stays within about 2 eps of the exact sum
+constexpr int kG2Flush = 256;
 
 __global__ void __launch_bounds__(kG2Threads)
 g2_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __restrict__ taus,
@@ -68,10 +72,11 @@ g2_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __re
         dacc[k] = 0.0;
     }
     double dmean = 0.0;
+    float macc = 0.0f, mcomp = 0.0f;
     const bool want_mean = blockIdx.y == 0;  // the first delay group sums the mean
     const int64_t seg0 = (int64_t)blockIdx.z * seg_len, seg1 = min(T, seg0 + seg_len);
-    for (int64_t t0 = seg0; t0 < seg1; t0 += kFlush) {
-        const int64_t t1 = min(seg1, t0 + kFlush);
+    for (int64_t t0 = seg0; t0 < seg1; t0 += kG2Flush) {
+        const int64_t t1 = min(seg1, t0 + kG2Flush);
         // frames t < T - tau_max have every delay inside the series: the loop
         // over them carries no bound checks and no index arithmetic but one
         // pointer step (the kernel is bound by instruction issue)
@@ -80,7 +85,12 @@ g2_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __re
         int64_t t = t0;
         for (; t < tf; ++t, row += P) {
             const float x = row[0];
-            if (want_mean) dmean += (double)x;
+            if (want_mean) {
+                const float ym = x - mcomp;
+                const float sm = macc + ym;
+                mcomp = (sm - macc) - ym;
+                macc = sm;
+            }
 #pragma unroll
             for (int k = 0; k < kTauGroup; ++k) {
                 const float y = fmaf(x, row[off[k]], -comp[k]);
@@ -91,7 +101,12 @@ g2_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __re
         }
         for (; t < t1; ++t, row += P) {
             const float x = row[0];
-            if (want_mean) dmean += (double)x;
+            if (want_mean) {
+                const float ym = x - mcomp;
+                const float sm = macc + ym;
+                mcomp = (sm - macc) - ym;
+                macc = sm;
+            }
 #pragma unroll
             for (int k = 0; k < kTauGroup; ++k) {
                 if (k < nt && t + s_tau[k] < T) {
@@ -107,6 +122,8 @@ g2_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __re
             dacc[k] += (double)acc[k] - (double)comp[k];
             acc[k] = comp[k] = 0.0f;
         }
+        dmean += (double)macc - (double)mcomp;
+        macc = mcomp = 0.0f;
     }
     const int64_t seg = blockIdx.z;
     if (want_mean) mpart[seg * P + p] = dmean;
