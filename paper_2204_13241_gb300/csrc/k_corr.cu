@@ -24,7 +24,7 @@
 // Intermediate scattering function on the amplitude series S[t][p] (Sec. 2.3,
 // Eqs. Fq_pq, norm_Fq) and the contrast it predicts (Eq. beta_alt_int):
 //   isf_kernel      like g2_kernel with complex products conj(S(t)) S(t+tau)
-//                   (compensated FP32 over 64-frame blocks, FP64 block sums),
+//                   (compensated FP32 over 256-frame blocks, FP64 block sums),
 //                   F = mean / sum f^2 and F_hat = F / F(q,0)
 //   isf_contrast_kernel per in-ring pixel, one pass over the delays d:
 //                   (1/K^2) [K + 2 (K sum_{d<K} |F_hat|^2 - sum_{d<K} d |F_hat|^2)]
@@ -40,9 +40,9 @@ namespace {
 constexpr int kTauGroup = 16;
 constexpr int kG2Threads = 128;
 constexpr int kFlush = 64;
-// frames per compensated FP32 block of g2_kernel before its FP64 totals: the
-// FP64 pipe is narrow on GB300, and a compensated sum of up to 256
-// non-negative terms stays within about 2 eps of the exact sum
+// frames per compensated FP32 block of g2_kernel and isf_kernel before their
+// FP64 totals: the FP64 pipe is narrow on GB300, and a compensated sum of up
+// to 256 terms stays within about 2 eps of the sum of their magnitudes
 constexpr int kG2Flush = 256;
 
 __global__ void __launch_bounds__(kG2Threads)
@@ -180,6 +180,13 @@ isf_kernel(const float2* __restrict__ S, int64_t T, int64_t P, const int32_t* __
         dre[k] = dim[k] = 0.0;
     }
     double dmean = 0.0;
+    float macc = 0.0f, mcomp = 0.0f;  // |S|^2, compensated like the products
+    auto add_mean = [&](float2 a) {
+        const float y = fmaf(a.x, a.x, fmaf(a.y, a.y, -mcomp));
+        const float s = macc + y;
+        mcomp = (s - macc) - y;
+        macc = s;
+    };
     // conj(a) b = (a.x b.x + a.y b.y) + i (a.x b.y - a.y b.x), compensated
     auto add = [&](int k, float2 a, float2 b) {
         const float yr = fmaf(a.x, b.x, fmaf(a.y, b.y, -cre[k]));
@@ -191,21 +198,21 @@ isf_kernel(const float2* __restrict__ S, int64_t T, int64_t P, const int32_t* __
         cim[k] = (si - aim[k]) - yi;
         aim[k] = si;
     };
-    for (int64_t t0 = 0; t0 < T; t0 += kFlush) {
-        const int64_t t1 = min(T, t0 + kFlush);
+    for (int64_t t0 = 0; t0 < T; t0 += kG2Flush) {
+        const int64_t t1 = min(T, t0 + kG2Flush);
         // frames whose delays all stay inside the series: no bound checks
         const int64_t tf = max(t0, min(t1, T - (int64_t)tau_max));
         const float2* row = S + t0 * P + p;
         int64_t t = t0;
         for (; t < tf; ++t, row += P) {
             const float2 a = row[0];
-            dmean = fma((double)a.x, (double)a.x, fma((double)a.y, (double)a.y, dmean));
+            add_mean(a);
 #pragma unroll
             for (int k = 0; k < kIsfGroup; ++k) add(k, a, row[off[k]]);
         }
         for (; t < t1; ++t, row += P) {
             const float2 a = row[0];
-            dmean = fma((double)a.x, (double)a.x, fma((double)a.y, (double)a.y, dmean));
+            add_mean(a);
 #pragma unroll
             for (int k = 0; k < kIsfGroup; ++k)
                 if (k < nt && t + s_tau[k] < T) add(k, a, row[off[k]]);
@@ -216,6 +223,8 @@ isf_kernel(const float2* __restrict__ S, int64_t T, int64_t P, const int32_t* __
             dim[k] += (double)aim[k] - (double)cim[k];
             are[k] = cre[k] = aim[k] = cim[k] = 0.0f;
         }
+        dmean += (double)macc - (double)mcomp;
+        macc = mcomp = 0.0f;
     }
     const double m = dmean / (double)T;  // F(q,0) sum f^2
 #pragma unroll
