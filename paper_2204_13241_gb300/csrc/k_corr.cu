@@ -40,6 +40,7 @@ namespace {
 constexpr int kTauGroup = 16;
 constexpr int kG2Threads = 128;
 constexpr int kFlush = 64;
+constexpr int64_t kPrefixSegs = 8;  // frame segments of the XSVS prefix sums
 // frames per compensated FP32 block of g2_kernel and isf_kernel before their
 // FP64 totals: the FP64 pipe is narrow on GB300, and a compensated sum of up
 // to 256 terms stays within about 2 eps of the sum of their magnitudes
@@ -285,32 +286,56 @@ __global__ void ring_mean_kernel(const double* __restrict__ b, int64_t n_in, con
     if (lane == 0) out[i] = acc / (double)(a1 - a0);
 }
 
-__global__ void prefix_kernel(const float* __restrict__ I, int64_t T, int64_t P,
-                              const int32_t* __restrict__ perm, int64_t n_in, double* __restrict__ C) {
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= n_in) return;
-    const int64_t p = perm[q];
-    double acc = 0.0;
-    C[q] = 0.0;
-    // eight frames' loads in flight per thread (the kernel has one thread per
-    // in-ring pixel, too few to hide load latency otherwise); the sums keep
-    // their sequential order
-    constexpr int kAhead = 8;
-    int64_t t = 0;
-    for (; t + kAhead <= T; t += kAhead) {
+// The prefix runs over frame segments in parallel (one thread per in-ring
+// pixel alone is too few to hide the load latency): segment_total_kernel sums
+// each (pixel, segment), then prefix_kernel starts every segment from the sum
+// of the totals before it.  The totals sit in kPrefixSegs rows after C's T+1.
+constexpr int kAhead = 8;  // frames' loads in flight per thread
+
+__device__ __forceinline__ double sum_frames(const float* __restrict__ I, int64_t P, int64_t p, int64_t t0,
+                                             int64_t t1, double acc, double* __restrict__ C, int64_t n_in,
+                                             int64_t q) {
+    int64_t t = t0;
+    for (; t + kAhead <= t1; t += kAhead) {
         float x[kAhead];
 #pragma unroll
         for (int k = 0; k < kAhead; ++k) x[k] = I[(t + k) * P + p];
 #pragma unroll
         for (int k = 0; k < kAhead; ++k) {
             acc += (double)x[k];
-            C[(t + k + 1) * n_in + q] = acc;
+            if (C) C[(t + k + 1) * n_in + q] = acc;
         }
     }
-    for (; t < T; ++t) {
+    for (; t < t1; ++t) {
         acc += (double)I[t * P + p];
-        C[(t + 1) * n_in + q] = acc;
+        if (C) C[(t + 1) * n_in + q] = acc;
     }
+    return acc;
+}
+
+// grid (pixel blocks, segments): tot[s][q] = sum of I over segment s
+__global__ void segment_total_kernel(const float* __restrict__ I, int64_t T, int64_t P,
+                                     const int32_t* __restrict__ perm, int64_t n_in, int64_t seg_len,
+                                     double* __restrict__ tot) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n_in) return;
+    const int64_t s = blockIdx.y;
+    const int64_t t0 = s * seg_len, t1 = min(T, t0 + seg_len);
+    tot[s * n_in + q] = sum_frames(I, P, perm[q], t0, t1, 0.0, nullptr, n_in, q);
+}
+
+// grid (pixel blocks, segments): C[t+1][q] for the frames t of segment s
+__global__ void prefix_kernel(const float* __restrict__ I, int64_t T, int64_t P,
+                              const int32_t* __restrict__ perm, int64_t n_in, int64_t seg_len,
+                              const double* __restrict__ tot, double* __restrict__ C) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n_in) return;
+    const int64_t s = blockIdx.y;
+    double acc = 0.0;
+    for (int64_t k = 0; k < s; ++k) acc += tot[k * n_in + q];
+    if (s == 0) C[q] = 0.0;
+    const int64_t t0 = s * seg_len, t1 = min(T, t0 + seg_len);
+    sum_frames(I, P, perm[q], t0, t1, acc, C, n_in, q);
 }
 
 // block = one chunk (ring, start, count) and a slice of `kw_slice` entries of
@@ -433,6 +458,27 @@ __global__ void finalize_kernel(const double2* __restrict__ partial, int n_chunk
 
 }  // namespace
 
+int64_t xsvs_prefix_rows(int64_t T) { return T + 1 + kPrefixSegs; }
+
+// C [T+1][n_in] prefix sums of the permuted pixels; the kPrefixSegs rows after
+// them hold the segment totals
+static cudaError_t launch_prefix(const float* I, int64_t T, int64_t P, const int32_t* d_perm, int64_t n_in,
+                                 double* C, cudaStream_t st) {
+    const int64_t segs = std::max<int64_t>(1, std::min<int64_t>(kPrefixSegs, T / 64));
+    const int64_t seg_len = T > 0 ? (T + segs - 1) / segs : 1;
+    double* tot = C + (T + 1) * n_in;
+    const dim3 grid((unsigned)((n_in + 127) / 128), (unsigned)segs);
+    if (segs > 1) {
+        ++tl_kernel_launches;
+        segment_total_kernel<<<grid, 128, 0, st>>>(I, T, P, d_perm, n_in, seg_len, tot);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    ++tl_kernel_launches;
+    prefix_kernel<<<grid, 128, 0, st>>>(I, T, P, d_perm, n_in, seg_len, tot, C);
+    return cudaGetLastError();
+}
+
 int g2_segments(int64_t T) {
     const int64_t blocks = (T + kFlush - 1) / kFlush;
     return (int)std::max<int64_t>(1, std::min<int64_t>(8, blocks));
@@ -468,9 +514,7 @@ cudaError_t launch_xsvs_partial(const float* I, int64_t T, int64_t P, const int3
                                int64_t n_kw, const int32_t* d_ring_first_chunk, int n_rings, double* prefix,
                                double2* partial, double* sums, cudaStream_t st) {
     if (n_in_rings > 0) {
-        ++tl_kernel_launches;
-        prefix_kernel<<<(unsigned)((n_in_rings + 127) / 128), 128, 0, st>>>(I, T, P, d_perm, n_in_rings, prefix);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_prefix(I, T, P, d_perm, n_in_rings, prefix, st);
         if (e != cudaSuccess) return e;
         int64_t slice = 64;
         if ((n_kw + slice - 1) / slice > 65535) slice = (n_kw + 65534) / 65535;
@@ -524,9 +568,7 @@ cudaError_t launch_xsvs(const float* I, int64_t T, int64_t P, const int32_t* d_p
                         int n_rings, double* prefix, double2* partial, double* beta,
                         cudaStream_t st) {
     if (n_in_rings > 0) {
-        ++tl_kernel_launches;
-        prefix_kernel<<<(unsigned)((n_in_rings + 127) / 128), 128, 0, st>>>(I, T, P, d_perm, n_in_rings, prefix);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_prefix(I, T, P, d_perm, n_in_rings, prefix, st);
         if (e != cudaSuccess) return e;
         // slices of the (K,w) list give enough blocks to keep the SMs busy
         int64_t slice = 64;

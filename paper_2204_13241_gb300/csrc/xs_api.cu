@@ -1432,7 +1432,7 @@ xs_status xs_xsvs_partial(xs_context* ctx, const float* I, int64_t T, int64_t P,
         off = o + bytes;
         return o;
     };
-    const size_t o_prefix = carve((size_t)(T + 1) * std::max<int64_t>(n_in, 1) * sizeof(double));
+    const size_t o_prefix = carve((size_t)xsvs_prefix_rows(T) * std::max<int64_t>(n_in, 1) * sizeof(double));
     const size_t o_partial = carve((size_t)n_kw * std::max(n_chunks, 1) * sizeof(double2));
     s = ensure_ws(ctx, off + 256);
     if (s != XS_OK) return s;
@@ -1535,7 +1535,7 @@ xs_status xs_xsvs_contrast(xs_context* ctx, const float* I, int64_t T, const xs_
         off = o + bytes;
         return o;
     };
-    const size_t o_prefix = carve((size_t)(T + 1) * n_in * sizeof(double));
+    const size_t o_prefix = carve((size_t)xsvs_prefix_rows(T) * n_in * sizeof(double));
     const size_t o_partial = carve((size_t)n_kw * n_chunks * sizeof(double2));
     s = ensure_ws(ctx, off + 256);
     if (s != XS_OK) return s;

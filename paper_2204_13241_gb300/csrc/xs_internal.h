@@ -122,6 +122,9 @@ struct XsvsLayout {
     int n_chunks;         // (ring, pixel range) chunks
     int64_t n_kw;         // sum over K of floor(T/K)
 };
+// rows of the XSVS prefix buffer (float64 [rows][pixels in rings]): T + 1
+// prefix rows and the frame-segment totals after them
+int64_t xsvs_prefix_rows(int64_t T);
 // Algorithm 2 grid: n^3 points of an orthorhombic cell, spacing h[a], k[a]
 // Gaussian weights per axis around each atom
 struct FftGrid {

@@ -54,6 +54,7 @@ def test_g2_rejects_bad_delay(xs):
     (23, 24, [1, 2, 3, 7, 23], 1.0),
     (100, 50, [1, 5, 10, 33, 100], 0.5),
     (10, 64, list(range(1, 11)), 1.0),
+    (700, 40, [1, 3, 7, 50, 700], 1.0),      # prefix sums over 8 frame segments
 ])
 def test_xsvs_stage_parity(xs, T, side, Ks, width):
     rng = np.random.default_rng(T * side)
