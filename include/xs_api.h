@@ -355,9 +355,14 @@ XS_API xs_status xs_set_wait_timeout_ns(xs_context* ctx, int64_t ns);
  * ("" = all), the summed device time in milliseconds and the number of
  * kernels since the last read, and forgets those records (others stay).  Launch groups: "phase"
  * (phase records, 1 kernel), "direct" (FP32 direct sum, 1-2), "tc"
- * (tensor-core contraction, 1), "g2" (1), "xsvs" (prefix, windows,
- * finalize: 1-3), "adjoint" (2).  xs_launch_count returns the number of kernels the
- * context has launched since it was created (tracing on or off). */
+ * (tensor-core contraction, 1), "split_finish" (pieces of the last wave, 1),
+ * "friedel" (fill of a half grid, 1), "g2" (2), "xsvs" (segment totals,
+ * prefix, windows, finalize: 1-4), "isf" (1), "isf_contrast" (2), "species"
+ * (form-factor table, per-species sum, finish: 1 each), "points" (gather,
+ * 1), "fft" (spread, three line passes, gather: 4-5), "batched"
+ * (graph replay: its kernels), "adjoint" (2).  xs_launch_count returns the
+ * number of kernels the context has launched since it was created (tracing
+ * on or off). */
 XS_API xs_status xs_profile_enable(xs_context* ctx, int32_t on);
 XS_API xs_status xs_profile_read(xs_context* ctx, const char* prefix, double* total_ms, int64_t* launches);
 XS_API xs_status xs_launch_count(xs_context* ctx, int64_t* count);
