@@ -6,18 +6,19 @@
 //   I[t][p] and I[t+tau][p] are coalesced across the pixels of a warp.
 //   Products and the mean (summed by the blocks of the first delay group)
 //   are summed with compensated (Kahan) FP32 updates over blocks of up to 256
-//   frames, and the block sums are added in FP64.  The kernel is
-//   bound by instruction issue: frames whose delays all stay inside the
-//   series run a loop with one pointer step per frame and a precomputed
-//   offset per delay, without bound checks.  Each segment writes FP64
+//   frames, and the block sums are added in FP64.  Frames whose delays all
+//   stay inside the series run a loop with one pointer step per frame and a
+//   precomputed offset per delay, without bound checks.  Each segment writes FP64
 //   partial sums; g2_finish_kernel adds the segments in order and divides.
 //   The segments (up to 8, each a whole number of 64-frame blocks) give the
 //   kernel more blocks.
 //
 // XSVS: pixels are first permuted ring by ring (host-built permutation), then
-//   prefix_kernel   C[t][p'] = sum_{t'<t} I[t'][perm[p']]       (FP64, [T+1][P'])
+//   segment_total_kernel, prefix_kernel
+//                   C[t][p'] = sum_{t'<t} I[t'][perm[p']]       (FP64, [T+1][P'])
+//                   over up to 8 frame segments in parallel
 //   window_kernel   per (ring chunk, (K,w)): sum_p x and sum_p x^2 with
-//                   x = C[(w+1)K][p'] - C[wK][p'] (one warp per (K,w))
+//                   x = C[(w+1)K][p'] - C[wK][p'] (one warp per 8 (K,w))
 //   finalize_kernel per (K, ring): ring sums over the ring's chunks in a fixed
 //                   order, beta per window, mean over windows.
 //
