@@ -329,11 +329,23 @@ def run_ours(args):
         g_h = torch.empty((len(taus), P), dtype=torch.float64).pin_memory()
         b_h = torch.empty((len(Ks), R), dtype=torch.float64).pin_memory()
 
+        side = torch.cuda.Stream()
+
         def e2e_step():
-            g, mean, beta = step(pos_h, f_h)
-            I_h.copy_(I, non_blocking=True)
+            xs.intensity(pos_h, f_h, box, grid, args.precision, out=I)
+            # the intensity goes back to the host on a side stream while g2
+            # and the contrast run; the next step waits for it before it
+            # writes I again
+            done = torch.cuda.Event()
+            done.record(stream)
+            side.wait_event(done)
+            with torch.cuda.stream(side):
+                I_h.copy_(I, non_blocking=True)
+            g, mean = xs.g2(I.view(T, -1), taus)
+            beta, counts = xs.xsvs_contrast(I, grid, box, Ks, R)
             g_h.copy_(g, non_blocking=True)
             b_h.copy_(beta, non_blocking=True)
+            stream.wait_stream(side)
 
         e2e_step()
         barrier()
