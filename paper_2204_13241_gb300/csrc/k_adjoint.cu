@@ -21,6 +21,7 @@ namespace xs {
 
 namespace {
 
+constexpr bool kAdjointOnTensorCores = true;  // false: the FP32 kernel below
 constexpr int kAdjAtoms = 64;
 constexpr int kAdjThreads = 256;
 constexpr int kAdjWarps = kAdjThreads / 32;
@@ -152,11 +153,13 @@ adjoint_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, GridDesc g, Mat
 
 }  // namespace
 
-size_t adjoint_workspace_bytes(const GridDesc& g) { return (size_t)g.pixels() * sizeof(float2); }
+static size_t h_bytes(const GridDesc& g) { return ((size_t)g.pixels() * sizeof(float2) + 1023) & ~(size_t)1023; }
+
+size_t adjoint_workspace_bytes(const GridDesc& g) { return h_bytes(g) + adjoint_tc_image_bytes(g); }
 
 cudaError_t launch_adjoint(const AtomRec* rec, int64_t n_atoms, int64_t n_pad, const GridDesc& g,
                            const Mat3& hinv, const float* amp, const float* dL_dI, void* workspace,
-                           float* grad, cudaStream_t st) {
+                           float* grad, int* err, int64_t timeout_ns, cudaStream_t st) {
     const int64_t P = g.pixels();
     float2* H = static_cast<float2*>(workspace);
     const int64_t hb = min((P + 255) / 256, (int64_t)4096);
@@ -164,6 +167,9 @@ cudaError_t launch_adjoint(const AtomRec* rec, int64_t n_atoms, int64_t n_pad, c
     h_kernel<<<(unsigned)hb, 256, 0, st>>>(amp, dL_dI, P, H);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (kAdjointOnTensorCores)
+        return launch_adjoint_tc(rec, n_atoms, n_pad, g, hinv, H, static_cast<char*>(workspace) + h_bytes(g), grad,
+                                 err, timeout_ns, st);
     const size_t smem = (size_t)kAdjYChunk * kAdjAtoms * sizeof(float2);
     e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

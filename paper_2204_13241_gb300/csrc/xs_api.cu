@@ -1665,7 +1665,8 @@ xs_status xs_intensity_backward(xs_context* ctx, const xs_traj* traj, const xs_q
     char* ws = static_cast<char*>(ctx->ws);
     AtomRec* rec = reinterpret_cast<AtomRec*>(ws + o_rec);
     XS_CUDA(traced(ctx, "phase", st, [&] { return launch_phase(traj->pos, traj->f, N, 1, n_pad, hm, popt, rec, ctx->d_err, st); }));
-    XS_CUDA(traced(ctx, "adjoint", st, [&] { return launch_adjoint(rec, N, n_pad, g, hm, amp, dL_dI, ws + o_h, dL_dr_out, st); }));
+    XS_CUDA(traced(ctx, "adjoint", st, [&] { return launch_adjoint(rec, N, n_pad, g, hm, amp, dL_dI, ws + o_h, dL_dr_out, ctx->d_err,
+                                                                           ctx->timeout_ns, st); }));
     return XS_OK;
 }
 
