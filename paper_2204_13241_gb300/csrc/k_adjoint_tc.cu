@@ -9,10 +9,12 @@
 //
 // The complex product is a real one with the real and imaginary parts folded
 // into K: k' = 2 y + p, and per complex row q four real rows
-//   r = 0: [Re H, -Im H] -> Re Z      r = 1: [Im H, Re H] -> Im Z
-//   r = 2: n_y [Re H, -Im H] -> Re Z_y  r = 3: n_y [Im H, Re H] -> Im Z_y
+//   [Re H, -Im H] -> Re Z      [Im H, Re H] -> Im Z
+//   n_y [Re H, -Im H] -> Re Z_y  n_y [Im H, Re H] -> Im Z_y
 // against B[j][2y + p] = (Re E_y, Im E_y), so every accumulator element is a
-// finished real or imaginary part.  adjoint_image_kernel writes A as split
+// finished real or imaginary part.  In a row tile, rows 2q' + p' (p' = 0, 1:
+// real, imaginary part) of the first 64 hold Z and those of the last 64 hold
+// Z_y, so each warp holds one kind.  adjoint_image_kernel writes A as split
 // BF16 (hi + lo; H exceeds the FP16 range) already in the shared-memory
 // layout the tensor core reads (MN-major, 128-byte swizzle), one 32 KB image
 // per (row tile of 32 q, stage of 32 n_y).
@@ -22,8 +24,9 @@
 // phases) and one thread issues 4 K-steps x 3 split passes of
 // tcgen05.mma.cta_group::1 (M = N = 128) into 128 TMEM columns; then each
 // thread owns one accumulator row: it forms E_xz times its part of Z or Z_y,
-// the row sums go over lanes by shuffles and over warps in a fixed order, and
-// each thread keeps the running Im T of its atom.  One 64 KB stage, so three
+// the row sums go over lanes by a transposed butterfly (lane l ends with
+// atom column l of 32) and over warps in a fixed order, and each thread keeps
+// the running Im T of its atom.  One 64 KB stage, so three
 // CTAs share an SM and overlap one another.  Every wait is bounded.
 #include <cuda_bf16.h>
 
@@ -178,16 +181,17 @@ __global__ void adjoint_image_kernel(const float2* __restrict__ H, GridDesc g, i
     const int64_t ts = i / ((int64_t)kAtK * kAtRows);  // mt * n_stages + s
     const int s = (int)(ts % n_stages);
     const int64_t mt = ts / n_stages;
-    const int64_t q = mt * kAtQ + (m >> 2);
-    const int r = m & 3;
+    const int64_t q = mt * kAtQ + ((m & 63) >> 1);
+    const bool im_row = (m & 1) != 0;
+    const bool zy_row = m >= 64;
     const int y = s * (kAtK / 2) + (kk >> 1);
     const int p = kk & 1;
     float v = 0.0f;
     if (q < (int64_t)g.nx * g.nz && y < g.ny) {
         const int64_t x = q % g.nx, z = q / g.nx;
         const float2 h = H[(z * g.ny + y) * g.nx + x];
-        v = p == 0 ? ((r & 1) ? h.y : h.x) : ((r & 1) ? h.x : -h.y);
-        if (r >= 2) v *= (float)(g.ny0 + y);
+        v = p == 0 ? (im_row ? h.y : h.x) : (im_row ? h.x : -h.y);
+        if (zy_row) v *= (float)(g.ny0 + y);
     }
     uint16_t hi, lo;
     at_split(v, hi, lo);
@@ -244,29 +248,45 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
     const uint32_t a_hi = stage, a_lo = stage + kAtHalf, b_hi = stage + 2 * kAtHalf, b_lo = stage + 3 * kAtHalf;
     const AtomRec me = ctl->rec[tid];
     const int64_t Q = (int64_t)g.nx * g.nz;
+    // this thread's B row (MN = tid): block, byte in the chunk, and the swizzled
+    // chunk of each of the 8 K rows of an atom
+    const uint32_t b_row = (uint32_t)(tid >> 6) * kAtBlock + (uint32_t)(tid & 7) * 2u;
+    uint32_t b_off[8];
+#pragma unroll
+    for (int kr = 0; kr < 8; ++kr) b_off[kr] = (uint32_t)kr * 128u + ((uint32_t)(((tid & 63) >> 3) ^ kr) << 4);
+    const float2 w_step = at_cis(me.uy, ctl->tab);
 
     float tx = 0.0f, ty = 0.0f, tz = 0.0f;  // Im T of this thread's atom
     uint32_t phase = 0;
     bool ok = true;
     for (int mt = 0; mt < n_mtiles && ok; ++mt) {
         for (int s = 0; s < n_stages && ok; ++s) {
-            // A: copy the image of (mt, s); B: E_y of this thread's atom
+            // A: copy the image of (mt, s); B: E_y of this thread's atom, from an
+            // exact seed per stage and the exact step exp(i 2 pi U_y) (32 FP32
+            // rotations stay far below the split format's resolution)
             const uint4* src = reinterpret_cast<const uint4*>(img + ((int64_t)mt * n_stages + s) * kAtImage);
             uint4* dst = reinterpret_cast<uint4*>(smem);
-            for (int i = tid; i < (int)(kAtImage / 16); i += kAtThreads) dst[i] = src[i];
+            uint4 tmp[kAtImage / 16 / kAtThreads];
+#pragma unroll
+            for (int i = 0; i < (int)(kAtImage / 16 / kAtThreads); ++i) tmp[i] = src[i * kAtThreads + tid];
+#pragma unroll
+            for (int i = 0; i < (int)(kAtImage / 16 / kAtThreads); ++i) dst[i * kAtThreads + tid] = tmp[i];
+            const int y0 = s * (kAtK / 2);
+            float2 e = at_cis((uint32_t)(g.ny0 + y0) * me.uy, ctl->tab);
+#pragma unroll
             for (int yy = 0; yy < kAtK / 2; ++yy) {
-                const int y = s * (kAtK / 2) + yy;
-                float2 e = make_float2(0.0f, 0.0f);
-                if (y < g.ny) e = at_cis((uint32_t)(g.ny0 + y) * me.uy, ctl->tab);
+                const float2 ev = (y0 + yy < g.ny) ? e : make_float2(0.0f, 0.0f);
                 uint16_t h0, l0, h1, l1;
-                at_split(e.x, h0, l0);
-                at_split(e.y, h1, l1);
-                const uint32_t o0 = at_chunk(tid, 2 * yy) + (uint32_t)(tid & 7) * 2u;
-                const uint32_t o1 = at_chunk(tid, 2 * yy + 1) + (uint32_t)(tid & 7) * 2u;
-                *reinterpret_cast<uint16_t*>(smem + 2 * kAtHalf + o0) = h0;
-                *reinterpret_cast<uint16_t*>(smem + 3 * kAtHalf + o0) = l0;
-                *reinterpret_cast<uint16_t*>(smem + 2 * kAtHalf + o1) = h1;
-                *reinterpret_cast<uint16_t*>(smem + 3 * kAtHalf + o1) = l1;
+                at_split(ev.x, h0, l0);
+                at_split(ev.y, h1, l1);
+                // k' = 2 yy and 2 yy + 1: K atom yy / 4, rows (2 yy) & 7 and (2 yy + 1) & 7
+                uint8_t* r0 = smem + b_row + (uint32_t)(yy >> 2) * 1024u + b_off[(2 * yy) & 7];
+                uint8_t* r1 = smem + b_row + (uint32_t)(yy >> 2) * 1024u + b_off[(2 * yy + 1) & 7];
+                *reinterpret_cast<uint16_t*>(r0 + 2 * kAtHalf) = h0;
+                *reinterpret_cast<uint16_t*>(r0 + 3 * kAtHalf) = l0;
+                *reinterpret_cast<uint16_t*>(r1 + 2 * kAtHalf) = h1;
+                *reinterpret_cast<uint16_t*>(r1 + 3 * kAtHalf) = l1;
+                e = make_float2(fmaf(e.x, w_step.x, -e.y * w_step.y), fmaf(e.x, w_step.y, e.y * w_step.x));
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
@@ -288,53 +308,59 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
             at_fence_after();
         }
         if (!ok) break;
-        // epilogue: this thread's accumulator row m = tid
-        const int64_t q = (int64_t)mt * kAtQ + (tid >> 2);
-        const int r = tid & 3;
-        const bool xrow = r < 2;
+        // epilogue: this thread's accumulator row m = tid; warps 0-1 hold Z,
+        // warps 2-3 hold Z_y; even rows real parts, odd rows imaginary parts
+        const int64_t q = (int64_t)mt * kAtQ + ((tid & 63) >> 1);
+        const bool im_row = (tid & 1) != 0;
+        const bool z_warp = warp < 2;
         int nxv = 0, nzv = 0;
         if (q < Q) {
             nxv = g.nx0 + (int)(q % g.nx);
             nzv = g.nz0 + (int)(q / g.nx);
         }
-        for (int c16 = 0; c16 < kAtAtoms / 16; ++c16) {
-            uint32_t v[16];
-            at_ld16(lane_base + (uint32_t)(c16 * 16), v);
+        const float wa = (q < Q) ? (z_warp ? (float)nxv : 1.0f) : 0.0f;
+        const float wb = (q < Q) ? (float)nzv : 0.0f;
+        for (int c32 = 0; c32 < kAtAtoms / 32; ++c32) {
+            uint32_t v[32];
+            at_ld16(lane_base + (uint32_t)(c32 * 32), v);
+            at_ld16(lane_base + (uint32_t)(c32 * 32 + 16), v + 16);
             at_wait_ld(v);
+            at_wait_ld(v + 16);
+            // Im[E X] = Re E Im X + Im E Re X, weighted by n_x (or 1) and n_z
+            float a[32], b[32];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int j = c16 * 16 + i;
-                const AtomRec& aj = ctl->rec[j];
+            for (int k = 0; k < 32; ++k) {
+                const AtomRec& aj = ctl->rec[c32 * 32 + k];
                 const float2 e = at_cis((uint32_t)nxv * aj.ux + (uint32_t)nzv * aj.uz, ctl->tab);
-                // Im[E Z] = Re E Im Z + Im E Re Z: rows r = 0, 2 hold real parts
-                const float c = (q < Q) ? ((r & 1) ? e.x : e.y) * __uint_as_float(v[i]) : 0.0f;
-                float a = xrow ? (float)nxv * c : c;
-                float b = xrow ? (float)nzv * c : 0.0f;
-                a += __shfl_xor_sync(0xffffffffu, a, 1);
-                a += __shfl_xor_sync(0xffffffffu, a, 4);
-                a += __shfl_xor_sync(0xffffffffu, a, 8);
-                a += __shfl_xor_sync(0xffffffffu, a, 16);
-                b += __shfl_xor_sync(0xffffffffu, b, 1);
-                b += __shfl_xor_sync(0xffffffffu, b, 2);
-                b += __shfl_xor_sync(0xffffffffu, b, 4);
-                b += __shfl_xor_sync(0xffffffffu, b, 8);
-                b += __shfl_xor_sync(0xffffffffu, b, 16);
-                // lanes with bit 1 clear summed the x rows, lane 2 the y rows
-                if (lane == 0) {
-                    red[(warp * kAtAtoms + j) * 3 + 0] = a;
-                    red[(warp * kAtAtoms + j) * 3 + 2] = b;
-                } else if (lane == 2) {
-                    red[(warp * kAtAtoms + j) * 3 + 1] = a;
+                const float c = (im_row ? e.x : e.y) * __uint_as_float(v[k]);
+                a[k] = wa * c;
+                b[k] = wb * c;
+            }
+            // transposed butterfly: at offset o the lanes with bit o keep the
+            // upper half of their values; lane l ends with the sum of column l
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                const bool up = (lane & o) != 0;
+#pragma unroll
+                for (int k = 0; k < o; ++k) {
+                    const float sa = up ? a[k] : a[k + o];
+                    a[k] = (up ? a[k + o] : a[k]) + __shfl_xor_sync(0xffffffffu, sa, o);
+                    if (z_warp) {
+                        const float sb = up ? b[k] : b[k + o];
+                        b[k] = (up ? b[k + o] : b[k]) + __shfl_xor_sync(0xffffffffu, sb, o);
+                    }
                 }
             }
+            float* rw = red + (warp * kAtAtoms + c32 * 32 + lane) * 3;
+            rw[0] = a[0];
+            rw[1] = b[0];
         }
         at_fence_before();
         __syncthreads();
-        for (int w = 0; w < 4; ++w) {
-            tx += red[(w * kAtAtoms + tid) * 3 + 0];
-            ty += red[(w * kAtAtoms + tid) * 3 + 1];
-            tz += red[(w * kAtAtoms + tid) * 3 + 2];
-        }
+        // warps 0-1: (n_x-weighted, n_z-weighted) sums of Im[E Z]; warps 2-3: Im[E Z_y]
+        tx += red[(0 * kAtAtoms + tid) * 3 + 0] + red[(1 * kAtAtoms + tid) * 3 + 0];
+        tz += red[(0 * kAtAtoms + tid) * 3 + 1] + red[(1 * kAtAtoms + tid) * 3 + 1];
+        ty += red[(2 * kAtAtoms + tid) * 3 + 0] + red[(3 * kAtAtoms + tid) * 3 + 0];
         __syncthreads();
         at_fence_after();
     }
