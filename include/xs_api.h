@@ -325,7 +325,11 @@ XS_API xs_status xs_ring_index(const xs_qgrid* grid, const xs_box* box, double r
  *   amp        device float32 [P][2], the S of this frame (xs_intensity amp_out)
  *   dL_dI      device float32 [P]
  *   dL_dr_out  device float32 [n_atoms][3]
- * FP32 arithmetic; every grid shape is accepted.
+ * The contraction over n_y runs on tensor cores in split BF16 (FP32
+ * accumulation; relative error near 1e-5), the rest in FP32; every grid shape
+ * is accepted.  Uses context workspace for H = dL/dI conj(S) and its
+ * tensor-core images (8 B per pixel plus 32 KB per 32 (n_x, n_z) rows and 32
+ * n_y).
  */
 XS_API xs_status xs_intensity_backward(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid,
                                 const float* amp, const float* dL_dI, float* dL_dr_out,
@@ -360,7 +364,7 @@ XS_API xs_status xs_set_wait_timeout_ns(xs_context* ctx, int64_t ns);
  * prefix, windows, finalize: 1-4), "isf" (1), "isf_contrast" (2), "species"
  * (form-factor table, per-species sum, finish: 1 each), "points" (gather,
  * 1), "fft" (spread, three line passes, gather: 4-5), "batched"
- * (graph replay: its kernels), "adjoint" (2).  xs_launch_count returns the
+ * (graph replay: its kernels), "adjoint" (3).  xs_launch_count returns the
  * number of kernels the context has launched since it was created (tracing
  * on or off). */
 XS_API xs_status xs_profile_enable(xs_context* ctx, int32_t on);
