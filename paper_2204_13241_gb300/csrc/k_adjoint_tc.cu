@@ -16,18 +16,18 @@
 // real, imaginary part) of the first 64 hold Z and those of the last 64 hold
 // Z_y, so each warp holds one kind.  adjoint_image_kernel writes A as split
 // BF16 (hi + lo; H exceeds the FP16 range) already in the shared-memory
-// layout the tensor core reads (MN-major, 128-byte swizzle), one 32 KB image
-// per (row tile of 32 q, stage of 32 n_y).
+// layout the tensor core reads (MN-major, 128-byte swizzle), one 16 KB image
+// per (row tile of 32 q, stage of 16 n_y).
 //
 // adjoint_tc_kernel: one CTA of 128 threads owns 128 atoms.  Per row tile and
 // stage it copies the A image, builds B (one thread per atom, exact integer
-// phases) and one thread issues 4 K-steps x 3 split passes of
+// phases) and one thread issues 2 K-steps x 3 split passes of
 // tcgen05.mma.cta_group::1 (M = N = 128) into 128 TMEM columns; then each
 // thread owns one accumulator row: it forms E_xz times its part of Z or Z_y,
 // the row sums go over lanes by a transposed butterfly (lane l ends with
 // atom column l of 32) and over warps in a fixed order, and each thread keeps
-// the running Im T of its atom.  One 64 KB stage, so three
-// CTAs share an SM and overlap one another.  Every wait is bounded.
+// the running Im T of its atom.  Two 32 KB stage buffers: one is filled while
+// the other is multiplied; three CTAs share an SM.  Every wait is bounded.
 #include <cuda_bf16.h>
 
 #include "xs_internal.h"
@@ -39,16 +39,17 @@ namespace {
 constexpr int kAtAtoms = 128;                       // MMA N: atoms per CTA
 constexpr int kAtRows = 128;                        // MMA M: 32 complex rows x 4
 constexpr int kAtQ = kAtRows / 4;                   // complex rows per row tile
-constexpr int kAtK = 64;                            // k' per stage (32 n_y)
+constexpr int kAtK = 32;                            // k' per stage (16 n_y)
 constexpr int kAtThreads = 128;
-constexpr uint32_t kAtBlock = (kAtK / 8) * 1024;    // 64-row MN block: 8 KB
+constexpr uint32_t kAtBlock = (kAtK / 8) * 1024;    // 64-row MN block: 4 KB
 constexpr uint32_t kAtHalf = 2 * kAtBlock;          // 128 rows of one operand half
 constexpr uint32_t kAtImage = 2 * kAtHalf;          // A hi + lo of one (row tile, stage)
-constexpr uint32_t kAtStage = 4 * kAtHalf;          // A hi, A lo, B hi, B lo: 64 KB
+constexpr uint32_t kAtStage = 4 * kAtHalf;          // A hi, A lo, B hi, B lo: 32 KB
+constexpr int kAtBufs = 2;                          // stage buffers: fill one while the other multiplies
 constexpr int kAtTab = 256;
 
 struct AtCtl {
-    uint64_t done;
+    uint64_t done[kAtBufs];
     uint64_t drain;
     uint32_t tmem;
     int abort;
@@ -56,9 +57,9 @@ struct AtCtl {
     AtomRec rec[kAtAtoms];
 };
 // the warps' row sums [warp][atom][Im T_x, Im T_y, Im T_z] reuse the stage
-static_assert(4 * kAtAtoms * 3 * sizeof(float) <= kAtStage, "row sums fit in the stage");
+static_assert(4 * kAtAtoms * 3 * sizeof(float) <= kAtBufs * kAtStage, "row sums fit in the stage buffers");
 
-constexpr size_t kAtSmemBytes = 1024 + kAtStage + sizeof(AtCtl);
+constexpr size_t kAtSmemBytes = 1024 + kAtBufs * kAtStage + sizeof(AtCtl);
 
 // byte offset of the 16-byte chunk holding MN rows [mn, mn+8) of K row k
 __host__ __device__ __forceinline__ uint32_t at_chunk(int mn, int k) {
@@ -208,7 +209,7 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
     const uint32_t raw = at_smem_u32(at_raw);
     uint8_t* smem = at_raw + (((raw + 1023u) & ~1023u) - raw);
     const uint32_t stage = at_smem_u32(smem);
-    AtCtl* ctl = reinterpret_cast<AtCtl*>(smem + kAtStage);
+    AtCtl* ctl = reinterpret_cast<AtCtl*>(smem + kAtBufs * kAtStage);
     float* red = reinterpret_cast<float*>(smem);  // [warp][atom][3], between stages
     volatile int* abort_flag = &ctl->abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -227,7 +228,7 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
         ctl->rec[tid] = a;
     }
     if (tid == 0) {
-        at_mbar_init(&ctl->done, 1);
+        for (int b = 0; b < kAtBufs; ++b) at_mbar_init(&ctl->done[b], 1);
         at_mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -245,7 +246,6 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
     const uint32_t tmem = ctl->tmem;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     constexpr uint32_t idesc = at_idesc(kAtRows, kAtAtoms);
-    const uint32_t a_hi = stage, a_lo = stage + kAtHalf, b_hi = stage + 2 * kAtHalf, b_lo = stage + 3 * kAtHalf;
     const AtomRec me = ctl->rec[tid];
     const int64_t Q = (int64_t)g.nx * g.nz;
     // this thread's B row (MN = tid): block, byte in the chunk, and the swizzled
@@ -257,15 +257,29 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
     const float2 w_step = at_cis(me.uy, ctl->tab);
 
     float tx = 0.0f, ty = 0.0f, tz = 0.0f;  // Im T of this thread's atom
-    uint32_t phase = 0;
+    // each commit completes one phase of its buffer's barrier; every phase is
+    // waited for exactly once: before the buffer is filled again, or at the end
+    // of a row tile (older buffer first)
+    uint32_t phases = 0u, pend = 0u;  // bit b: buffer b's barrier parity, commit not yet waited for
+    int64_t issued = 0;
     bool ok = true;
     for (int mt = 0; mt < n_mtiles && ok; ++mt) {
         for (int s = 0; s < n_stages && ok; ++s) {
+            const int bs = (int)(issued & 1);
+            if ((pend >> bs) & 1u) {
+                ok = at_wait(&ctl->done[bs], (phases >> bs) & 1u, abort_flag, err, timeout_ns);
+                phases ^= 1u << bs;
+                pend &= ~(1u << bs);
+                if (!ok) break;
+                at_fence_after();
+            }
+            uint8_t* buf = smem + (uint32_t)bs * kAtStage;
+            const uint32_t bufa = stage + (uint32_t)bs * kAtStage;
             // A: copy the image of (mt, s); B: E_y of this thread's atom, from an
-            // exact seed per stage and the exact step exp(i 2 pi U_y) (32 FP32
+            // exact seed per stage and the exact step exp(i 2 pi U_y) (16 FP32
             // rotations stay far below the split format's resolution)
             const uint4* src = reinterpret_cast<const uint4*>(img + ((int64_t)mt * n_stages + s) * kAtImage);
-            uint4* dst = reinterpret_cast<uint4*>(smem);
+            uint4* dst = reinterpret_cast<uint4*>(buf);
             uint4 tmp[kAtImage / 16 / kAtThreads];
 #pragma unroll
             for (int i = 0; i < (int)(kAtImage / 16 / kAtThreads); ++i) tmp[i] = src[i * kAtThreads + tid];
@@ -280,8 +294,8 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
                 at_split(ev.x, h0, l0);
                 at_split(ev.y, h1, l1);
                 // k' = 2 yy and 2 yy + 1: K atom yy / 4, rows (2 yy) & 7 and (2 yy + 1) & 7
-                uint8_t* r0 = smem + b_row + (uint32_t)(yy >> 2) * 1024u + b_off[(2 * yy) & 7];
-                uint8_t* r1 = smem + b_row + (uint32_t)(yy >> 2) * 1024u + b_off[(2 * yy + 1) & 7];
+                uint8_t* r0 = buf + b_row + (uint32_t)(yy >> 2) * 1024u + b_off[(2 * yy) & 7];
+                uint8_t* r1 = buf + b_row + (uint32_t)(yy >> 2) * 1024u + b_off[(2 * yy + 1) & 7];
                 *reinterpret_cast<uint16_t*>(r0 + 2 * kAtHalf) = h0;
                 *reinterpret_cast<uint16_t*>(r0 + 3 * kAtHalf) = l0;
                 *reinterpret_cast<uint16_t*>(r1 + 2 * kAtHalf) = h1;
@@ -292,6 +306,7 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
             __syncthreads();
             if (tid == 0) {
                 at_fence_after();
+                const uint32_t a_hi = bufa, a_lo = bufa + kAtHalf, b_hi = bufa + 2 * kAtHalf, b_lo = bufa + 3 * kAtHalf;
 #pragma unroll
                 for (int kk = 0; kk < kAtK / 16; ++kk) {
                     const uint32_t ko = (uint32_t)kk * 2048u;  // two 8-row K atoms per K = 16
@@ -299,15 +314,24 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
                     at_mma(tmem, at_desc(a_hi + ko), at_desc(b_lo + ko), idesc, 1u);
                     at_mma(tmem, at_desc(a_lo + ko), at_desc(b_hi + ko), idesc, 1u);
                 }
-                at_commit(&ctl->done);
+                at_commit(&ctl->done[bs]);
             }
-            // the stage is free (and, after the last one, the accumulator final)
-            // once the MMAs complete
-            ok = at_wait(&ctl->done, phase, abort_flag, err, timeout_ns);
-            phase ^= 1u;
-            at_fence_after();
+            pend |= 1u << bs;
+            ++issued;
         }
         if (!ok) break;
+        // the row tile's last MMAs: then both buffers are free and the
+        // accumulator final
+        for (int k = 0; k < kAtBufs && ok; ++k) {
+            const int bb = (int)((issued + k) & 1);
+            if ((pend >> bb) & 1u) {
+                ok = at_wait(&ctl->done[bb], (phases >> bb) & 1u, abort_flag, err, timeout_ns);
+                phases ^= 1u << bb;
+                pend &= ~(1u << bb);
+            }
+        }
+        if (!ok) break;
+        at_fence_after();
         // epilogue: this thread's accumulator row m = tid; warps 0-1 hold Z,
         // warps 2-3 hold Z_y; even rows real parts, odd rows imaginary parts
         const int64_t q = (int64_t)mt * kAtQ + ((tid & 63) >> 1);
