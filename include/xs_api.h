@@ -328,7 +328,7 @@ XS_API xs_status xs_ring_index(const xs_qgrid* grid, const xs_box* box, double r
  * The contraction over n_y runs on tensor cores in split BF16 (FP32
  * accumulation; relative error near 1e-5), the rest in FP32; every grid shape
  * is accepted.  Uses context workspace for H = dL/dI conj(S) and its
- * tensor-core images (8 B per pixel plus 32 KB per 32 (n_x, n_z) rows and 32
+ * tensor-core images (8 B per pixel plus 16 KB per 32 (n_x, n_z) rows and 16
  * n_y).
  */
 XS_API xs_status xs_intensity_backward(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid,
