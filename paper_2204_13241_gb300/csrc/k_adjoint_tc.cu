@@ -1,4 +1,4 @@
-// Tensor-core form of the adjoint (the heavy contraction of k_adjoint.cu).
+// Tensor-core kernels of the adjoint (k_adjoint.cu forms H and launches them).
 //
 // With H_q = G_q conj(S_q) and rows q = (n_x, n_z) of the grid,
 //   Z(q, j)   = sum_y H(q, y) E_y(y, j),    Z_y(q, j) = sum_y n_y H(q, y) E_y(y, j),
@@ -56,7 +56,8 @@ struct AtCtl {
     float2 tab[kAtTab];      // exp(i 2 pi k / 256)
     AtomRec rec[kAtAtoms];
 };
-// the warps' row sums [warp][atom][Im T_x, Im T_y, Im T_z] reuse the stage
+// the warps' row sums [warp][atom][2 of 3] reuse the stage buffers: warps 0-1
+// the n_x- and n_z-weighted sums of Im[E Z], warps 2-3 the sum of Im[E Z_y]
 static_assert(4 * kAtAtoms * 3 * sizeof(float) <= kAtBufs * kAtStage, "row sums fit in the stage buffers");
 
 constexpr size_t kAtSmemBytes = 1024 + kAtBufs * kAtStage + sizeof(AtCtl);
