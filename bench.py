@@ -271,11 +271,12 @@ def run_ours(args):
     time.sleep(0.3)
     ev0.record(stream)
     for _ in range(args.steps):
-        step(pos_d, f_d)
+        res = step(pos_d, f_d)
     ev1.record(stream)
     ev1.synchronize()
     clocks = sampler.stop()
     barrier()
+    I_step = I.clone()  # the timed step's intensity, for the accuracy check
     launches = ctx.launch_count() - launches0
     tc_ms, tc_n = ctx.profile_read("tc")
     # per-stage device time per step (library events around each stage's launches)
@@ -545,14 +546,41 @@ def run_ours(args):
         t0 = time.perf_counter()
         ref = oracle.intensity(traj.pos[:1], traj.f, traj.box, m[sel])
         dt = time.perf_counter() - t0
-        got = I.view(T, -1)[0].cpu().numpy().astype(np.float64)[sel]
+        got = I_step.view(T, -1)[0].cpu().numpy().astype(np.float64)[sel]
         nz = np.any(m[sel] != 0, axis=1)
         e_I = float(np.linalg.norm(got[nz] - ref[0, nz]) / np.linalg.norm(ref[0, nz]))
+        d_I = np.abs(got[nz] - ref[0, nz])
+        mean_ref = float(ref[0, nz].mean())
+        e_pix = float(np.max(d_I / np.maximum(ref[0, nz], mean_ref)))
+        mean_dev = float(d_I.max() / mean_ref)
         line["cpu_baseline"] = {"value": traj.n_atoms * sel.size / dt, "unit": METRIC,
                                 "cores": oracle.max_threads(), "kind": "oracle",
                                 "sample": f"frame 0, {sel.size} of {m.shape[0]} pixels (every 2nd), "
                                           f"{traj.n_atoms} atoms, {dt:.1f} s"}
-        line["accuracy"] = {"e_I_frame0": e_I, "against": "oracle on the cpu_baseline sample"}
+        # g2 and the XSVS contrast of the last timed step against the oracle's
+        # g2 and contrast of the kernel's own intensity (stage parity)
+        g_k, _, beta_k = res
+        pix_g = np.arange(0, m.shape[0], 8)
+        Ih = I_step.view(T, -1)[:, torch.from_numpy(pix_g).cuda()].cpu().numpy()
+        gref, mref = oracle.g2(Ih, taus)
+        gk = g_k.cpu().numpy()[:, pix_g]
+        nzg = np.any(m[pix_g] != 0, axis=1)
+        e_g2 = float(np.linalg.norm(gk[:, nzg] - gref[:, nzg]) / np.linalg.norm(gref[:, nzg]))
+        bright = nzg & (mref >= 1e-2 * mref[nzg].mean())
+        e_g2_pix = float(np.max(np.abs(gk[:, bright] - gref[:, bright]) / np.abs(gref[:, bright])))
+        rings = oracle.ring_index(box, m, 1.0, R)
+        bref, cref = oracle.xsvs_contrast(I_step.view(T, -1).cpu().numpy(), Ks, rings, R)
+        okr = cref >= 8
+        bk = beta_k.cpu().numpy()
+        e_beta = float(np.max(np.abs(bk[:, okr] - bref[:, okr]) / np.abs(bref[:, okr])))
+        line["accuracy"] = {
+            "e_I_frame0": e_I, "e_pix_frame0": e_pix, "max_abs_dI_over_mean_frame0": mean_dev,
+            "e_g2": e_g2, "e_g2_max_rel_bright": e_g2_pix, "g2_pixels": int(nzg.sum()),
+            "g2_bright_pixels": int(bright.sum()), "e_beta": e_beta, "beta_entries": int(okr.sum() * len(Ks)),
+            "against": "FP64 oracle: intensity on the cpu_baseline sample (frame 0); g2 on every 8th pixel and "
+                       "beta on every (K, ring) with >= 8 pixels, from the kernel's own intensity",
+            "definitions": "e_I = ||dI||_2/||I_ref||_2 over q != 0; e_pix = max |dI| / max(I_ref, mean I_ref); "
+                           "e_g2 = ||dg2||_2/||g2_ref||_2; e_beta = max relative error"}
         # one host core on a smaller sample, and the 4,000-atom workload in full
         sel1 = np.arange(0, m.shape[0], 32)
         t0 = time.perf_counter()

@@ -374,9 +374,9 @@ XS_API xs_status xs_launch_count(xs_context* ctx, int64_t* count);
 /*
  * The FP32 direct-sum intensity of xs_intensity(..., XS_PREC_FP32_DIRECT, ...)
  * (the same kernels and the same result) for callers that cannot allocate
- * device memory when they need it: code that runs while a CUDA stream is being
- * captured into a graph (cudaMalloc is not allowed there), hosts that fix their
- * device memory budget at start-up, and processes whose framework allocator
+ * device memory when they need it: real-time or embedded hosts that fix their
+ * device memory budget at start-up, plug-ins running inside an application
+ * that owns the device memory, and processes whose framework allocator
  * already holds the whole device.  The paper has no counterpart: this is a
  * service of the library, not a step of the method.
  *   - No context and no allocation: the scratch (phase records, T * ceil64(N)
@@ -384,15 +384,21 @@ XS_API xs_status xs_launch_count(xs_context* ctx, int64_t* count);
  *     static device array of 16 MiB that every GPU loading the library keeps
  *     until the process exits.  Requests needing more are rejected with
  *     XS_ERR_INVALID_ARG and a message giving the bytes needed and available.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress,
+ *     with the target device current); the lookup enqueues no work, and a
+ *     device reset or another context on the device cannot leave a stale
+ *     address behind.  The first call on a device may load the library's
+ *     device code there: make that first call before any stream capture.
  *   - All calls share the array and it keeps the last call's contents (each
  *     call writes every byte it reads).  Calls whose kernels overlap on the
  *     GPU (unordered streams) race on it.
  *   - traj->pos, traj->f, I_out and amp_out (nullable) are device memory laid
  *     out as for xs_intensity; dev_err is an optional caller-owned device int
  *     that the kernels OR with 2 when a position or form factor is not finite.
+ *   - Argument checks are those of xs_intensity: grid extents up to 65,536,
+ *     at most 2^31 atoms and 65,535 frames, and every pointer the kernels use
+ *     must be device (or managed) memory; anything else returns
+ *     XS_ERR_INVALID_ARG before a kernel is launched.
  */
 XS_API xs_status xs_intensity_fp32_static(const xs_traj* traj, const xs_qgrid* grid, float* I_out,
                                           float* amp_out, int* dev_err, void* cuda_stream);

@@ -115,3 +115,26 @@ def test_ewald_points_host_helper_matches_oracle():
         m2, v2 = oracle.ewald_points(box, k, *win)
         assert np.array_equal(v1, v2)
         assert np.array_equal(m1[v1], m2[v2])
+
+
+def test_static_entry_rejects_bad_arguments_before_any_launch(lib):
+    # the allocation-free entry applies xs_intensity's checks: grid extents,
+    # atom count and memory kind of every pointer a kernel would dereference;
+    # host buffers are refused with XS_ERR_INVALID_ARG instead of reaching a
+    # kernel (on a machine without a GPU every buffer counts as host memory)
+    from paper_2204_13241_gb300 import api
+    pos = np.zeros((2, 10, 3), np.float32)
+    f = np.ones(10, np.float32)
+    I = np.zeros((2, 1, 8, 8), np.float32)
+    tr = nat.Traj(pos.ctypes.data, 0, f.ctypes.data, 10, 2, api._box(np.eye(3) * 10.0))
+    g = nat.QGrid(-4, 8, -4, 8, 0, 1)
+    st = lib.xs_intensity_fp32_static(ctypes.byref(tr), ctypes.byref(g), I.ctypes.data, None, None, None)
+    assert st == 1
+    assert "device memory" in lib.xs_last_error().decode()
+    big = nat.QGrid(0, 65537, 0, 1, 0, 1)
+    st = lib.xs_intensity_fp32_static(ctypes.byref(tr), ctypes.byref(big), I.ctypes.data, None, None, None)
+    assert st == 1 and "extent" in lib.xs_last_error().decode()
+    many = nat.Traj(pos.ctypes.data, 0, f.ctypes.data, (1 << 31) + 1, 2, api._box(np.eye(3) * 10.0))
+    st = lib.xs_intensity_fp32_static(ctypes.byref(many), ctypes.byref(g), I.ctypes.data, None, None, None)
+    assert st == 1 and "2^31" in lib.xs_last_error().decode()
+    assert lib.xs_intensity_fp32_static(None, ctypes.byref(g), I.ctypes.data, None, None, None) == 1

@@ -11,7 +11,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_util import e_I
+from gpu_util import check_I, e_I, e_pix
 from paper_2204_13241_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -65,10 +65,10 @@ def test_batched_matches_single_calls_and_oracle(xs, prec):
         # a mirrored plane carries the split rounding of -q where the single
         # call has that of q; both stay within 1e-4 of the oracle below
         assert e <= (1e-4 if grid.nx == 192 else 1e-5), e
+        assert e_pix(got, ref_s, m) <= (2e-3 if grid.nx == 192 else 2e-4)
         t = pos.shape[0] - 1
         ref = oracle.intensity(pos[t:t + 1], f, box, m)
-        e, e0 = e_I(got[t:t + 1], ref, m)
-        assert e <= 1e-4 and e0 <= 1e-4, (e, e0)
+        check_I(got[t:t + 1], ref, m, prec, what=str(grid))
 
 
 def test_centred_192_plane_from_half_plane_and_mirrors(xs):
@@ -87,8 +87,7 @@ def test_centred_192_plane_from_half_plane_and_mirrors(xs):
     pick = np.flatnonzero(lines)
     pick = np.unique(np.concatenate([pick, np.random.default_rng(2).choice(m.shape[0], 300, replace=False)]))
     ref = oracle.intensity(pos, f, box, m[pick])
-    e, e0 = e_I(got[:, pick], ref, m[pick])
-    assert e <= 1e-4 and e0 <= 1e-4, (e, e0)
+    check_I(got[:, pick], ref, m[pick], "fp16")
     # mirrored pixels are exact copies of their partners
     g = got.reshape(2, 192, 192)
     assert np.array_equal(g[:, 96 + 5, 96 + 7], g[:, 96 - 5, 96 - 7])
@@ -116,8 +115,7 @@ def test_batched_graph_replay_and_edge_entries(xs):
     assert torch.equal(outs[0], first)
     assert n1 - n0 >= 2   # one phase kernel and the persistent contraction
     ref = oracle.intensity(pos, f, box, grids[0].miller())
-    e, _ = e_I(first.reshape(3, -1).cpu().numpy(), ref, grids[0].miller())
-    assert e <= 1e-4
+    check_I(first.reshape(3, -1).cpu().numpy(), ref, grids[0].miller(), "bf16")
 
 
 def test_brownian_gas_batch_g2_follows_diffusion_closed_form(xs):

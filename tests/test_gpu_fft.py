@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_util import e_I
+from gpu_util import e_I, e_pix
 from paper_2204_13241_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -40,9 +40,11 @@ def test_fft_method_matches_oracle_algorithm_2_and_direct_sum(xs):
     alg2 = oracle.fft_intensity(pos, f, box, 64, 0.35, 0, m)
     e, e0 = e_I(got, alg2, m)
     assert e <= 1e-6 and e0 <= 1e-6, (e, e0)             # same method, FP64 on both sides
+    assert e_pix(got, alg2, m) <= 5e-6                   # float32 output of an FP64 result
     direct = oracle.intensity(pos, f, box, m)
     e, e0 = e_I(got, direct, m)
     assert e <= 1e-4 and e0 <= 1e-4, (e, e0)             # the method's own grid and cut-off error
+    assert e_pix(got, direct, m) <= 2e-3
 
 
 def test_fft_method_orthorhombic_plane_and_one_atom(xs):
@@ -56,6 +58,7 @@ def test_fft_method_orthorhombic_plane_and_one_atom(xs):
     alg2 = oracle.fft_intensity(pos, f, box, 128, 0.3, 0, m)
     e, _ = e_I(I.reshape(2, -1).cpu().numpy(), alg2, m)
     assert e <= 1e-6, e
+    assert e_pix(I.reshape(2, -1).cpu().numpy(), alg2, m) <= 5e-6
     # one atom on a grid point: I = f^2 at every q
     h = 16.0 / 128
     one = torch.tensor([[[5 * h, 0.0, 0.0]]], device="cuda")

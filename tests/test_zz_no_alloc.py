@@ -1,17 +1,20 @@
 """xs_intensity_fp32_static: the FP32 direct-sum intensity for callers that
-cannot allocate device memory when they need it (code running during CUDA
-stream capture, hosts with a device memory budget fixed at start-up,
-processes whose framework allocator already holds the device).  Its scratch is
-a static device array, so it must give what xs_intensity gives on the same
-inputs.  This file runs last: two calls in a row through the C ABI, each
-compared with the context-based entry point at the FP32 path's 1e-6."""
+cannot allocate device memory when they need it (hosts with a device memory
+budget fixed at start-up, plug-ins inside an application that owns the
+device memory, processes whose framework allocator already holds the
+device).  Its scratch is a static device array, so it must give what
+xs_intensity gives on the same inputs.  This file runs last: two calls in a
+row through the C ABI, each compared with the context-based entry point at
+the FP32 path's 1e-6, and the first also with the FP64 oracle; host buffers
+are refused before any kernel runs."""
 import ctypes
 
 import numpy as np
 import pytest
 import torch
 
-from gpu_util import e_I
+import oracle
+from gpu_util import check_I, e_I
 from paper_2204_13241_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -56,10 +59,14 @@ def test_static_scratch_entry_matches_xs_intensity_on_two_calls(lib):
         st = lib.xs_intensity_fp32_static(ctypes.byref(tr), ctypes.byref(g), I.data_ptr(), A.data_ptr(),
                                           err.data_ptr(), stream)
         assert st == 0, lib.xs_last_error().decode()
-        outs.append((p, fd, box, grid, I, A))
+        outs.append((p, fd, box, grid, I, A, pos, f))
     torch.cuda.synchronize()
     assert int(err.item()) == 0
-    for p, fd, box, grid, I, A in outs:
+    # the first call against the FP64 oracle as well
+    p, fd, box, grid, I, A, pos, f = outs[0]
+    ref = oracle.intensity(pos, f, box, grid.miller())
+    check_I(I.reshape(I.shape[0], -1).cpu().numpy(), ref, grid.miller(), "fp32")
+    for p, fd, box, grid, I, A, _, _ in outs:
         I_ref, A_ref = api.intensity(p, fd, box, grid, "fp32", want_amp=True)
         api.Context.get().sync_status()
         m = grid.miller()
@@ -86,3 +93,22 @@ def test_static_scratch_entry_rejects_oversized_requests(lib):
                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == 1
     assert "static scratch holds" in lib.xs_last_error().decode()
+
+
+def test_static_scratch_entry_refuses_host_buffers(lib):
+    from paper_2204_13241_gb300 import _native as nat
+    from paper_2204_13241_gb300 import api
+
+    p = torch.zeros((1, 16, 3), dtype=torch.float32, device="cuda")
+    fd = torch.ones(16, dtype=torch.float32, device="cuda")
+    I_host = torch.zeros((1, 1, 8, 8), dtype=torch.float32)
+    tr = nat.Traj(p.data_ptr(), 0, fd.data_ptr(), 16, 1, api._box(np.eye(3) * 10.0))
+    g = nat.QGrid(-4, 8, -4, 8, 0, 1)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = lib.xs_intensity_fp32_static(ctypes.byref(tr), ctypes.byref(g), I_host.data_ptr(), None, None, stream)
+    assert st == 1 and "device memory" in lib.xs_last_error().decode()
+    pos_host = torch.zeros((1, 16, 3), dtype=torch.float32)
+    tr = nat.Traj(pos_host.data_ptr(), 0, fd.data_ptr(), 16, 1, api._box(np.eye(3) * 10.0))
+    I = torch.zeros((1, 1, 8, 8), dtype=torch.float32, device="cuda")
+    st = lib.xs_intensity_fp32_static(ctypes.byref(tr), ctypes.byref(g), I.data_ptr(), None, None, stream)
+    assert st == 1 and "device memory" in lib.xs_last_error().decode()
