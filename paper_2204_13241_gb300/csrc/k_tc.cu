@@ -20,9 +20,10 @@
 //   * 8 producer warps per CTA write the tables straight into shared memory in
 //     the MN-major, 128-byte-swizzled layout the tensor core reads.  Each
 //     thread owns one atom and a run of 32 consecutive n, held as pairs
-//     (n, n+1) in packed FP32x2 registers: the run starts from exact seeds
-//     exp(i 2 pi n0 U) and exp(i 2 pi (n0+1) U) (U = 32-bit turn count, n U mod
-//     2^32 is exact) and advances by the exact step exp(i 2 pi 2U).  Each value
+//     (n, n+1) in packed FP32x2 registers: the run starts from seeds
+//     exp(i 2 pi n0 U) and exp(i 2 pi (n0+1) U) of exact turn counts (U =
+//     32-bit turn count, n U mod 2^32 is exact), evaluated in registers
+//     (cis_turns), and advances by the step exp(i 2 pi 2U).  Each value
 //     c is split into hi = RN(c) and lo = RN(c - hi) (FP16 or BF16).
 //   * Producer warps arrive on a barrier of their own CTA (CTA-scope
 //     release); in CTA 1 one relay thread forwards each filled stage to CTA 0
@@ -77,7 +78,6 @@ constexpr uint32_t kMNBlockBytes = (kBK / 8) * 1024;  // 8 KB: leading byte offs
 constexpr uint32_t kHalfBytes = 2 * kMNBlockBytes;     // 128 rows of one operand half
 constexpr uint32_t kStageBytes = 4 * kHalfBytes;       // A hi, A lo, B hi, B lo: 64 KB
 constexpr uint32_t kTmemCols = 512;                    // two 256-column FP32 accumulators
-constexpr int kTabSize = 256;
 
 struct SmemCtl {
     uint64_t full[kStages];   // CTA 0: its producer warps and the peer's relay
@@ -88,7 +88,6 @@ struct SmemCtl {
     uint64_t drain;
     uint32_t tmem_base;
     int abort;
-    float2 tab[kTabSize];     // exp(i 2 pi k / 256)
 };
 
 constexpr size_t kSmemBytes = 1024 + kStages * kStageBytes + sizeof(SmemCtl);
@@ -272,17 +271,17 @@ __device__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_fla
 
 // ---- table construction ------------------------------------------------------
 
-// exp(i 2 pi P / 2^32) for a 32-bit turn count: the top 8 bits pick
-// exp(i 2 pi k / 256) from a table, the remaining angle t < 2 pi / 256 uses the
-// Taylor polynomials cos t = 1 - t^2/2 + t^4/24 and sin t = t - t^3/6 + t^5/120
-// (truncation below 3e-13), and the two factors are multiplied.
-__device__ __forceinline__ float2 cis_turns(uint32_t P, const float2* tab) {
-    const float2 a = tab[P >> 24];
-    const float t = (float)(P & 0xFFFFFFu) * 1.4629180792671596e-9f;  // 2 pi / 2^32
-    const float t2 = t * t;
-    const float c = fmaf(t2, fmaf(t2, 1.0f / 24.0f, -0.5f), 1.0f);
-    const float s = t * fmaf(t2, fmaf(t2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
-    return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+// exp(i 2 pi P / 2^32) for a 32-bit turn count, in registers: sincospif of the
+// top 24 bits ((P >> 8) 2^-23 in [0, 2) is exact in FP32), rotated by the
+// remaining angle t = (P & 255) 2 pi / 2^32 < 3.8e-7 rad, for which cos t = 1
+// and sin t = t hold to FP32 precision (the neglected terms are below 1e-13).
+// No shared-memory table: the producers' random table loads had taken 12% of
+// the shared-memory data stage, which the tensor core's operand reads share.
+__device__ __forceinline__ float2 cis_turns(uint32_t P) {
+    float s, c;
+    sincospif((float)(P >> 8) * 1.1920928955078125e-7f, &s, &c);  // 2^-23
+    const float t = (float)(P & 0xFFu) * 1.4629180792671596e-9f;  // 2 pi / 2^32
+    return make_float2(fmaf(-s, t, c), fmaf(c, t, s));
 }
 
 // v = (v0, v1) -> packed hi = (RN(v0), RN(v1)) and lo = (RN(v0 - hi0), RN(v1 - hi1));
@@ -448,11 +447,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
     const uint32_t rank = cluster_rank();  // 0: issues the MMAs of the pair
     const int64_t pair = blockIdx.x >> 1, n_pairs = gridDim.x >> 1;
 
-    for (int i = threadIdx.x; i < kTabSize; i += kThreads) {
-        double s, c;
-        sincospi((double)i / (kTabSize / 2), &s, &c);
-        ctl->tab[i] = make_float2((float)c, (float)s);
-    }
     if (threadIdx.x == kMmaWarp * 32) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&ctl->full[s], kProdWarps + 1);
@@ -515,18 +509,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                     r_next = __ldg(up_next.rec + (int64_t)up_next.s0 * kBK + k);
                 // exact step z^2 and seeds E(n0), E(n0 + 1) of this thread's run
                 const uint32_t U = is_a ? r.x : r.y;
-                const float2 z2 = cis_turns(2u * U, ctl->tab);
+                const float2 z2 = cis_turns(2u * U);
                 const float2 ZR = make_float2(z2.x, z2.x), ZI = make_float2(z2.y, z2.y);
                 const float2 NZI = make_float2(-z2.y, -z2.y);
-                float2 E0 = cis_turns(n0 * U, ctl->tab);
-                float2 E1 = cis_turns((n0 + 1u) * U, ctl->tab);
+                float2 E0 = cis_turns(n0 * U);
+                float2 E1 = cis_turns((n0 + 1u) * U);
                 float2 Ex = make_float2(0.0f, 0.0f);
-                if (extra) Ex = cis_turns((uint32_t)(32 * (int)rank + 32) * U, ctl->tab);
+                if (extra) Ex = cis_turns((uint32_t)(32 * (int)rank + 32) * U);
                 if (!is_a) {
                     const float f = __uint_as_float(r.w);
                     float2 wv = make_float2(f, 0.0f);
                     if (nz != 0u) {
-                        const float2 ez = cis_turns(nz * r.z, ctl->tab);
+                        const float2 ez = cis_turns(nz * r.z);
                         wv = make_float2(f * ez.x, f * ez.y);
                     }
                     E0 = cmul(E0, wv);
