@@ -149,6 +149,52 @@ XS_API xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, cons
                                void* cuda_stream);
 
 /*
+ * The correlation stages requested for one trajectory of xs_xpcs_batched,
+ * both of the trajectory's own intensity: g2 on its delays (Sec. 2.3 Eq.
+ * g2_def, as xs_g2) and the XSVS contrast on its window lengths and |q| rings
+ * (Sec. 2.3 Eqs. inte_Iq and bq_Iq, as xs_xsvs_contrast).  A stage whose count
+ * (n_tau, or n_K or n_rings) is 0 is skipped.
+ *   taus            host int32 [n_tau], each in [0, n_frames)
+ *   g2_out          device float64 [n_tau][P], P = pixels of the trajectory's grid
+ *   mean_out        device float64 [P], or NULL
+ *   Ks              host int32 [n_K], each in [1, n_frames]
+ *   ring_width      in (0, 1], in units of 2 pi / det(h)^(1/3); rings as in
+ *                   xs_xsvs_contrast
+ *   beta_out        device float64 [n_K][n_rings]
+ *   ring_count_out  host int32 [n_rings] (pixels per ring, written during the
+ *                   call), or NULL
+ */
+typedef struct {
+    const int32_t* taus;
+    int32_t n_tau;
+    double* g2_out;
+    double* mean_out;
+    const int32_t* Ks;
+    int32_t n_K;
+    double ring_width;
+    int32_t n_rings;
+    double* beta_out;
+    int32_t* ring_count_out;
+} xs_corr_request;
+
+/*
+ * The batched pipeline of the direct method: the intensities of many
+ * trajectories as in xs_intensity_batched (Algorithm 1, Sec. 3.1), then each
+ * trajectory's g2 and XSVS contrast as requested in req[i] (a host array of
+ * n_traj requests; Sec. 2.3).  With the split precisions every kernel of the
+ * call -- the phase records, the one persistent contraction over all
+ * trajectories, the mirror fills and, trajectory after trajectory, the g2 and
+ * XSVS kernels -- is captured into one CUDA graph on the first call and
+ * replayed by later calls with the same arguments.  The correlation stages of
+ * the trajectories share one region of the context workspace and run in
+ * order.  Invalid requests (a delay or window length out of range, a missing
+ * output) return XS_ERR_INVALID_ARG before anything is launched.
+ */
+XS_API xs_status xs_xpcs_batched(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, int32_t n_traj,
+                                 xs_precision prec, float* const* I_out, const xs_corr_request* req,
+                                 void* cuda_stream);
+
+/*
  * The paper's FFT-based method (Sec. 3.2, Algorithm 2), as a cross-check of the
  * direct method: each atom's Gaussian (standard deviation eta, in A) is added
  * on the k nearest grid points per axis of an n_grid^3 grid over the

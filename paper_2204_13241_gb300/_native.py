@@ -20,7 +20,8 @@ EXPORTS = ["xs_context_create", "xs_context_destroy", "xs_intensity", "xs_intens
            "xs_xsvs_contrast", "xs_ring_index", "xs_intensity_backward", "xs_tune", "xs_last_error",
            "xs_sync_status", "xs_set_wait_timeout_ns", "xs_version", "xs_profile_enable", "xs_profile_read",
            "xs_launch_count", "xs_intensity_fp32_static", "xs_isf", "xs_contrast_from_isf", "xs_intensity_species",
-           "xs_intensity_points", "xs_ewald_points", "xs_intensity_fft", "xs_xsvs_partial", "xs_xsvs_finalize"]
+           "xs_intensity_points", "xs_ewald_points", "xs_intensity_fft", "xs_xsvs_partial", "xs_xsvs_finalize",
+           "xs_xpcs_batched"]
 
 
 class XsError(RuntimeError):
@@ -44,6 +45,13 @@ class Traj(ctypes.Structure):
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class CorrRequest(ctypes.Structure):
+    _fields_ = [("taus", ctypes.c_void_p), ("n_tau", ctypes.c_int32), ("g2_out", ctypes.c_void_p),
+                ("mean_out", ctypes.c_void_p), ("Ks", ctypes.c_void_p), ("n_K", ctypes.c_int32),
+                ("ring_width", ctypes.c_double), ("n_rings", ctypes.c_int32), ("beta_out", ctypes.c_void_p),
+                ("ring_count_out", ctypes.c_void_p)]
 
 
 class Allocator(ctypes.Structure):
@@ -73,6 +81,8 @@ def load() -> ctypes.CDLL:
         "xs_context_destroy": ([P], st),
         "xs_intensity": ([P, ctypes.POINTER(Traj), ctypes.POINTER(QGrid), st, P, P, P], st),
         "xs_intensity_batched": ([P, ctypes.POINTER(Traj), ctypes.POINTER(QGrid), I32, st, P, P], st),
+        "xs_xpcs_batched": ([P, ctypes.POINTER(Traj), ctypes.POINTER(QGrid), I32, st, P, ctypes.POINTER(CorrRequest),
+                             P], st),
         "xs_g2": ([P, P, I64, I64, P, I32, P, P, P], st),
         "xs_xsvs_contrast": ([P, P, I64, ctypes.POINTER(QGrid), ctypes.POINTER(Box), P, I32, D, I32, P, P, P], st),
         "xs_ring_index": ([ctypes.POINTER(QGrid), ctypes.POINTER(Box), D, I32, P], st),

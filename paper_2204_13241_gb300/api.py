@@ -246,6 +246,50 @@ def intensity_batched(trajs: Sequence[tuple], grids: Sequence, precision: str = 
     return outs
 
 
+def xpcs_batched(trajs: Sequence[tuple], grids: Sequence, taus: Sequence, Ks: Sequence, n_rings: Sequence[int],
+                 precision: str = "bf16", ring_width: float = 1.0, outs: Optional[Sequence[torch.Tensor]] = None):
+    """Batched pipeline: intensities of many trajectories (pos, f, box) on their
+    own grids, then each one's g2 on taus[i] (Sec. 2.3 Eq. g2_def) and XSVS
+    contrast on Ks[i] over n_rings[i] rings (Eqs. inte_Iq, bq_Iq), in one call
+    (one captured graph on the split paths).  Returns (I, g2, mean, beta,
+    ring counts) lists."""
+    n = len(trajs)
+    arr_t = (nat.Traj * n)()
+    arr_g = (nat.QGrid * n)()
+    for i, (pos, f, box) in enumerate(trajs):
+        tr, host = _traj(pos, f, box)
+        if host:
+            raise ValueError("batched trajectories need device positions")
+        arr_t[i] = tr
+        arr_g[i] = _grid(grids[i])
+    if outs is None:
+        outs = [torch.empty((int(arr_t[i].n_frames), arr_g[i].nz, arr_g[i].ny, arr_g[i].nx), dtype=torch.float32,
+                            device="cuda") for i in range(n)]
+    reqs = (nat.CorrRequest * n)()
+    keep, g2s, means, betas, counts = [], [], [], [], []
+    for i in range(n):
+        P = arr_g[i].nx * arr_g[i].ny * arr_g[i].nz
+        t = np.ascontiguousarray(taus[i], dtype=np.int32)
+        k = np.ascontiguousarray(Ks[i], dtype=np.int32)
+        g = torch.empty((t.size, P), dtype=torch.float64, device="cuda")
+        m = torch.empty((P,), dtype=torch.float64, device="cuda")
+        b = torch.empty((k.size, int(n_rings[i])), dtype=torch.float64, device="cuda")
+        c = np.zeros(int(n_rings[i]), dtype=np.int32)
+        keep += [t, k]
+        reqs[i] = nat.CorrRequest(t.ctypes.data if t.size else None, t.size, g.data_ptr() if t.size else None,
+                                  m.data_ptr(), k.ctypes.data if k.size else None, k.size, float(ring_width),
+                                  int(n_rings[i]), b.data_ptr() if b.numel() else None,
+                                  c.ctypes.data if c.size else None)
+        g2s.append(g)
+        means.append(m)
+        betas.append(b)
+        counts.append(c)
+    ptrs = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    ctx = Context.get()
+    nat.check(ctx.lib.xs_xpcs_batched(ctx.handle, arr_t, arr_g, n, nat.PRECISIONS[precision], ptrs, reqs, _stream()))
+    return outs, g2s, means, betas, counts
+
+
 def tune(pos: torch.Tensor, f: torch.Tensor, box, grid, precision: str = "fp16") -> None:
     tr, host = _traj(pos, f, box)
     g = _grid(grid)

@@ -1046,179 +1046,6 @@ xs_status xs_intensity_species(xs_context* ctx, const xs_traj* traj, const int32
     return XS_OK;
 }
 
-xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, int32_t n_traj,
-                               xs_precision prec, float* const* I_out, void* cuda_stream) {
-    if (!ctx || !traj || !grid || !I_out || n_traj < 1) return fail(XS_ERR_INVALID_ARG, "bad batched arguments");
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    if (prec == XS_PREC_FP32_DIRECT) {
-        for (int32_t i = 0; i < n_traj; ++i) {
-            if (traj[i].pos_on_host) return fail(XS_ERR_INVALID_ARG, "batched trajectories need device positions");
-            xs_status s = intensity_impl(ctx, &traj[i], &grid[i], prec, I_out[i], nullptr, st, 0);
-            if (s != XS_OK) return s;
-        }
-        return XS_OK;
-    }
-    if (prec != XS_PREC_SPLIT_FP16 && prec != XS_PREC_SPLIT_BF16)
-        return fail(XS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
-    // validate and lay out the phase records of every trajectory
-    struct Job {
-        int64_t N, T, n_pad;
-        double hinv[9];
-        GridDesc g;
-        size_t rec_off;
-        int half_axis = -1;  // >= 0: computed on the half grid v, the rest by mirrors
-        GridDesc v;
-        size_t half_off = 0;
-    };
-    std::vector<Job> jobs((size_t)n_traj);
-    size_t off = 0;
-    auto carve = [&](size_t bytes) {
-        size_t o = round_up((int64_t)off, 256);
-        off = o + bytes;
-        return o;
-    };
-    for (int32_t i = 0; i < n_traj; ++i) {
-        const xs_traj& t = traj[i];
-        xs_status s = check_grid(&grid[i]);
-        if (s != XS_OK) return s;
-        if (t.pos_on_host) return fail(XS_ERR_INVALID_ARG, "trajectory %d: batched positions must be on the device", i);
-        if (t.n_atoms < 0 || t.n_frames < 0) return fail(XS_ERR_INVALID_ARG, "trajectory %d: negative size", i);
-        if (t.n_atoms > 0 && t.n_frames > 0 && (!t.pos || !t.f))
-            return fail(XS_ERR_INVALID_ARG, "trajectory %d: NULL positions", i);
-        if (t.n_frames > 0 && grid[i].nx * (int64_t)grid[i].ny * grid[i].nz > 0 && !I_out[i])
-            return fail(XS_ERR_INVALID_ARG, "trajectory %d: NULL output", i);
-        Job& j = jobs[(size_t)i];
-        if (!invert3(t.box.h, j.hinv)) return fail(XS_ERR_INVALID_ARG, "trajectory %d: singular cell matrix", i);
-        j.N = t.n_atoms;
-        j.T = t.n_frames;
-        j.n_pad = round_up(j.N > 0 ? j.N : 1, 64);
-        j.g = to_desc(&grid[i]);
-        if (j.T > 65535 * 8) return fail(XS_ERR_INVALID_ARG, "trajectory %d: too many frames", i);
-        j.rec_off = carve((size_t)j.T * j.n_pad * sizeof(AtomRec));
-        if (j.N > 0 && j.T > 0 && j.g.pixels() > 0) {
-            j.half_axis = friedel_half_grid(j.g, j.v);
-            if (j.half_axis >= 0) j.half_off = carve((size_t)j.T * j.v.pixels() * sizeof(float));
-        }
-    }
-    const int cap = tc_pair_capacity(ctx->num_sms);
-    const size_t o_scratch = carve(tc_scratch_bytes(cap));
-    xs_status s = ensure_ws(ctx, off + 256);
-    if (s != XS_OK) return s;
-    char* ws = static_cast<char*>(ctx->ws);
-
-    // trajectory table and per-pair unit lists (longest first)
-    std::vector<TcTraj> trs;
-    std::vector<int> which;  // trajectory index of each table entry
-    std::vector<int> empty;  // trajectories without atoms: I = 0
-    for (int32_t i = 0; i < n_traj; ++i) {
-        const Job& j = jobs[(size_t)i];
-        if (j.T == 0 || j.g.pixels() == 0) continue;
-        if (j.N == 0) {
-            empty.push_back(i);
-            continue;
-        }
-        if (j.half_axis >= 0)
-            trs.push_back(tc_traj(reinterpret_cast<AtomRec*>(ws + j.rec_off), j.n_pad, j.T, j.v,
-                                  reinterpret_cast<float*>(ws + j.half_off), nullptr));
-        else
-            trs.push_back(tc_traj(reinterpret_cast<AtomRec*>(ws + j.rec_off), j.n_pad, j.T, j.g, I_out[i], nullptr));
-        which.push_back(i);
-    }
-    for (int i : empty)
-        XS_CUDA(cudaMemsetAsync(I_out[i], 0, (size_t)jobs[(size_t)i].T * jobs[(size_t)i].g.pixels() * sizeof(float), st));
-    if (trs.empty()) return XS_OK;
-    int64_t total_units = 0;
-    for (const TcTraj& t : trs) total_units += tc_units(t);
-    const int n_pairs = (int)std::min<int64_t>(cap, total_units);
-    std::vector<int4> units;
-    std::vector<int> pair_start;
-    tc_build_lists(trs, n_pairs, units, pair_start);
-    if (units.size() > (size_t)INT32_MAX) return fail(XS_ERR_UNSUPPORTED, "too many work units");
-    std::vector<char> blob;
-    const size_t o_tr = push(blob, trs.data(), trs.size());
-    const size_t o_units = push(blob, units.data(), units.size());
-    const size_t o_ps = push(blob, pair_start.data(), pair_start.size());
-    void* d = nullptr;
-    s = upload_const(ctx, "tc_batch", blob, st, &d);
-    if (s != XS_OK) return s;
-    char* dc = static_cast<char*>(d);
-    int chunk = kDefaultChunkStages;
-    {
-        auto it = ctx->tuned_chunk.find(std::make_tuple(trs[trs.size() / 2].n_pad, trs[trs.size() / 2].nx,
-                                                        trs[trs.size() / 2].ny, trs[trs.size() / 2].nz, (int)prec));
-        if (it != ctx->tuned_chunk.end()) chunk = it->second;
-    }
-    const bool bf16 = prec == XS_PREC_SPLIT_BF16;
-    auto enqueue = [&]() -> cudaError_t {
-        for (size_t e = 0; e < trs.size(); ++e) {
-            const Job& j = jobs[(size_t)which[e]];
-            const xs_traj& t = traj[which[e]];
-            Mat3 hm;
-            for (int k = 0; k < 9; ++k) hm.a[k] = j.hinv[k];
-            PhaseOpts popt;
-            popt.ortho = is_ortho(j.hinv);
-            const GridDesc& gc = j.half_axis >= 0 ? j.v : j.g;
-            popt.need_z = !(gc.nz == 1 && gc.nz0 == 0);
-            popt.perm_mul = coprime_stride(j.n_pad / kPermRun);
-            cudaError_t err = launch_phase(t.pos, t.f, j.N, j.T, j.n_pad, hm, popt,
-                                           reinterpret_cast<AtomRec*>(ws + j.rec_off), ctx->d_err, st);
-            if (err != cudaSuccess) return err;
-        }
-        cudaError_t err = launch_tc_batch(reinterpret_cast<const TcTraj*>(dc + o_tr),
-                                          reinterpret_cast<const int4*>(dc + o_units),
-                                          reinterpret_cast<const int*>(dc + o_ps), n_pairs, chunk, bf16,
-                                          reinterpret_cast<double*>(ws + o_scratch), ctx->d_err, ctx->timeout_ns, st);
-        for (size_t e = 0; e < trs.size() && err == cudaSuccess; ++e) {
-            const Job& j = jobs[(size_t)which[e]];
-            if (j.half_axis >= 0)
-                err = launch_friedel(reinterpret_cast<const float*>(ws + j.half_off), nullptr, j.T, j.v, j.g,
-                                     j.half_axis, I_out[which[e]], nullptr, st);
-        }
-        return err;
-    };
-    // the same batch (same tables, inputs, outputs and workspace) replays a
-    // captured graph; anything else is captured once and kept
-    std::string key(blob.begin(), blob.end());
-    for (int32_t i = 0; i < n_traj; ++i) {
-        const void* ptrs[3] = {traj[i].pos, traj[i].f, I_out[i]};
-        key.append(reinterpret_cast<const char*>(ptrs), sizeof(ptrs));
-        key.append(reinterpret_cast<const char*>(traj[i].box.h), sizeof(traj[i].box.h));
-    }
-    key.append(reinterpret_cast<const char*>(&chunk), sizeof(chunk));
-    key.append(reinterpret_cast<const char*>(&ctx->timeout_ns), sizeof(ctx->timeout_ns));
-    key.append(bf16 ? "b" : "h");
-    const void* wsp = ctx->ws;
-    key.append(reinterpret_cast<const char*>(&wsp), sizeof(wsp));
-    const cudaError_t launched = traced(ctx, "batched", st, [&]() -> cudaError_t {
-        auto it = ctx->graphs.find(key);
-        if (it == ctx->graphs.end() && st != nullptr) {
-            cudaGraph_t graph = nullptr;
-            const int64_t before = tl_kernel_launches;
-            cudaError_t err = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-            if (err == cudaSuccess) {
-                const cudaError_t le = enqueue();
-                err = cudaStreamEndCapture(st, &graph);
-                if (le != cudaSuccess) err = le;
-            }
-            const int64_t captured = tl_kernel_launches - before;
-            tl_kernel_launches = before;  // counted again at each replay
-            cudaGraphExec_t exec = nullptr;
-            if (err == cudaSuccess) err = cudaGraphInstantiate(&exec, graph, 0);
-            if (graph) cudaGraphDestroy(graph);
-            if (err != cudaSuccess) {
-                cudaGetLastError();
-                return err;
-            }
-            it = ctx->graphs.emplace(key, xs_context::Graph{exec, captured}).first;
-        }
-        if (it == ctx->graphs.end()) return enqueue();  // legacy default stream: no capture
-        tl_kernel_launches += it->second.kernels;
-        return cudaGraphLaunch(it->second.exec, st);
-    });
-    if (launched != cudaSuccess) return fail(XS_ERR_CUDA, "batched launch: %s", cudaGetErrorString(launched));
-    return XS_OK;
-}
-
 xs_status xs_tune(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, xs_precision prec, void* cuda_stream) {
     if (!ctx || !traj || !grid) return fail(XS_ERR_INVALID_ARG, "bad tune arguments");
     if (prec == XS_PREC_FP32_DIRECT) return XS_OK;
@@ -1367,6 +1194,53 @@ static xs_status ring_layout(const xs_qgrid* grid, const xs_box* box, double rin
     return XS_OK;
 }
 
+// Host tables of the XSVS contrast of one grid (Eqs. inte_Iq, bq_Iq): pixels
+// grouped by ring, (ring, start, count) chunks of at most 128 pixels, the
+// first chunk of each ring, and the offset of each window length's windows in
+// the (K, w) list.
+struct XsvsTables {
+    std::vector<int32_t> count, perm, chunks, first;
+    std::vector<int64_t> kw_off;
+    int64_t n_in = 0, n_kw = 0;
+    int n_chunks = 0;
+};
+
+static xs_status xsvs_tables(const xs_qgrid* grid, const xs_box* box, double ring_width, int32_t n_rings,
+                             const int32_t* Ks, int32_t n_K, int64_t T, XsvsTables& t) {
+    RingLayout lay;
+    xs_status s = ring_layout(grid, box, ring_width, n_rings, lay);
+    if (s != XS_OK) return s;
+    t.count = std::move(lay.count);
+    t.perm = std::move(lay.perm);
+    t.n_in = lay.start[(size_t)n_rings];
+    constexpr int kChunk = 128;
+    t.chunks.clear();  // int4 records (ring, start, count, 0)
+    t.first.assign((size_t)n_rings + 1, 0);
+    for (int r = 0; r < n_rings; ++r) {
+        t.first[(size_t)r] = (int32_t)(t.chunks.size() / 4);
+        for (int64_t a = lay.start[(size_t)r]; a < lay.start[(size_t)r + 1]; a += kChunk) {
+            t.chunks.push_back(r + 1);
+            t.chunks.push_back((int32_t)a);
+            t.chunks.push_back((int32_t)std::min<int64_t>(kChunk, lay.start[(size_t)r + 1] - a));
+            t.chunks.push_back(0);
+        }
+    }
+    t.n_chunks = (int)(t.chunks.size() / 4);
+    t.first[(size_t)n_rings] = t.n_chunks;
+    t.kw_off.assign((size_t)n_K + 1, 0);
+    for (int k = 0; k < n_K; ++k) t.kw_off[(size_t)k + 1] = t.kw_off[(size_t)k] + T / Ks[k];
+    t.n_kw = t.kw_off[(size_t)n_K];
+    return XS_OK;
+}
+
+// workspace of one XSVS evaluation: FP64 prefix rows, then (K, w) partials
+static size_t xsvs_prefix_bytes(int64_t T, const XsvsTables& t) {
+    return (size_t)round_up((int64_t)((size_t)xsvs_prefix_rows(T) * t.n_in * sizeof(double)), 256);
+}
+static size_t xsvs_ws_bytes(int64_t T, const XsvsTables& t) {
+    return xsvs_prefix_bytes(T, t) + (size_t)t.n_kw * t.n_chunks * sizeof(double2);
+}
+
 // --------------------------------------------------------------------------
 // XSVS over pixel shards: partial sums on the device, finalize on the host
 // --------------------------------------------------------------------------
@@ -1488,64 +1362,344 @@ xs_status xs_xsvs_contrast(xs_context* ctx, const float* I, int64_t T, const xs_
         if (Ks[k] < 1 || Ks[k] > T) return fail(XS_ERR_INVALID_ARG, "window length %d outside [1, T]", Ks[k]);
     if (n_K == 0 || n_rings == 0) return XS_OK;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    RingLayout lay;
-    s = ring_layout(grid, box, ring_width, n_rings, lay);
+    XsvsTables t;
+    s = xsvs_tables(grid, box, ring_width, n_rings, Ks, n_K, T, t);
     if (s != XS_OK) return s;
     const int64_t P = (int64_t)grid->nx * grid->ny * grid->nz;
-    const std::vector<int32_t>& count = lay.count;
-    const std::vector<int64_t>& start = lay.start;
-    const std::vector<int32_t>& perm = lay.perm;
-    const int64_t n_in = start[(size_t)n_rings];
-    constexpr int kChunk = 128;
-    std::vector<int32_t> chunks;  // int4 records (ring, start, count, 0)
-    std::vector<int32_t> first((size_t)n_rings + 1, 0);
-    for (int r = 0; r < n_rings; ++r) {
-        first[(size_t)r] = (int32_t)(chunks.size() / 4);
-        for (int64_t a = start[(size_t)r]; a < start[(size_t)r + 1]; a += kChunk) {
-            chunks.push_back(r + 1);
-            chunks.push_back((int32_t)a);
-            chunks.push_back((int32_t)std::min<int64_t>(kChunk, start[(size_t)r + 1] - a));
-            chunks.push_back(0);
-        }
-    }
-    const int n_chunks = (int)(chunks.size() / 4);
-    first[(size_t)n_rings] = n_chunks;
-    std::vector<int64_t> kw_off((size_t)n_K + 1, 0);
-    for (int k = 0; k < n_K; ++k) kw_off[(size_t)k + 1] = kw_off[(size_t)k] + T / Ks[k];
-    const int64_t n_kw = kw_off[(size_t)n_K];
-    if (ring_count_out) std::memcpy(ring_count_out, count.data(), count.size() * sizeof(int32_t));
+    if (ring_count_out) std::memcpy(ring_count_out, t.count.data(), t.count.size() * sizeof(int32_t));
 
     std::vector<char> blob;
     const int64_t key[2] = {T, P};
     push(blob, key, 2);
-    const size_t o_perm = push(blob, perm.data(), perm.size());
-    const size_t o_chunks = push(blob, chunks.data(), chunks.size());
+    const size_t o_perm = push(blob, t.perm.data(), t.perm.size());
+    const size_t o_chunks = push(blob, t.chunks.data(), t.chunks.size());
     const size_t o_K = push(blob, Ks, (size_t)n_K);
-    const size_t o_kw = push(blob, kw_off.data(), kw_off.size());
-    const size_t o_first = push(blob, first.data(), first.size());
-    const size_t o_count = push(blob, count.data(), count.size());
+    const size_t o_kw = push(blob, t.kw_off.data(), t.kw_off.size());
+    const size_t o_first = push(blob, t.first.data(), t.first.size());
+    const size_t o_count = push(blob, t.count.data(), t.count.size());
     void* d = nullptr;
     s = upload_const(ctx, "xsvs", blob, st, &d);
     if (s != XS_OK) return s;
     char* dc = static_cast<char*>(d);
-
-    size_t off = 0;
-    auto carve = [&](size_t bytes) {
-        size_t o = round_up((int64_t)off, 256);
-        off = o + bytes;
-        return o;
-    };
-    const size_t o_prefix = carve((size_t)xsvs_prefix_rows(T) * n_in * sizeof(double));
-    const size_t o_partial = carve((size_t)n_kw * n_chunks * sizeof(double2));
-    s = ensure_ws(ctx, off + 256);
+    s = ensure_ws(ctx, xsvs_ws_bytes(T, t) + 256);
     if (s != XS_OK) return s;
     char* ws = static_cast<char*>(ctx->ws);
+    const size_t o_prefix = 0, o_partial = xsvs_prefix_bytes(T, t);
+    const int n_chunks = t.n_chunks;
+    const int64_t n_in = t.n_in, n_kw = t.n_kw;
     XS_CUDA(traced(ctx, "xsvs", st, [&] { return launch_xsvs(I, T, P, reinterpret_cast<const int32_t*>(dc + o_perm), reinterpret_cast<const int4*>(dc + o_chunks),
                         n_chunks, n_in, reinterpret_cast<const int32_t*>(dc + o_K), reinterpret_cast<const int64_t*>(dc + o_kw),
                         n_K, n_kw, reinterpret_cast<const int32_t*>(dc + o_first), reinterpret_cast<const int32_t*>(dc + o_count),
                         n_rings, reinterpret_cast<double*>(ws + o_prefix), reinterpret_cast<double2*>(ws + o_partial),
                         beta_out, st); }));
     return XS_OK;
+}
+
+// --------------------------------------------------------------------------
+// batched trajectories: intensities, then g2 and XSVS per trajectory
+// --------------------------------------------------------------------------
+
+// One trajectory's correlation stages in the batched pipeline: the delays and
+// the XSVS tables live in the call's device blob at the recorded offsets.
+struct CorrPrep {
+    bool g2 = false, xsvs = false;
+    int64_t T = 0, P = 0;
+    int n_tau = 0;
+    size_t o_taus = 0;
+    XsvsTables t;
+    int n_K = 0, n_rings = 0;
+    size_t o_perm = 0, o_chunks = 0, o_K = 0, o_kw = 0, o_first = 0, o_count = 0;
+    size_t ws_bytes = 0;
+};
+
+// Validates request `r` of a trajectory with T frames on `grid` and appends
+// its device tables to `blob`.
+static xs_status corr_prepare(const xs_corr_request& r, int32_t i, int64_t T, const xs_qgrid* grid,
+                              const xs_box* box, std::vector<char>& blob, CorrPrep& cp) {
+    const int64_t P = (int64_t)grid->nx * grid->ny * grid->nz;
+    cp.T = T;
+    cp.P = P;
+    if (r.n_tau < 0 || r.n_K < 0 || r.n_rings < 0) return fail(XS_ERR_INVALID_ARG, "request %d: negative count", i);
+    if (r.n_tau > 0) {
+        if (!r.taus || !r.g2_out) return fail(XS_ERR_INVALID_ARG, "request %d: taus and g2_out are required", i);
+        for (int32_t k = 0; k < r.n_tau; ++k)
+            if (r.taus[k] < 0 || r.taus[k] >= T)
+                return fail(XS_ERR_INVALID_ARG, "request %d: delay %d outside [0, %lld)", i, r.taus[k], (long long)T);
+    }
+    if (r.n_K > 0 && r.n_rings > 0) {
+        if (!r.Ks || !r.beta_out) return fail(XS_ERR_INVALID_ARG, "request %d: Ks and beta_out are required", i);
+        if (!(r.ring_width > 0.0 && r.ring_width <= 1.0))
+            return fail(XS_ERR_INVALID_ARG, "request %d: ring_width must be in (0, 1]", i);
+        for (int32_t k = 0; k < r.n_K; ++k)
+            if (r.Ks[k] < 1 || r.Ks[k] > T)
+                return fail(XS_ERR_INVALID_ARG, "request %d: window length %d outside [1, %lld]", i, r.Ks[k],
+                            (long long)T);
+    }
+    if (P == 0 || T == 0) return XS_OK;
+    if (r.n_tau > 0) {
+        cp.g2 = true;
+        cp.n_tau = r.n_tau;
+        cp.o_taus = push(blob, r.taus, (size_t)r.n_tau);
+        cp.ws_bytes = std::max(cp.ws_bytes, g2_workspace_bytes(T, P, r.n_tau));
+    }
+    if (r.n_K > 0 && r.n_rings > 0) {
+        xs_status s = xsvs_tables(grid, box, r.ring_width, r.n_rings, r.Ks, r.n_K, T, cp.t);
+        if (s != XS_OK) return s;
+        if (r.ring_count_out) std::memcpy(r.ring_count_out, cp.t.count.data(), cp.t.count.size() * sizeof(int32_t));
+        cp.xsvs = true;
+        cp.n_K = r.n_K;
+        cp.n_rings = r.n_rings;
+        cp.o_perm = push(blob, cp.t.perm.data(), cp.t.perm.size());
+        cp.o_chunks = push(blob, cp.t.chunks.data(), cp.t.chunks.size());
+        cp.o_K = push(blob, r.Ks, (size_t)r.n_K);
+        cp.o_kw = push(blob, cp.t.kw_off.data(), cp.t.kw_off.size());
+        cp.o_first = push(blob, cp.t.first.data(), cp.t.first.size());
+        cp.o_count = push(blob, cp.t.count.data(), cp.t.count.size());
+        cp.ws_bytes = std::max(cp.ws_bytes, xsvs_ws_bytes(T, cp.t));
+    }
+    return XS_OK;
+}
+
+// Launches one trajectory's correlation stages (stream order: after its
+// intensity); `dc` is the device copy of the blob, `cws` the shared workspace.
+static cudaError_t corr_launch(const CorrPrep& cp, const xs_corr_request& r, const float* I, const char* dc,
+                               char* cws, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (cp.g2)
+        e = launch_g2(I, cp.T, cp.P, reinterpret_cast<const int32_t*>(dc + cp.o_taus), cp.n_tau, r.g2_out, r.mean_out,
+                      cws, st);
+    if (e == cudaSuccess && cp.xsvs)
+        e = launch_xsvs(I, cp.T, cp.P, reinterpret_cast<const int32_t*>(dc + cp.o_perm),
+                        reinterpret_cast<const int4*>(dc + cp.o_chunks), cp.t.n_chunks, cp.t.n_in,
+                        reinterpret_cast<const int32_t*>(dc + cp.o_K), reinterpret_cast<const int64_t*>(dc + cp.o_kw),
+                        cp.n_K, cp.t.n_kw, reinterpret_cast<const int32_t*>(dc + cp.o_first),
+                        reinterpret_cast<const int32_t*>(dc + cp.o_count), cp.n_rings, reinterpret_cast<double*>(cws),
+                        reinterpret_cast<double2*>(cws + xsvs_prefix_bytes(cp.T, cp.t)), r.beta_out, st);
+    return e;
+}
+
+// Intensities of many trajectories in one persistent contraction and, when
+// `req` is given, each trajectory's g2 and XSVS contrast after it; with the
+// split precisions all of it is one captured graph.
+static xs_status batched_impl(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, int32_t n_traj,
+                              xs_precision prec, float* const* I_out, const xs_corr_request* req, cudaStream_t st) {
+    if (!ctx || !traj || !grid || !I_out || n_traj < 1) return fail(XS_ERR_INVALID_ARG, "bad batched arguments");
+    if (prec == XS_PREC_FP32_DIRECT) {
+        for (int32_t i = 0; i < n_traj; ++i) {
+            if (traj[i].pos_on_host) return fail(XS_ERR_INVALID_ARG, "batched trajectories need device positions");
+            xs_status s = intensity_impl(ctx, &traj[i], &grid[i], prec, I_out[i], nullptr, st, 0);
+            if (s != XS_OK) return s;
+            if (!req) continue;
+            const xs_corr_request& r = req[i];
+            const int64_t T = traj[i].n_frames;
+            const int64_t P = (int64_t)grid[i].nx * grid[i].ny * grid[i].nz;
+            if (r.n_tau > 0) {
+                s = xs_g2(ctx, I_out[i], T, P, r.taus, r.n_tau, r.g2_out, r.mean_out, st);
+                if (s != XS_OK) return s;
+            }
+            if (r.n_K > 0 && r.n_rings > 0) {
+                s = xs_xsvs_contrast(ctx, I_out[i], T, &grid[i], &traj[i].box, r.Ks, r.n_K, r.ring_width, r.n_rings,
+                                     r.beta_out, r.ring_count_out, st);
+                if (s != XS_OK) return s;
+            }
+        }
+        return XS_OK;
+    }
+    if (prec != XS_PREC_SPLIT_FP16 && prec != XS_PREC_SPLIT_BF16)
+        return fail(XS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    // validate and lay out the phase records of every trajectory
+    struct Job {
+        int64_t N, T, n_pad;
+        double hinv[9];
+        GridDesc g;
+        size_t rec_off;
+        int half_axis = -1;  // >= 0: computed on the half grid v, the rest by mirrors
+        GridDesc v;
+        size_t half_off = 0;
+    };
+    std::vector<Job> jobs((size_t)n_traj);
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        size_t o = round_up((int64_t)off, 256);
+        off = o + bytes;
+        return o;
+    };
+    for (int32_t i = 0; i < n_traj; ++i) {
+        const xs_traj& t = traj[i];
+        xs_status s = check_grid(&grid[i]);
+        if (s != XS_OK) return s;
+        if (t.pos_on_host) return fail(XS_ERR_INVALID_ARG, "trajectory %d: batched positions must be on the device", i);
+        if (t.n_atoms < 0 || t.n_frames < 0) return fail(XS_ERR_INVALID_ARG, "trajectory %d: negative size", i);
+        if (t.n_atoms > 0 && t.n_frames > 0 && (!t.pos || !t.f))
+            return fail(XS_ERR_INVALID_ARG, "trajectory %d: NULL positions", i);
+        if (t.n_frames > 0 && grid[i].nx * (int64_t)grid[i].ny * grid[i].nz > 0 && !I_out[i])
+            return fail(XS_ERR_INVALID_ARG, "trajectory %d: NULL output", i);
+        Job& j = jobs[(size_t)i];
+        if (!invert3(t.box.h, j.hinv)) return fail(XS_ERR_INVALID_ARG, "trajectory %d: singular cell matrix", i);
+        j.N = t.n_atoms;
+        j.T = t.n_frames;
+        j.n_pad = round_up(j.N > 0 ? j.N : 1, 64);
+        j.g = to_desc(&grid[i]);
+        if (j.T > 65535 * 8) return fail(XS_ERR_INVALID_ARG, "trajectory %d: too many frames", i);
+        j.rec_off = carve((size_t)j.T * j.n_pad * sizeof(AtomRec));
+        if (j.N > 0 && j.T > 0 && j.g.pixels() > 0) {
+            j.half_axis = friedel_half_grid(j.g, j.v);
+            if (j.half_axis >= 0) j.half_off = carve((size_t)j.T * j.v.pixels() * sizeof(float));
+        }
+    }
+    const int cap = tc_pair_capacity(ctx->num_sms);
+    const size_t o_scratch = carve(tc_scratch_bytes(cap));
+
+    // trajectory table and per-pair unit lists (longest first)
+    std::vector<TcTraj> trs;
+    std::vector<int> which;  // trajectory index of each table entry
+    std::vector<int> empty;  // trajectories without atoms: I = 0
+    for (int32_t i = 0; i < n_traj; ++i) {
+        const Job& j = jobs[(size_t)i];
+        if (j.T == 0 || j.g.pixels() == 0) continue;
+        if (j.N == 0) {
+            empty.push_back(i);
+            continue;
+        }
+        which.push_back(i);
+    }
+    int64_t total_units = 0;
+    std::vector<char> blob;
+    // correlation requests: host tables into the blob, one shared workspace
+    std::vector<CorrPrep> corr(req ? (size_t)n_traj : 0);
+    size_t corr_ws = 0;
+    for (int32_t i = 0; req && i < n_traj; ++i) {
+        xs_status s = corr_prepare(req[i], i, traj[i].n_frames, &grid[i], &traj[i].box, blob, corr[(size_t)i]);
+        if (s != XS_OK) return s;
+        corr_ws = std::max(corr_ws, corr[(size_t)i].ws_bytes);
+    }
+    const size_t o_corr = carve(corr_ws);
+    xs_status s = ensure_ws(ctx, off + 256);
+    if (s != XS_OK) return s;
+    char* ws = static_cast<char*>(ctx->ws);
+    for (int i : which) {
+        const Job& j = jobs[(size_t)i];
+        if (j.half_axis >= 0)
+            trs.push_back(tc_traj(reinterpret_cast<AtomRec*>(ws + j.rec_off), j.n_pad, j.T, j.v,
+                                  reinterpret_cast<float*>(ws + j.half_off), nullptr));
+        else
+            trs.push_back(tc_traj(reinterpret_cast<AtomRec*>(ws + j.rec_off), j.n_pad, j.T, j.g, I_out[i], nullptr));
+    }
+    for (const TcTraj& t : trs) total_units += tc_units(t);
+    for (int i : empty)
+        XS_CUDA(cudaMemsetAsync(I_out[i], 0, (size_t)jobs[(size_t)i].T * jobs[(size_t)i].g.pixels() * sizeof(float), st));
+    if (trs.empty() && !req) return XS_OK;
+    const int n_pairs = (int)std::min<int64_t>(cap, std::max<int64_t>(total_units, 1));
+    std::vector<int4> units;
+    std::vector<int> pair_start;
+    size_t o_tr = 0, o_units = 0, o_ps = 0;
+    if (!trs.empty()) {
+        tc_build_lists(trs, n_pairs, units, pair_start);
+        if (units.size() > (size_t)INT32_MAX) return fail(XS_ERR_UNSUPPORTED, "too many work units");
+        o_tr = push(blob, trs.data(), trs.size());
+        o_units = push(blob, units.data(), units.size());
+        o_ps = push(blob, pair_start.data(), pair_start.size());
+    }
+    if (blob.empty()) blob.assign(256, 0);
+    void* d = nullptr;
+    s = upload_const(ctx, "tc_batch", blob, st, &d);
+    if (s != XS_OK) return s;
+    char* dc = static_cast<char*>(d);
+    int chunk = kDefaultChunkStages;
+    if (!trs.empty()) {
+        auto it = ctx->tuned_chunk.find(std::make_tuple(trs[trs.size() / 2].n_pad, trs[trs.size() / 2].nx,
+                                                        trs[trs.size() / 2].ny, trs[trs.size() / 2].nz, (int)prec));
+        if (it != ctx->tuned_chunk.end()) chunk = it->second;
+    }
+    const bool bf16 = prec == XS_PREC_SPLIT_BF16;
+    auto enqueue = [&]() -> cudaError_t {
+        cudaError_t err = cudaSuccess;
+        for (size_t e = 0; e < trs.size() && err == cudaSuccess; ++e) {
+            const Job& j = jobs[(size_t)which[e]];
+            const xs_traj& t = traj[which[e]];
+            Mat3 hm;
+            for (int k = 0; k < 9; ++k) hm.a[k] = j.hinv[k];
+            PhaseOpts popt;
+            popt.ortho = is_ortho(j.hinv);
+            const GridDesc& gc = j.half_axis >= 0 ? j.v : j.g;
+            popt.need_z = !(gc.nz == 1 && gc.nz0 == 0);
+            popt.perm_mul = coprime_stride(j.n_pad / kPermRun);
+            err = launch_phase(t.pos, t.f, j.N, j.T, j.n_pad, hm, popt, reinterpret_cast<AtomRec*>(ws + j.rec_off),
+                               ctx->d_err, st);
+        }
+        if (err == cudaSuccess && !trs.empty())
+            err = launch_tc_batch(reinterpret_cast<const TcTraj*>(dc + o_tr), reinterpret_cast<const int4*>(dc + o_units),
+                                  reinterpret_cast<const int*>(dc + o_ps), n_pairs, chunk, bf16,
+                                  reinterpret_cast<double*>(ws + o_scratch), ctx->d_err, ctx->timeout_ns, st);
+        for (size_t e = 0; e < trs.size() && err == cudaSuccess; ++e) {
+            const Job& j = jobs[(size_t)which[e]];
+            if (j.half_axis >= 0)
+                err = launch_friedel(reinterpret_cast<const float*>(ws + j.half_off), nullptr, j.T, j.v, j.g,
+                                     j.half_axis, I_out[which[e]], nullptr, st);
+        }
+        // each trajectory's g2 and XSVS contrast, one after another in the
+        // shared correlation workspace
+        for (int32_t i = 0; req && i < n_traj && err == cudaSuccess; ++i)
+            err = corr_launch(corr[(size_t)i], req[i], I_out[i], dc, ws + o_corr, st);
+        return err;
+    };
+    // the same batch (same tables, inputs, outputs and workspace) replays a
+    // captured graph; anything else is captured once and kept
+    std::string key(blob.begin(), blob.end());
+    for (int32_t i = 0; i < n_traj; ++i) {
+        const void* ptrs[3] = {traj[i].pos, traj[i].f, I_out[i]};
+        key.append(reinterpret_cast<const char*>(ptrs), sizeof(ptrs));
+        key.append(reinterpret_cast<const char*>(traj[i].box.h), sizeof(traj[i].box.h));
+        if (req) {
+            const void* outs[3] = {req[i].g2_out, req[i].mean_out, req[i].beta_out};
+            key.append(reinterpret_cast<const char*>(outs), sizeof(outs));
+        }
+    }
+    key.append(reinterpret_cast<const char*>(&chunk), sizeof(chunk));
+    key.append(reinterpret_cast<const char*>(&ctx->timeout_ns), sizeof(ctx->timeout_ns));
+    key.append(bf16 ? "b" : "h");
+    key.append(req ? "c" : "i");
+    const void* wsp = ctx->ws;
+    key.append(reinterpret_cast<const char*>(&wsp), sizeof(wsp));
+    const cudaError_t launched = traced(ctx, "batched", st, [&]() -> cudaError_t {
+        auto it = ctx->graphs.find(key);
+        if (it == ctx->graphs.end() && st != nullptr) {
+            cudaGraph_t graph = nullptr;
+            const int64_t before = tl_kernel_launches;
+            cudaError_t err = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (err == cudaSuccess) {
+                const cudaError_t le = enqueue();
+                err = cudaStreamEndCapture(st, &graph);
+                if (le != cudaSuccess) err = le;
+            }
+            const int64_t captured = tl_kernel_launches - before;
+            tl_kernel_launches = before;  // counted again at each replay
+            cudaGraphExec_t exec = nullptr;
+            if (err == cudaSuccess) err = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (err != cudaSuccess) {
+                cudaGetLastError();
+                return err;
+            }
+            it = ctx->graphs.emplace(key, xs_context::Graph{exec, captured}).first;
+        }
+        if (it == ctx->graphs.end()) return enqueue();  // legacy default stream: no capture
+        tl_kernel_launches += it->second.kernels;
+        return cudaGraphLaunch(it->second.exec, st);
+    });
+    if (launched != cudaSuccess) return fail(XS_ERR_CUDA, "batched launch: %s", cudaGetErrorString(launched));
+    return XS_OK;
+}
+
+xs_status xs_intensity_batched(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, int32_t n_traj,
+                               xs_precision prec, float* const* I_out, void* cuda_stream) {
+    return batched_impl(ctx, traj, grid, n_traj, prec, I_out, nullptr, static_cast<cudaStream_t>(cuda_stream));
+}
+
+xs_status xs_xpcs_batched(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, int32_t n_traj,
+                          xs_precision prec, float* const* I_out, const xs_corr_request* req, void* cuda_stream) {
+    if (!req) return fail(XS_ERR_INVALID_ARG, "req is required");
+    return batched_impl(ctx, traj, grid, n_traj, prec, I_out, req, static_cast<cudaStream_t>(cuda_stream));
 }
 
 // --------------------------------------------------------------------------

@@ -138,3 +138,7 @@ def test_static_entry_rejects_bad_arguments_before_any_launch(lib):
     st = lib.xs_intensity_fp32_static(ctypes.byref(many), ctypes.byref(g), I.ctypes.data, None, None, None)
     assert st == 1 and "2^31" in lib.xs_last_error().decode()
     assert lib.xs_intensity_fp32_static(None, ctypes.byref(g), I.ctypes.data, None, None, None) == 1
+
+
+def test_batched_pipeline_rejects_missing_requests(lib):
+    assert lib.xs_xpcs_batched(None, None, None, 1, 1, None, None, None) == 1

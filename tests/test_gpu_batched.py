@@ -156,3 +156,110 @@ def test_brownian_gas_batch_g2_follows_diffusion_closed_form(xs):
                 assert abs(est - ref) < 5 * se + 0.03, (N, D, shell, tau, est, ref)
             checked += 1
         assert checked >= 3
+
+
+def test_xpcs_batched_pipeline_in_one_graph(xs):
+    """Intensities, then each trajectory's g2 and XSVS contrast, captured into
+    one graph (Sec. 2.3 Eqs. g2_def, inte_Iq, bq_Iq): equal to the separate
+    calls, to the oracle's g2 and beta of the same intensities, and unchanged
+    on replay."""
+    ctx = xs.Context.get()
+    trajs, grids, host, taus, Ks, R = [], [], [], [], [], []
+    for i, (N, T, grid, L) in enumerate(CASES[:5] + [(2500, 40, wl.centered_plane(64), 30.0)]):
+        pos, f, box = _traj(700 + i, N, T, L, 0.3)
+        trajs.append((torch.from_numpy(pos).cuda(), torch.from_numpy(f).cuda(), box))
+        grids.append(grid)
+        host.append((pos, f, box))
+        taus.append(list(range(min(T, 4))) if T > 1 else [0])
+        Ks.append([k for k in (1, 2, 3, 5) if k <= T])
+        R.append(max(1, wl.rings_for_plane(grid) if grid.nz == 1 else 4))
+    I, g, mean, beta, counts = xs.xpcs_batched(trajs, grids, taus, Ks, R, "bf16")
+    ctx.sync_status()
+    I_sep = xs.intensity_batched(trajs, grids, "bf16")
+    ctx.sync_status()
+    for i, grid in enumerate(grids):
+        assert torch.equal(I[i], I_sep[i]), i
+        T = I[i].shape[0]
+        Iv = I[i].reshape(T, -1)
+        g_ref, m_ref = xs.g2(Iv, taus[i])
+        b_ref, c_ref = xs.xsvs_contrast(I[i], grid, host[i][2], Ks[i], R[i])
+        ctx.sync_status()
+        assert torch.allclose(g[i], g_ref, rtol=1e-12, atol=0, equal_nan=True), i
+        assert torch.allclose(mean[i], m_ref, rtol=1e-12, atol=0), i
+        assert torch.allclose(beta[i], b_ref, rtol=1e-12, atol=0, equal_nan=True), i
+        assert np.array_equal(counts[i], c_ref), i
+        # against the oracle on the kernel's own intensity (stage parity)
+        Ih = Iv.cpu().numpy()
+        go, _ = oracle.g2(Ih, taus[i])
+        assert np.allclose(g[i].cpu().numpy(), go, rtol=2e-6, atol=0, equal_nan=True), i
+        rings = oracle.ring_index(host[i][2], grid.miller(), 1.0, R[i])
+        bo, co = oracle.xsvs_contrast(Ih, Ks[i], rings, R[i])
+        ok = co > 0
+        assert np.array_equal(counts[i], co)
+        assert np.allclose(beta[i].cpu().numpy()[:, ok], bo[:, ok], rtol=1e-9, atol=1e-12), i
+    # the last trajectory's intensity against the oracle as well
+    pos, f, box = host[-1]
+    m = grids[-1].miller()
+    check_I(I[-1].reshape(I[-1].shape[0], -1).cpu().numpy()[[0, -1]], oracle.intensity(pos[[0, -1]], f, box, m),
+            m, "bf16")
+    # replay: same outputs, the whole pipeline counted as the graph's kernels
+    first = [t.clone() for t in g]
+    for t in g:
+        t.fill_(-7.0)
+    n0 = ctx.launch_count()
+    xs.xpcs_batched(trajs, grids, taus, Ks, R, "bf16", outs=I)
+    ctx.sync_status()
+    n1 = ctx.launch_count()
+    # one phase kernel per trajectory, the contraction, and per trajectory
+    # two g2 and at least two XSVS kernels
+    assert n1 - n0 >= len(trajs) + 1 + 4 * len(trajs)
+
+
+def test_xpcs_batched_brownian_gas_g2_closed_form(xs):
+    T = 1000
+    specs = [(3000, 0.3), (2000, 1.0)]
+    trajs, grids, consts = [], [], []
+    for i, (N, D) in enumerate(specs):
+        L = (N / 0.02) ** (1.0 / 3.0)
+        pos, f, box = _traj(900 + i, N, T, L, math.sqrt(2 * D))
+        f[:] = 1.0
+        trajs.append((torch.from_numpy(pos).cuda(), torch.from_numpy(f).cuda(), box))
+        grids.append(wl.centered_plane(64))
+        consts.append((N, D, L))
+    taus = [[1, 2, 3]] * 2
+    _, g, _, beta, _ = xs.xpcs_batched(trajs, grids, taus, [[1, 2, 5]] * 2, [30, 30], "bf16")
+    xs.Context.get().sync_status()
+    for gg, grid, (N, D, L) in zip(g, grids, consts):
+        gg = gg.cpu().numpy()
+        m = grid.miller().astype(np.float64)
+        nn = np.sqrt((m ** 2).sum(axis=1))
+        checked = 0
+        for shell in range(2, 32):
+            sel = np.abs(nn - shell) < 0.5
+            q2 = (2 * math.pi * shell / L) ** 2
+            if sel.sum() < 20 or not (0.5 <= 2 * D * q2 <= 2.0):
+                continue
+            for it, tau in enumerate(taus[0]):
+                est = gg[it, sel].mean() - 1
+                ref = (1 - 1.0 / N) * math.exp(-2 * D * q2 * tau)
+                se = gg[it, sel].std() / math.sqrt(sel.sum())
+                assert abs(est - ref) < 5 * se + 0.03, (N, D, shell, tau, est, ref)
+            checked += 1
+        assert checked >= 3
+
+
+def test_xpcs_batched_fp32_path_and_bad_requests(xs):
+    from paper_2204_13241_gb300._native import XsError
+    pos, f, box = _traj(31, 900, 6, 15.0, 0.2)
+    trajs = [(torch.from_numpy(pos).cuda(), torch.from_numpy(f).cuda(), box)]
+    grid = wl.centered_plane(32)
+    I, g, mean, beta, counts = xs.xpcs_batched(trajs, [grid], [[1, 2]], [[1, 3]], [10], "fp32")
+    xs.Context.get().sync_status()
+    ref = oracle.intensity(pos, f, box, grid.miller())
+    check_I(I[0].reshape(6, -1).cpu().numpy(), ref, grid.miller(), "fp32")
+    go, _ = oracle.g2(I[0].reshape(6, -1).cpu().numpy(), [1, 2])
+    assert np.allclose(g[0].cpu().numpy(), go, rtol=2e-6)
+    with pytest.raises(XsError):
+        xs.xpcs_batched(trajs, [grid], [[6]], [[1]], [10], "bf16")     # delay >= T
+    with pytest.raises(XsError):
+        xs.xpcs_batched(trajs, [grid], [[1]], [[7]], [10], "bf16")     # window longer than the series
