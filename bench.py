@@ -530,6 +530,21 @@ def run_ours(args):
         e1.synchronize()
         ctx.sync_status()
         b_ms = e0.elapsed_time(e1) / 2
+        # the autotuner: tile kind x chunk length per shape bucket, then the
+        # same call again with every trajectory on its bucket's choice
+        t_tune = time.perf_counter()
+        xs.tune_batched(trajs, grids, "bf16")
+        t_tune = time.perf_counter() - t_tune
+        choices = [xs.tuned_choice(prm["n_atoms"], g, "bf16") for prm, g in zip(params, grids)]
+        xs.intensity_batched(trajs, grids, "bf16", outs)     # captures the tuned graph
+        ctx.sync_status()
+        e0.record(stream)
+        for _ in range(2):
+            xs.intensity_batched(trajs, grids, "bf16", outs)
+        e1.record(stream)
+        e1.synchronize()
+        ctx.sync_status()
+        bt_ms = e0.elapsed_time(e1) / 2
         # the whole pipeline: each trajectory's g2 on 64 log-spaced delays and
         # XSVS contrast on 1-2-5 windows over unit rings, in the same graph
         taus_b = [[int(t) for t in wl.log_delays(prm["n_frames"], 64)] for prm in params]
@@ -547,6 +562,12 @@ def run_ours(args):
         line["batched"] = {"workload": "64 ideal-gas trajectories, N log-uniform 2e3-5e5, T 100-2000, "
                                        "planes 64^2-256^2, split BF16, one persistent launch per call",
                            "units": b_units, "ms_per_call": b_ms, "value": b_units / (b_ms * 1e-3), "unit": METRIC,
+                           "tiles": "default rule: 128 x 64 tiles where n_y <= 64, else 128 x 128",
+                           "tuned": {"ms_per_call": bt_ms, "value": b_units / (bt_ms * 1e-3), "unit": METRIC,
+                                     "tuning_s": t_tune,
+                                     "tile_kinds": {"128x128": sum(1 for c in choices if c[0] == 0),
+                                                    "128x64": sum(1 for c in choices if c[0] == 1)},
+                                     "chunks": {str(k): sum(1 for c in choices if c[1] == k) for k in (16, 32, 64)}},
                            "pipeline": {"what": "intensity, then per trajectory g2 (64 log delays) and XSVS "
                                                 "(1-2-5 windows, unit rings), one captured graph per call",
                                         "ms_per_call": p_ms, "value": b_units / (p_ms * 1e-3), "unit": METRIC,

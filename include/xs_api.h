@@ -381,11 +381,27 @@ XS_API xs_status xs_intensity_backward(xs_context* ctx, const xs_traj* traj, con
                                 const float* amp, const float* dL_dI, float* dL_dr_out,
                                 void* cuda_stream);
 
-/* Times the tensor-core tile choices for this trajectory shape and grid and
- * keeps the fastest in the context (later calls of the same shape use it).
- * Synchronizes the stream. */
+/* Autotuner of the tensor-core path (no counterpart in the paper: Algorithm 1
+ * does not depend on how the q grid is tiled).  Times, on up to 64 frames of
+ * `traj` (device positions) on `grid`, every tile kind -- 128 n_x x 128 n_y
+ * (tile_kind 0) and 128 n_x x 64 n_y (tile_kind 1; not for grids contracted
+ * as a half, which are planned on 128 x 128 tiles) -- with FP32 accumulation
+ * chunks of 16, 32 and 64 stages of 64 atoms, and keeps the fastest pair in
+ * the context under the trajectory's shape bucket: atom count rounded down to
+ * a power of two (after padding to a multiple of 64), grid extents and
+ * precision.  Later xs_intensity calls, and every trajectory of later
+ * batched calls, whose bucket matches use it; untuned shapes take tile kind 1
+ * when the grid's n_y extent is at most 64 (the same number of tiles), else
+ * tile kind 0, with 64-stage chunks.  Synchronizes the stream. */
 XS_API xs_status xs_tune(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, xs_precision prec,
                   void* cuda_stream);
+
+/* The tile kind (0: 128 x 128, 1: 128 x 64) and chunk length (stages of 64
+ * atoms) that the split precisions use for n_atoms atoms on `grid`: the
+ * tuned choice of the shape bucket (see xs_tune), else the default rule.
+ * Host only; launches nothing. */
+XS_API xs_status xs_tuned_choice(xs_context* ctx, int64_t n_atoms, const xs_qgrid* grid, xs_precision prec,
+                                 int32_t* tile_kind, int32_t* chunk_stages);
 
 /* Message for the last non-OK status returned on the calling thread. */
 XS_API const char* xs_last_error(void);

@@ -21,7 +21,7 @@ EXPORTS = ["xs_context_create", "xs_context_destroy", "xs_intensity", "xs_intens
            "xs_sync_status", "xs_set_wait_timeout_ns", "xs_version", "xs_profile_enable", "xs_profile_read",
            "xs_launch_count", "xs_intensity_fp32_static", "xs_isf", "xs_contrast_from_isf", "xs_intensity_species",
            "xs_intensity_points", "xs_ewald_points", "xs_intensity_fft", "xs_xsvs_partial", "xs_xsvs_finalize",
-           "xs_xpcs_batched"]
+           "xs_xpcs_batched", "xs_tuned_choice"]
 
 
 class XsError(RuntimeError):
@@ -88,6 +88,7 @@ def load() -> ctypes.CDLL:
         "xs_ring_index": ([ctypes.POINTER(QGrid), ctypes.POINTER(Box), D, I32, P], st),
         "xs_intensity_backward": ([P, ctypes.POINTER(Traj), ctypes.POINTER(QGrid), P, P, P, P], st),
         "xs_tune": ([P, ctypes.POINTER(Traj), ctypes.POINTER(QGrid), st, P], st),
+        "xs_tuned_choice": ([P, I64, ctypes.POINTER(QGrid), st, ctypes.POINTER(I32), ctypes.POINTER(I32)], st),
         "xs_last_error": ([], ctypes.c_char_p),
         "xs_sync_status": ([P, P], st),
         "xs_set_wait_timeout_ns": ([P, I64], st),

@@ -297,6 +297,37 @@ def tune(pos: torch.Tensor, f: torch.Tensor, box, grid, precision: str = "fp16")
     nat.check(ctx.lib.xs_tune(ctx.handle, ctypes.byref(tr), ctypes.byref(g), nat.PRECISIONS[precision], _stream()))
 
 
+def tuned_choice(n_atoms: int, grid, precision: str = "fp16") -> tuple[int, int]:
+    """(tile kind, chunk stages) the split path uses for this shape: 0 is the
+    128 x 128 tile, 1 the 128 x 64 tile (see xs_tune)."""
+    g = _grid(grid)
+    k, c = ctypes.c_int32(), ctypes.c_int32()
+    ctx = Context.get()
+    nat.check(ctx.lib.xs_tuned_choice(ctx.handle, int(n_atoms), ctypes.byref(g), nat.PRECISIONS[precision],
+                                      ctypes.byref(k), ctypes.byref(c)))
+    return int(k.value), int(c.value)
+
+
+def tune_batched(trajs: Sequence[tuple], grids: Sequence, precision: str = "bf16") -> None:
+    """Runs the tuner once per distinct shape bucket of a batch (atoms by
+    powers of two after padding, grid), so that every trajectory of later
+    batched calls uses its bucket's tile kind and chunk length."""
+    seen = set()
+    for (pos, f, box), grid in zip(trajs, grids):
+        n = int(pos.shape[1])
+        npad = max(64, (n + 63) // 64 * 64)
+        key = (npad.bit_length() - 1, tuple(_grid_tuple(grid)))
+        if key in seen:
+            continue
+        seen.add(key)
+        tune(pos, f, box, grid, precision)
+
+
+def _grid_tuple(grid):
+    g = _grid(grid)
+    return (g.nx0, g.nx, g.ny0, g.ny, g.nz0, g.nz)
+
+
 def g2(I: torch.Tensor, taus: Sequence[int], want_mean: bool = True):
     """g2(q,tau) per pixel (Sec. 2.3 Eq. g2_def) of I [T][...]; returns
     (g2 float64 [n_tau][P], mean float64 [P])."""

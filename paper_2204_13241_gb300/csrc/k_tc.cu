@@ -19,11 +19,11 @@
 // its A rows against all 256 B columns.
 //   * 8 producer warps per CTA write the tables straight into shared memory in
 //     the MN-major, 128-byte-swizzled layout the tensor core reads.  Each
-//     thread owns one atom and a run of 32 consecutive n, held as pairs
-//     (n, n+1) in packed FP32x2 registers: the run starts from seeds
-//     exp(i 2 pi n0 U) and exp(i 2 pi (n0+1) U) of exact turn counts (U =
-//     32-bit turn count, n U mod 2^32 is exact), evaluated in registers
-//     (cis_turns), and advances by the step exp(i 2 pi 2U).  Each value
+//     thread owns one atom and a run of consecutive n (32 or 16), held as
+//     pairs (n, n+1) in packed FP32x2 registers: the run starts from the
+//     seed exp(i 2 pi n0 U) of an exact turn count (U = 32-bit turn count,
+//     n U mod 2^32 is exact) and z = exp(i 2 pi U), takes exp(i 2 pi (n0+1) U)
+//     = seed z, and advances by the step z^2.  Each value
 //     c is split into hi = RN(c) and lo = RN(c - hi) (FP16 or BF16).
 //   * Producer warps arrive on a barrier of their own CTA (CTA-scope
 //     release); in CTA 1 one relay thread forwards each filled stage to CTA 0
@@ -62,35 +62,64 @@ namespace xs {
 
 namespace {
 
-constexpr int kBN = 256;   // MMA N (and M of the pair): 128 complex n as Re/Im rows
-constexpr int kBK = 64;    // atoms per stage
-constexpr int kStages = 3;
-constexpr int kTile = 128;  // n_x and n_y per pair tile
-constexpr int kHalf = 64;   // n per CTA and axis
-constexpr int kRun = 32;    // consecutive n per producer thread and stage
+constexpr int kBK = 64;     // atoms per stage
+constexpr int kTile = 128;  // n_x per pair tile (M of the pair: Re/Im rows of 128 n_x)
+constexpr int kHalf = 64;   // n_x per CTA
 constexpr int kEpiWarps = 4;
 constexpr int kMmaWarp = 4;
-constexpr int kProdWarps = 8;
-constexpr int kThreads = (kEpiWarps + 1 + kProdWarps) * 32;
+constexpr int kMaxStages = 4;
 // MN-major SW128 tiles: blocks of 64 MN elements (128-byte rows), 8 K rows per
 // 1024-byte swizzle atom; a stage holds kBK / 8 = 8 K atoms per MN block.
 constexpr uint32_t kMNBlockBytes = (kBK / 8) * 1024;  // 8 KB: leading byte offset
-constexpr uint32_t kHalfBytes = 2 * kMNBlockBytes;     // 128 rows of one operand half
-constexpr uint32_t kStageBytes = 4 * kHalfBytes;       // A hi, A lo, B hi, B lo: 64 KB
-constexpr uint32_t kTmemCols = 512;                    // two 256-column FP32 accumulators
+constexpr uint32_t kAHalfBytes = 2 * kMNBlockBytes;    // 128 A rows of one operand half
+
+// The two tile kinds.  Per CTA the A side is always the Re/Im rows of 64 n_x
+// and the B side the Re/Im rows of kTileY / 2 n_y; each producer thread owns
+// one atom and a run of kRun consecutive n of one side.
+template <int KIND>
+struct Cfg;
+template <>
+struct Cfg<kTcTile128> {
+    static constexpr int kTileY = 128;  // n_y per pair tile
+    static constexpr int kBN = 256;     // MMA N: Re/Im columns of kTileY n_y
+    static constexpr int kRun = 32;
+    static constexpr int kStages = 3;
+    static constexpr uint32_t kTmemCols = 512;  // two 256-column FP32 accumulators
+};
+template <>
+struct Cfg<kTcTile64> {
+    static constexpr int kTileY = 64;
+    static constexpr int kBN = 128;
+    static constexpr int kRun = 16;
+    static constexpr int kStages = 4;
+    static constexpr uint32_t kTmemCols = 256;  // two 128-column FP32 accumulators
+};
 
 struct SmemCtl {
-    uint64_t full[kStages];   // CTA 0: its producer warps and the peer's relay
-    uint64_t fill[kStages];   // CTA 1: its producer warps (forwarded by the relay)
-    uint64_t empty[kStages];  // each CTA: MMA commits
+    uint64_t full[kMaxStages];   // CTA 0: its producer warps and the peer's relay
+    uint64_t fill[kMaxStages];   // CTA 1: its producer warps (forwarded by the relay)
+    uint64_t empty[kMaxStages];  // each CTA: MMA commits
     uint64_t acc_full[2];     // each CTA: MMA commits
     uint64_t acc_empty[2];    // CTA 0: epilogue warps of both CTAs
     uint64_t drain;
     uint32_t tmem_base;
     int abort;
+    float2 tab[256];          // exp(i 2 pi k / 256)
 };
 
-constexpr size_t kSmemBytes = 1024 + kStages * kStageBytes + sizeof(SmemCtl);
+template <int KIND>
+struct Lay {
+    using C = Cfg<KIND>;
+    static constexpr int kARuns = kHalf / C::kRun;              // runs over the CTA's n_x
+    static constexpr int kBRuns = (C::kTileY / 2) / C::kRun;    // runs over the CTA's n_y
+    static constexpr int kProdWarps = 2 * (kARuns + kBRuns);    // two warps (32 atoms each) per run
+    static constexpr int kThreads = (kEpiWarps + 1 + kProdWarps) * 32;
+    static constexpr uint32_t kBHalfBytes = (uint32_t)(C::kTileY / 64) * kMNBlockBytes;
+    static constexpr uint32_t kStageBytes = 2 * kAHalfBytes + 2 * kBHalfBytes;  // A hi, A lo, B hi, B lo
+    static constexpr size_t kSmemBytes = 1024 + (size_t)C::kStages * kStageBytes + sizeof(SmemCtl);
+    static_assert(C::kStages <= kMaxStages, "stage barriers");
+    static_assert(kProdWarps * 32 + (kEpiWarps + 1) * 32 <= 1024, "block size");
+};
 
 struct TcArgs {
     TcTraj single;          // the trajectory when `units` is null
@@ -271,17 +300,20 @@ __device__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_fla
 
 // ---- table construction ------------------------------------------------------
 
-// exp(i 2 pi P / 2^32) for a 32-bit turn count, in registers: sincospif of the
-// top 24 bits ((P >> 8) 2^-23 in [0, 2) is exact in FP32), rotated by the
-// remaining angle t = (P & 255) 2 pi / 2^32 < 3.8e-7 rad, for which cos t = 1
-// and sin t = t hold to FP32 precision (the neglected terms are below 1e-13).
-// No shared-memory table: the producers' random table loads had taken 12% of
-// the shared-memory data stage, which the tensor core's operand reads share.
-__device__ __forceinline__ float2 cis_turns(uint32_t P) {
-    float s, c;
-    sincospif((float)(P >> 8) * 1.1920928955078125e-7f, &s, &c);  // 2^-23
-    const float t = (float)(P & 0xFFu) * 1.4629180792671596e-9f;  // 2 pi / 2^32
-    return make_float2(fmaf(-s, t, c), fmaf(c, t, s));
+// exp(i 2 pi P / 2^32) for a 32-bit turn count: the top 8 bits pick
+// exp(i 2 pi k / 256) from a table in shared memory, the remaining angle
+// t < 2 pi / 256 uses the Taylor polynomials cos t = 1 - t^2/2 + t^4/24 and
+// sin t = t - t^3/6 + t^5/120 (truncation below 3e-13), and the two factors
+// are multiplied: about 15 instructions.  Evaluating the seeds in registers
+// with sincospif of the top 24 bits instead took about twice the
+// instructions and made the producer-bound tiles 2-5% slower.
+__device__ __forceinline__ float2 cis_turns(uint32_t P, const float2* tab) {
+    const float2 a = tab[P >> 24];
+    const float t = (float)(P & 0xFFFFFFu) * 1.4629180792671596e-9f;  // 2 pi / 2^32
+    const float t2 = t * t;
+    const float c = fmaf(t2, fmaf(t2, 1.0f / 24.0f, -0.5f), 1.0f);
+    const float s = t * fmaf(t2, fmaf(t2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
+    return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
 }
 
 // v = (v0, v1) -> packed hi = (RN(v0), RN(v1)) and lo = (RN(v0 - hi0), RN(v1 - hi1));
@@ -342,6 +374,8 @@ struct Unit {
     int s0, s1;    // stage range of this piece of the unit
     int split;     // split unit index, or -1 for a whole unit
     int part;
+    int chunk;     // stages per accumulation chunk (0: the launch's)
+    int tile_y;    // n_y per tile
 };
 
 __device__ __forceinline__ Unit make_unit(const TcTraj& tr, int t, int iz, int tx, int ty) {
@@ -359,11 +393,14 @@ __device__ __forceinline__ Unit make_unit(const TcTraj& tr, int t, int iz, int t
     u.iz = iz;
     u.tx = tx;
     u.ty = ty;
-    u.centred = tr.nx0 + tx * kTile == -kHalf && tr.ny0 + ty * kTile == -kHalf && tr.nz0 + iz == 0;
+    u.tile_y = tc_tile_y(tr.kind);
+    u.centred = tr.kind == kTcTile128 && tr.nx0 + tx * kTile == -kHalf && tr.ny0 + ty * u.tile_y == -kHalf &&
+                tr.nz0 + iz == 0;
     u.s0 = 0;
     u.s1 = tr.n_stages;
     u.split = -1;
     u.part = 0;
+    u.chunk = tr.chunk;
     return u;
 }
 
@@ -415,7 +452,8 @@ __global__ void split_finish_kernel(TcArgs a, int64_t n_pairs) {
     if (pix >= kTile * kTile) return;
     const int xi = pix / kTile, yi = pix - xi * kTile;
     const Unit up = single_unit(a.single, a.full * n_pairs + r);
-    const int ix = up.tx * kTile + xi, iy = up.ty * kTile + yi;
+    if (yi >= up.tile_y) return;
+    const int ix = up.tx * kTile + xi, iy = up.ty * up.tile_y + yi;
     if (ix >= up.nx || iy >= up.ny) return;
     const double2* base = a.partial + (size_t)r * a.parts * (kTile * kTile) + pix;
     double re = 0.0, im = 0.0;
@@ -432,8 +470,15 @@ __global__ void split_finish_kernel(TcArgs a, int64_t n_pairs) {
     }
 }
 
-template <bool BF16>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kernel(TcArgs args) {
+template <bool BF16, int KIND>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads, 1) tc_kernel(TcArgs args) {
+    using C = Cfg<KIND>;
+    using L = Lay<KIND>;
+    constexpr int kStages = C::kStages;
+    constexpr uint32_t kStageBytes = L::kStageBytes;
+    constexpr int kProdWarps = L::kProdWarps;
+    constexpr int kRun = C::kRun;
+    constexpr int kBN = C::kBN;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
@@ -447,6 +492,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
     const uint32_t rank = cluster_rank();  // 0: issues the MMAs of the pair
     const int64_t pair = blockIdx.x >> 1, n_pairs = gridDim.x >> 1;
 
+    for (int i = threadIdx.x; i < 256; i += L::kThreads) {
+        double sn, cs;
+        sincospi((double)i / 128, &sn, &cs);
+        ctl->tab[i] = make_float2((float)cs, (float)sn);
+    }
     if (threadIdx.x == kMmaWarp * 32) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&ctl->full[s], kProdWarps + 1);
@@ -461,7 +511,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
         ctl->abort = 0;
         fence_barrier_init();
     }
-    if (warp == 0) tmem_alloc_pair(&ctl->tmem_base, kTmemCols);
+    if (warp == 0) tmem_alloc_pair(&ctl->tmem_base, C::kTmemCols);
     tc_fence_before();
     cluster_sync();  // barriers of both CTAs initialised, tensor memory allocated
     tc_fence_after();
@@ -471,15 +521,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
 
     if (warp >= kMmaWarp + 1) {
         // ------------------------------------------------------------ producers
-        // warp w: atoms [32 (w & 1), +32) of the stage; w >> 1 = 0, 1: A rows
-        // (n_x), 2, 3: B rows (n_y)
+        // warp w: atoms [32 (w & 1), +32) of the stage; run ri = w >> 1: the
+        // first kARuns runs cover the CTA's 64 n_x (A rows), the others its
+        // kTileY / 2 n_y (B rows)
         const int w = warp - (kMmaWarp + 1);
         const int ri = w >> 1;
-        const bool is_a = ri < 2;
-        // general tiles: a run of 32 consecutive n of this CTA's half;
-        // centred tiles: base values X(32 rank + s), s in [s0, s0 + 16)
-        const int run0 = kRun * (ri & 1);
-        const int s0 = (kRun / 2) * (ri & 1);
+        const bool is_a = ri < L::kARuns;
+        // general tiles: a run of kRun consecutive n of this CTA's half;
+        // centred tiles (128 x 128 only): base values X(32 rank + s), s in
+        // [s0, s0 + 16)
+        const int run0 = kRun * (is_a ? ri : ri - L::kARuns);
+        const int s0 = 16 * (ri & 1);
         const int k = 32 * (w & 1) + lane;
         int slot = 0;
         uint32_t phase = 0;  // parity of the current pass over the ring of stages
@@ -494,12 +546,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
             if (has_next) up_next = get_unit(args, pair, n_pairs, ku + 1);
             const int st1 = up.s1;
             const uint4* rec_cur = up.rec + k;
-            const bool centred = up.centred;
+            const bool centred = KIND == kTcTile128 && up.centred;
             const bool extra = centred && (ri & 1) == 0;  // also builds X(32 rank + 32)
             const uint32_t n0 =
                 centred ? (uint32_t)(32 * (int)rank + s0)
                         : (is_a ? (uint32_t)(up.nx0 + up.tx * kTile + kHalf * (int)rank + run0)
-                                : (uint32_t)(up.ny0 + up.ty * kTile + kHalf * (int)rank + run0));
+                                : (uint32_t)(up.ny0 + up.ty * C::kTileY + (C::kTileY / 2) * (int)rank + run0));
             const uint32_t nz = (uint32_t)(up.nz0 + up.iz);
             for (int s = up.s0; s < st1; ++s) {
                 const uint4 r = r_next;
@@ -507,20 +559,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                     r_next = __ldg(rec_cur + (int64_t)(s + 1) * kBK);
                 else if (has_next)
                     r_next = __ldg(up_next.rec + (int64_t)up_next.s0 * kBK + k);
-                // exact step z^2 and seeds E(n0), E(n0 + 1) of this thread's run
+                // seed E(n0) and z = E(1) of this thread's run, E(n0 + 1) = E(n0) z
+                // and the step z^2 (two table evaluations instead of three
+                // made producer-bound tiles 2-7% faster, at the same error)
                 const uint32_t U = is_a ? r.x : r.y;
-                const float2 z2 = cis_turns(2u * U);
+                const float2 z1 = cis_turns(U, ctl->tab);
+                float2 E0 = cis_turns(n0 * U, ctl->tab);
+                float2 E1 = cmul(E0, z1);
+                const float2 z2 = cmul(z1, z1);
                 const float2 ZR = make_float2(z2.x, z2.x), ZI = make_float2(z2.y, z2.y);
                 const float2 NZI = make_float2(-z2.y, -z2.y);
-                float2 E0 = cis_turns(n0 * U);
-                float2 E1 = cis_turns((n0 + 1u) * U);
                 float2 Ex = make_float2(0.0f, 0.0f);
-                if (extra) Ex = cis_turns((uint32_t)(32 * (int)rank + 32) * U);
+                if (extra) Ex = cis_turns((uint32_t)(32 * (int)rank + 32) * U, ctl->tab);
                 if (!is_a) {
                     const float f = __uint_as_float(r.w);
                     float2 wv = make_float2(f, 0.0f);
                     if (nz != 0u) {
-                        const float2 ez = cis_turns(nz * r.z);
+                        const float2 ez = cis_turns(nz * r.z, ctl->tab);
                         wv = make_float2(f * ez.x, f * ez.y);
                     }
                     E0 = cmul(E0, wv);
@@ -534,13 +589,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                     break;
                 }
                 const uint32_t sb = stage_base + (uint32_t)slot * kStageBytes;
-                const uint32_t hi_base = is_a ? sb : sb + 2 * kHalfBytes;
-                const uint32_t lo_base = hi_base + kHalfBytes;
-                if (centred) {
+                const uint32_t hi_base = is_a ? sb : sb + 2 * kAHalfBytes;
+                const uint32_t lo_base = hi_base + (is_a ? kAHalfBytes : L::kBHalfBytes);
+                if (KIND == kTcTile128 && centred) {
                     uint32_t xh = 0u, xl = 0u;  // X(32 rank + 32) as packed (Re, Im)
                     if (extra) split2<BF16>(Ex, xh, xl);
 #pragma unroll
-                    for (int g = 0; g < kRun / 8; ++g) {
+                    for (int g = 0; g < 4; ++g) {  // 16 base values
                         uint32_t h[4], l[4];
 #pragma unroll
                         for (int q = 0; q < 2; ++q) {
@@ -601,6 +656,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
         // ------------------------------------------------------------ MMA issue
         if (rank == 0 && lane == 0) {
             constexpr uint32_t idesc = make_idesc(BF16, 2 * 128, kBN);
+            static_assert(kBN % 16 == 0 && kBN >= 16 && kBN <= 256, "MMA N for M = 256");
             int64_t a_cnt = 0;
             int slot = 0;
             uint32_t phase = 0;
@@ -608,7 +664,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
             for (int64_t ku = 0; ku < my_units && ok; ++ku) {
                 const Unit uu = get_unit(args, pair, n_pairs, ku);
                 const int n_stages = uu.s1 - uu.s0;
-                const int n_chunks = (n_stages + args.chunk_stages - 1) / args.chunk_stages;
+                const int cs = uu.chunk > 0 ? uu.chunk : args.chunk_stages;
+                const int n_chunks = (n_stages + cs - 1) / cs;
                 for (int c = 0; c < n_chunks && ok; ++c, ++a_cnt) {
                     const int b = (int)(a_cnt & 1);
                     const uint32_t use = (uint32_t)(a_cnt >> 1);
@@ -618,9 +675,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t d_tmem = tmem + (uint32_t)b * 256u;
-                    const int s0 = c * args.chunk_stages;
-                    const int s1 = min(n_stages, s0 + args.chunk_stages);
+                    const uint32_t d_tmem = tmem + (uint32_t)b * (uint32_t)kBN;
+                    const int s0 = c * cs;
+                    const int s1 = min(n_stages, s0 + cs);
                     for (int s = s0; s < s1; ++s) {
                         if (!wait_bar(&ctl->full[slot], phase, abort_flag, args.err, args.timeout_ns, 20000u)) {
                             ok = false;
@@ -628,9 +685,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                         }
                         tc_fence_after();
                         const uint32_t a_hi = stage_base + (uint32_t)slot * kStageBytes;
-                        const uint32_t a_lo = a_hi + kHalfBytes;
-                        const uint32_t b_hi = a_hi + 2 * kHalfBytes;
-                        const uint32_t b_lo = b_hi + kHalfBytes;
+                        const uint32_t a_lo = a_hi + kAHalfBytes;
+                        const uint32_t b_hi = a_hi + 2 * kAHalfBytes;
+                        const uint32_t b_lo = b_hi + L::kBHalfBytes;
 #pragma unroll
                         for (int kk = 0; kk < kBK / 16; ++kk) {
                             const uint32_t ko = (uint32_t)kk * 2048u;  // two 8-row K atoms per K = 16
@@ -692,8 +749,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
         bool ok = true;
         for (int64_t ku = 0; ku < my_units && ok; ++ku) {
             const Unit up = get_unit(args, pair, n_pairs, ku);
-            const int n_chunks = (up.s1 - up.s0 + args.chunk_stages - 1) / args.chunk_stages;
-            const bool centred = up.centred;
+            const int cs = up.chunk > 0 ? up.chunk : args.chunk_stages;
+            const int n_chunks = (up.s1 - up.s0 + cs - 1) / cs;
+            const bool centred = KIND == kTcTile128 && up.centred;
             const int xi = centred ? xi_c : kHalf * (int)rank + x_slot;
             const double sx = centred ? (double)sx_c : 1.0;  // sign of the stored Im x rows
             for (int c = 0; c < n_chunks; ++c, ++a_cnt) {
@@ -708,7 +766,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dcol = lane_base + (uint32_t)b * 256u;
+                const uint32_t dcol = lane_base + (uint32_t)b * (uint32_t)kBN;
                 const bool first = c == 0, last = c == n_chunks - 1;
 #pragma unroll 1
                 for (int j = 0; j < kBN / 16; ++j) {
@@ -742,7 +800,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] = (double)hi[i] + (double)lo[i];
                     // columns 16j .. 16j+15 hold n_y local m = 8j .. 8j+7 in groups of 4
-                    // (Re m, Re m+1, Im m, Im m+1); the Re lane finishes m = 8j..8j+3 with
+                    // (Re m, Re m+1, Im m, Im m+1): CTA r's B rows are columns
+                    // [r kBN / 2, (r + 1) kBN / 2), n_y [r kTileY / 2, ...), so
+                    // m = 8j for both tile kinds; the Re lane finishes m = 8j..8j+3 with
                     // the Im values of its partner lane (lane ^ 2), the Im lane m = 8j+4..8j+7
                     double own[8], rcv[8];
 #pragma unroll
@@ -776,7 +836,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
                                 }
                                 const double sre = p_rr - sx * sy * p_ii;
                                 const double sim = sy * p_ri + sx * p_ir;
-                                const int iy = up.ty * kTile + yi;
+                                const int iy = up.ty * C::kTileY + yi;
                                 if (part_dst) {
                                     part_dst[yi] = make_double2(sre, sim);
                                 } else if (iy < up.ny) {
@@ -802,7 +862,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) tc_kern
     tc_fence_before();
     cluster_sync();  // no CTA leaves while the pair's MMAs or its peer may still touch it
     tc_fence_after();
-    if (warp == 0) tmem_dealloc_pair(tmem, kTmemCols);
+    if (warp == 0) tmem_dealloc_pair(tmem, C::kTmemCols);
 }
 
 }  // namespace
@@ -811,18 +871,20 @@ bool tc_supported(const GridDesc& g) { return g.nx >= 1 && g.ny >= 1 && g.nz >= 
 
 int64_t tc_atom_multiple() { return kBK; }
 
-int tc_pair_capacity(int num_sms) {
+template <int KIND>
+static int pair_capacity_of(int num_sms) {
     // pairs that can be resident at once (a cluster needs two SMs of one GPC)
     static int max_pairs = -1;
     if (max_pairs < 0) {
-        cudaFuncSetAttribute((const void*)tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBytes);
-        cudaFuncSetAttribute((const void*)tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBytes);
+        using L = Lay<KIND>;
+        cudaFuncSetAttribute((const void*)tc_kernel<false, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)L::kSmemBytes);
+        cudaFuncSetAttribute((const void*)tc_kernel<true, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)L::kSmemBytes);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(2 * (unsigned)std::max(1, num_sms / 2), 1, 1);
-        cfg.blockDim = dim3(kThreads, 1, 1);
-        cfg.dynamicSmemBytes = kSmemBytes;
+        cfg.blockDim = dim3(L::kThreads, 1, 1);
+        cfg.dynamicSmemBytes = L::kSmemBytes;
         cudaLaunchAttribute attr;
         attr.id = cudaLaunchAttributeClusterDimension;
         attr.val.clusterDim.x = 2;
@@ -831,7 +893,7 @@ int tc_pair_capacity(int num_sms) {
         cfg.attrs = &attr;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, (const void*)tc_kernel<false>, &cfg) != cudaSuccess || n < 1) {
+        if (cudaOccupancyMaxActiveClusters(&n, (const void*)tc_kernel<false, KIND>, &cfg) != cudaSuccess || n < 1) {
             cudaGetLastError();
             n = std::max(1, num_sms / 2);
         }
@@ -840,15 +902,24 @@ int tc_pair_capacity(int num_sms) {
     return max_pairs;
 }
 
-TcTraj tc_traj(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g, float* I, float* amp) {
+int tc_pair_capacity(int num_sms, int kind) {
+    return kind == kTcTile64 ? pair_capacity_of<kTcTile64>(num_sms) : pair_capacity_of<kTcTile128>(num_sms);
+}
+
+int tc_default_kind(const GridDesc& g) { return g.ny <= 64 ? kTcTile64 : kTcTile128; }
+
+TcTraj tc_traj(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g, float* I, float* amp, int kind,
+               int chunk) {
     TcTraj t;
+    t.kind = kind == kTcTile64 ? kTcTile64 : kTcTile128;
+    t.chunk = chunk;
     t.rec = reinterpret_cast<const uint4*>(rec);
     t.I = I;
     t.amp = amp;
     t.n_pad = n_pad;
     t.n_stages = (int)(n_pad / kBK);
     t.tiles_x = (g.nx + kTile - 1) / kTile;
-    t.tiles_y = (g.ny + kTile - 1) / kTile;
+    t.tiles_y = (g.ny + tc_tile_y(t.kind) - 1) / tc_tile_y(t.kind);
     t.nx0 = g.nx0;
     t.nx = g.nx;
     t.ny0 = g.ny0;
@@ -907,16 +978,21 @@ void tc_deal_units(const std::vector<TcTraj>& trajs, const std::vector<int4>& al
     pair_start[n_pairs] = (int)units.size();
 }
 
-static cudaError_t launch(const TcArgs& a, int n_pairs, bool bf16, cudaStream_t st) {
-    const void* fn = bf16 ? (const void*)tc_kernel<true> : (const void*)tc_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+template <bool BF16, int KIND>
+static cudaError_t launch_kind(const TcArgs& a, int n_pairs, cudaStream_t st) {
+    using L = Lay<KIND>;
+    const void* fn = (const void*)tc_kernel<BF16, KIND>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kSmemBytes);
     if (e != cudaSuccess) return e;
     ++tl_kernel_launches;
-    if (bf16)
-        tc_kernel<true><<<2 * n_pairs, kThreads, kSmemBytes, st>>>(a);
-    else
-        tc_kernel<false><<<2 * n_pairs, kThreads, kSmemBytes, st>>>(a);
+    tc_kernel<BF16, KIND><<<2 * n_pairs, L::kThreads, L::kSmemBytes, st>>>(a);
     return cudaGetLastError();
+}
+
+static cudaError_t launch(const TcArgs& a, int n_pairs, bool bf16, int kind, cudaStream_t st) {
+    if (kind == kTcTile64)
+        return bf16 ? launch_kind<true, kTcTile64>(a, n_pairs, st) : launch_kind<false, kTcTile64>(a, n_pairs, st);
+    return bf16 ? launch_kind<true, kTcTile128>(a, n_pairs, st) : launch_kind<false, kTcTile128>(a, n_pairs, st);
 }
 
 TcSplit tc_split_plan(int64_t units, int n_pairs, int n_stages, int chunk_stages) {
@@ -976,7 +1052,7 @@ cudaError_t launch_tc_single(const TcTraj& tr, int n_pairs, const TcSplit& sp, i
     }
     const int64_t pieces = sp.full * n_pairs + sp.rem * sp.parts;
     n_pairs = (int)std::min<int64_t>(n_pairs, pieces);
-    return launch(a, n_pairs, bf16, st);
+    return launch(a, n_pairs, bf16, tr.kind, st);
 }
 
 cudaError_t launch_tc_split_finish(const TcTraj& tr, int n_pairs, const TcSplit& sp, void* split_buf,
@@ -997,7 +1073,7 @@ cudaError_t launch_tc_split_finish(const TcTraj& tr, int n_pairs, const TcSplit&
 }
 
 cudaError_t launch_tc_batch(const TcTraj* d_trajs, const int4* d_units, const int* d_pair_start, int n_pairs,
-                            int chunk_stages, bool bf16, double* scratch, int* err, int64_t timeout_ns,
+                            int chunk_stages, bool bf16, int kind, double* scratch, int* err, int64_t timeout_ns,
                             cudaStream_t st) {
     TcArgs a{};
     a.trajs = d_trajs;
@@ -1007,7 +1083,7 @@ cudaError_t launch_tc_batch(const TcTraj* d_trajs, const int4* d_units, const in
     a.scratch = scratch;
     a.err = err;
     a.timeout_ns = timeout_ns;
-    return launch(a, n_pairs, bf16, st);
+    return launch(a, n_pairs, bf16, kind, st);
 }
 
 }  // namespace xs

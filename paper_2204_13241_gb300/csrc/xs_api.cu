@@ -86,6 +86,15 @@ bool is_ortho(const double* hinv) {
     return hinv[1] == 0.0 && hinv[2] == 0.0 && hinv[3] == 0.0 && hinv[5] == 0.0 && hinv[6] == 0.0 && hinv[7] == 0.0;
 }
 
+// shape bucket of the tuner's cache: atoms by powers of two (the choice of
+// tile kind and chunk length hardly depends on the exact count), the
+// contracted grid's extents and the precision
+std::tuple<int, int, int, int, int> tc_bucket(int64_t n_pad, const GridDesc& g, int prec) {
+    int lg = 0;
+    while (lg < 62 && ((int64_t)1 << (lg + 1)) <= n_pad) ++lg;
+    return std::make_tuple(lg, g.nx, g.ny, g.nz, prec);
+}
+
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -109,7 +118,12 @@ struct xs_context {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr};
     cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
-    std::map<std::tuple<int64_t, int, int, int, int>, int> tuned_chunk;  // (n_pad, nx, ny, nz, prec)
+    // tuner results per shape bucket (tc_bucket): tile kind and chunk length
+    struct TcChoice {
+        int kind;
+        int chunk;
+    };
+    std::map<std::tuple<int, int, int, int, int>, TcChoice> tuned;
     // small device-side tables, one slot per caller tag, re-uploaded only
     // when their content changes (so repeated calls enqueue no host copies)
     struct ConstSlot {
@@ -382,7 +396,7 @@ xs_status xs_sync_status(xs_context* ctx, void* cuda_stream) {
 
 static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid,
                                 xs_precision prec, float* I_out, float* amp_out, cudaStream_t st,
-                                int chunk_override) {
+                                int chunk_override, int kind_override = -1) {
     if (!ctx || !traj || !I_out) return fail(XS_ERR_INVALID_ARG, "context, trajectory and I_out are required");
     xs_status s = check_grid(grid);
     if (s != XS_OK) return s;
@@ -451,12 +465,19 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
     DirectPlan dplan{};
     int tc_pairs = 0;
     int chunk_stages = kDefaultChunkStages;
+    int tile_kind = kTcTile128;
     if (use_tc) {
-        auto key = std::make_tuple(n_pad, g.nx, g.ny, g.nz, (int)prec);
-        auto it = ctx->tuned_chunk.find(key);
-        if (it != ctx->tuned_chunk.end()) chunk_stages = it->second;
+        // half grids are planned on 128 x 128 tiles; otherwise the tuned tile
+        // kind of this shape, else the default rule
+        tile_kind = half_axis >= 0 ? kTcTile128 : tc_default_kind(gc);
+        auto it = ctx->tuned.find(tc_bucket(n_pad, gc, (int)prec));
+        if (it != ctx->tuned.end()) {
+            chunk_stages = it->second.chunk;
+            if (half_axis < 0) tile_kind = it->second.kind;
+        }
         if (chunk_override > 0) chunk_stages = chunk_override;
-        tc_pairs = tc_pair_capacity(ctx->num_sms);
+        if (kind_override >= 0 && half_axis < 0) tile_kind = kind_override;
+        tc_pairs = tc_pair_capacity(ctx->num_sms, tile_kind);
     } else {
         dplan = plan_direct(n_pad, fchunk, g, ctx->num_sms);
     }
@@ -471,7 +492,7 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
     const size_t o_rec = carve((size_t)fchunk * rec_per_frame);
     const size_t o_part = carve(use_tc ? tc_scratch_bytes(tc_pairs) : dplan.partial_bytes);
     auto split_of = [&](int64_t nf) {
-        return tc_split_plan(tc_units(tc_traj(nullptr, n_pad, nf, gc, nullptr, nullptr)), tc_pairs,
+        return tc_split_plan(tc_units(tc_traj(nullptr, n_pad, nf, gc, nullptr, nullptr, tile_kind)), tc_pairs,
                              (int)(n_pad / tc_atom_multiple()), chunk_stages);
     };
     size_t split_bytes = 0;
@@ -540,7 +561,7 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
             if (use_tc) {
                 float* Ih = half_axis >= 0 ? reinterpret_cast<float*>(ws + o_half) : Ic;
                 float* Ah = half_axis >= 0 ? (Ac ? reinterpret_cast<float*>(ws + o_half_amp) : nullptr) : Ac;
-                const TcTraj tr = tc_traj(rec, n_pad, nf, gc, Ih, Ah);
+                const TcTraj tr = tc_traj(rec, n_pad, nf, gc, Ih, Ah, tile_kind);
                 const TcSplit sp = split_of(nf);
                 XS_CUDA(traced(ctx, "tc", st, [&] {
                     return launch_tc_single(tr, tc_pairs, sp, chunk_stages, prec == XS_PREC_SPLIT_BF16,
@@ -876,6 +897,7 @@ xs_status xs_intensity_points(xs_context* ctx, const xs_traj* traj, const int32_
         XS_CUDA(traced(ctx, "tc", st, [&] {
             return launch_tc_batch(reinterpret_cast<const TcTraj*>(dc + o_tr), reinterpret_cast<const int4*>(dc + o_units),
                                    reinterpret_cast<const int*>(dc + o_ps), n_pairs, kDefaultChunkStages, prec == XS_PREC_SPLIT_BF16,
+                                   kTcTile128,
                                    reinterpret_cast<double*>(ws + o_part), ctx->d_err, ctx->timeout_ns, st);
         }));
         XS_CUDA(traced(ctx, "points", st, [&] {
@@ -947,10 +969,18 @@ xs_status xs_intensity_species(xs_context* ctx, const xs_traj* traj, const int32
     const size_t per_frame = (size_t)n_pad_max * sizeof(AtomRec) + (size_t)P * (2 * sizeof(float) + sizeof(float) + 2 * sizeof(double));
     int64_t fchunk = std::max<int64_t>(1, std::min<int64_t>(T, (int64_t)(((size_t)6 << 30) / per_frame)));
     if (fchunk > 65535) fchunk = 65535;
-    int tc_pairs = 0, chunk_stages = kDefaultChunkStages;
+    // tile kind and chunk length per species' atom count, as xs_intensity
+    // chooses them (tuned per shape bucket, else the default rule)
+    auto choice_of = [&](int64_t n_pad) {
+        xs_context::TcChoice c{tc_default_kind(g), kDefaultChunkStages};
+        auto it = ctx->tuned.find(tc_bucket(n_pad, g, (int)prec));
+        if (it != ctx->tuned.end()) c = it->second;
+        return c;
+    };
+    int tc_pairs = 0;
     DirectPlan dmax{};
     if (use_tc) {
-        tc_pairs = tc_pair_capacity(ctx->num_sms);
+        tc_pairs = std::max(tc_pair_capacity(ctx->num_sms, kTcTile128), tc_pair_capacity(ctx->num_sms, kTcTile64));
     } else {
         for (int sp = 0; sp < n_species; ++sp) {
             const int64_t n = start[(size_t)sp + 1] - start[(size_t)sp];
@@ -968,8 +998,9 @@ xs_status xs_intensity_species(xs_context* ctx, const xs_traj* traj, const int32
     const size_t o_rec = carve((size_t)fchunk * n_pad_max * sizeof(AtomRec));
     const size_t o_part = carve(use_tc ? tc_scratch_bytes(tc_pairs) : dmax.partial_bytes);
     auto split_of = [&](int64_t n_pad, int64_t nf) {
-        return tc_split_plan(tc_units(tc_traj(nullptr, n_pad, nf, g, nullptr, nullptr)), tc_pairs,
-                             (int)(n_pad / tc_atom_multiple()), chunk_stages);
+        const xs_context::TcChoice c = choice_of(n_pad);
+        return tc_split_plan(tc_units(tc_traj(nullptr, n_pad, nf, g, nullptr, nullptr, c.kind)),
+                             tc_pair_capacity(ctx->num_sms, c.kind), (int)(n_pad / tc_atom_multiple()), c.chunk);
     };
     size_t split_bytes = 0;
     if (use_tc) {
@@ -1014,15 +1045,17 @@ xs_status xs_intensity_species(xs_context* ctx, const xs_traj* traj, const int32
             XS_CUDA(traced(ctx, "phase", st,
                            [&] { return launch_phase(pos_c, traj->f, ns, nf, n_pad, hm, popt, rec, ctx->d_err, st); }));
             if (use_tc) {
-                const TcTraj tr = tc_traj(rec, n_pad, nf, g, I_tmp, S_tmp);
+                const xs_context::TcChoice ch = choice_of(n_pad);
+                const int pairs = tc_pair_capacity(ctx->num_sms, ch.kind);
+                const TcTraj tr = tc_traj(rec, n_pad, nf, g, I_tmp, S_tmp, ch.kind);
                 const TcSplit spl = split_of(n_pad, nf);
                 XS_CUDA(traced(ctx, "tc", st, [&] {
-                    return launch_tc_single(tr, tc_pairs, spl, chunk_stages, prec == XS_PREC_SPLIT_BF16,
+                    return launch_tc_single(tr, pairs, spl, ch.chunk, prec == XS_PREC_SPLIT_BF16,
                                             reinterpret_cast<double*>(ws + o_part), ws + o_split, ctx->d_err,
                                             ctx->timeout_ns, st);
                 }));
                 XS_CUDA(traced(ctx, "split_finish", st,
-                               [&] { return launch_tc_split_finish(tr, tc_pairs, spl, ws + o_split, st); }));
+                               [&] { return launch_tc_split_finish(tr, pairs, spl, ws + o_split, st); }));
             } else {
                 const DirectPlan pc = plan_direct(n_pad, nf, g, ctx->num_sms);
                 if (pc.partial_bytes > dmax.partial_bytes) return fail(XS_ERR_CUDA, "internal: partial plan grew");
@@ -1057,6 +1090,12 @@ xs_status xs_tune(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, xs
     const int64_t P = g.pixels();
     const int64_t T = std::min<int64_t>(traj->n_frames, 64);
     if (P == 0 || T == 0 || traj->n_atoms == 0) return XS_OK;
+    // the grid the contraction runs on (a half grid where that saves tiles,
+    // always on 128 x 128 tiles) and the key the intensity calls look up
+    GridDesc gc = g;
+    const bool half = friedel_half_grid(g, gc) >= 0;
+    if (!half) gc = g;
+    const int64_t n_pad = round_up(traj->n_atoms, 64);
     XS_CUDA(cudaStreamSynchronize(st));
     float* out = static_cast<float*>(ctx->raw_alloc((size_t)T * P * sizeof(float)));
     if (!out) return fail(XS_ERR_NO_MEMORY, "tuning buffer allocation failed");
@@ -1065,34 +1104,60 @@ xs_status xs_tune(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, xs
     cudaEvent_t e0, e1;
     XS_CUDA(cudaEventCreate(&e0));
     XS_CUDA(cudaEventCreate(&e1));
-    // the tensor core's FP32 accumulation is not round-to-nearest: no chunk
-    // longer than 4,096 atoms, so its bias stays far below the 1e-4 target
-    const int cands[] = {16, 32, 64};
-    int best = 32;
+    // tile kinds x chunk lengths, each timed after a warm-up call.  The tensor
+    // core's FP32 accumulation is not round-to-nearest: no chunk longer than
+    // 4,096 atoms, so its bias stays far below the 1e-4 target
+    const int chunks[] = {16, 32, 64};
+    std::vector<int> kinds = {kTcTile128};
+    if (!half) kinds.push_back(kTcTile64);
+    xs_context::TcChoice best{kTcTile128, kDefaultChunkStages};
     float best_ms = 1e30f;
-    for (int c : cands) {
-        s = intensity_impl(ctx, &sub, grid, prec, out, nullptr, st, c);  // warm-up
-        if (s != XS_OK) break;
-        XS_CUDA(cudaEventRecord(e0, st));
-        s = intensity_impl(ctx, &sub, grid, prec, out, nullptr, st, c);
-        if (s != XS_OK) break;
-        XS_CUDA(cudaEventRecord(e1, st));
-        XS_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        XS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = c;
+    for (int kind : kinds) {
+        for (int c : chunks) {
+            s = intensity_impl(ctx, &sub, grid, prec, out, nullptr, st, c, kind);  // warm-up
+            if (s != XS_OK) break;
+            XS_CUDA(cudaEventRecord(e0, st));
+            s = intensity_impl(ctx, &sub, grid, prec, out, nullptr, st, c, kind);
+            if (s != XS_OK) break;
+            XS_CUDA(cudaEventRecord(e1, st));
+            XS_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            XS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = {kind, c};
+            }
         }
+        if (s != XS_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(st);
     ctx->raw_free(out);
     if (s != XS_OK) return s;
-    const int64_t n_pad = round_up(traj->n_atoms, 64);
-    ctx->tuned_chunk[std::make_tuple(n_pad, g.nx, g.ny, g.nz, (int)prec)] = best;
+    ctx->tuned[tc_bucket(n_pad, gc, (int)prec)] = best;
     return xs_sync_status(ctx, cuda_stream);
+}
+
+xs_status xs_tuned_choice(xs_context* ctx, int64_t n_atoms, const xs_qgrid* grid, xs_precision prec,
+                          int32_t* tile_kind, int32_t* chunk_stages) {
+    if (!ctx || !grid || !tile_kind || !chunk_stages || n_atoms < 0) return fail(XS_ERR_INVALID_ARG, "bad arguments");
+    xs_status s = check_grid(grid);
+    if (s != XS_OK) return s;
+    const GridDesc g = to_desc(grid);
+    GridDesc gc = g;
+    const bool half = friedel_half_grid(g, gc) >= 0;
+    if (!half) gc = g;
+    const int64_t n_pad = round_up(n_atoms > 0 ? n_atoms : 1, 64);
+    auto it = ctx->tuned.find(tc_bucket(n_pad, gc, (int)prec));
+    if (it == ctx->tuned.end()) {
+        *tile_kind = half ? kTcTile128 : tc_default_kind(gc);
+        *chunk_stages = kDefaultChunkStages;
+        return XS_OK;
+    }
+    *tile_kind = half ? kTcTile128 : it->second.kind;
+    *chunk_stages = it->second.chunk;
+    return XS_OK;
 }
 
 // --------------------------------------------------------------------------
@@ -1547,7 +1612,7 @@ static xs_status batched_impl(xs_context* ctx, const xs_traj* traj, const xs_qgr
             if (j.half_axis >= 0) j.half_off = carve((size_t)j.T * j.v.pixels() * sizeof(float));
         }
     }
-    const int cap = tc_pair_capacity(ctx->num_sms);
+    const int cap = std::max(tc_pair_capacity(ctx->num_sms, kTcTile128), tc_pair_capacity(ctx->num_sms, kTcTile64));
     const size_t o_scratch = carve(tc_scratch_bytes(cap));
 
     // trajectory table and per-pair unit lists (longest first)
@@ -1577,40 +1642,68 @@ static xs_status batched_impl(xs_context* ctx, const xs_traj* traj, const xs_qgr
     xs_status s = ensure_ws(ctx, off + 256);
     if (s != XS_OK) return s;
     char* ws = static_cast<char*>(ctx->ws);
+    // each trajectory's tile kind and chunk length: tuned for its shape
+    // bucket (xs_tune), else the default rule; half grids use 128 x 128 tiles
     for (int i : which) {
         const Job& j = jobs[(size_t)i];
+        const GridDesc& gc = j.half_axis >= 0 ? j.v : j.g;
+        int kind = j.half_axis >= 0 ? kTcTile128 : tc_default_kind(gc), chunk = 0;
+        auto it = ctx->tuned.find(tc_bucket(j.n_pad, gc, (int)prec));
+        if (it != ctx->tuned.end()) {
+            chunk = it->second.chunk;
+            if (j.half_axis < 0) kind = it->second.kind;
+        }
         if (j.half_axis >= 0)
             trs.push_back(tc_traj(reinterpret_cast<AtomRec*>(ws + j.rec_off), j.n_pad, j.T, j.v,
-                                  reinterpret_cast<float*>(ws + j.half_off), nullptr));
+                                  reinterpret_cast<float*>(ws + j.half_off), nullptr, kind, chunk));
         else
-            trs.push_back(tc_traj(reinterpret_cast<AtomRec*>(ws + j.rec_off), j.n_pad, j.T, j.g, I_out[i], nullptr));
+            trs.push_back(tc_traj(reinterpret_cast<AtomRec*>(ws + j.rec_off), j.n_pad, j.T, j.g, I_out[i], nullptr,
+                                  kind, chunk));
     }
     for (const TcTraj& t : trs) total_units += tc_units(t);
     for (int i : empty)
         XS_CUDA(cudaMemsetAsync(I_out[i], 0, (size_t)jobs[(size_t)i].T * jobs[(size_t)i].g.pixels() * sizeof(float), st));
     if (trs.empty() && !req) return XS_OK;
-    const int n_pairs = (int)std::min<int64_t>(cap, std::max<int64_t>(total_units, 1));
-    std::vector<int4> units;
-    std::vector<int> pair_start;
-    size_t o_tr = 0, o_units = 0, o_ps = 0;
+    // one persistent launch per tile kind, each over the units of its
+    // trajectories (entries of the one trajectory table), longest first
+    struct KindLaunch {
+        int kind, n_pairs = 0;
+        size_t o_units = 0, o_ps = 0;
+    };
+    std::vector<KindLaunch> kls;
+    size_t o_tr = 0;
     if (!trs.empty()) {
-        tc_build_lists(trs, n_pairs, units, pair_start);
-        if (units.size() > (size_t)INT32_MAX) return fail(XS_ERR_UNSUPPORTED, "too many work units");
         o_tr = push(blob, trs.data(), trs.size());
-        o_units = push(blob, units.data(), units.size());
-        o_ps = push(blob, pair_start.data(), pair_start.size());
+        for (int kind : {kTcTile128, kTcTile64}) {
+            std::vector<int4> all;
+            for (size_t e = 0; e < trs.size(); ++e) {
+                const TcTraj& t = trs[e];
+                if (t.kind != kind) continue;
+                for (int f = 0; f < t.n_frames; ++f)
+                    for (int z = 0; z < t.nz; ++z)
+                        for (int ty = 0; ty < t.tiles_y; ++ty)
+                            for (int tx = 0; tx < t.tiles_x; ++tx)
+                                all.push_back(make_int4((int)e, f, z, tx | (ty << 16)));
+            }
+            if (all.empty()) continue;
+            if (all.size() > (size_t)INT32_MAX) return fail(XS_ERR_UNSUPPORTED, "too many work units");
+            KindLaunch kl;
+            kl.kind = kind;
+            kl.n_pairs = (int)std::min<int64_t>(tc_pair_capacity(ctx->num_sms, kind), (int64_t)all.size());
+            std::vector<int4> units;
+            std::vector<int> pair_start;
+            tc_deal_units(trs, all, kl.n_pairs, units, pair_start);
+            kl.o_units = push(blob, units.data(), units.size());
+            kl.o_ps = push(blob, pair_start.data(), pair_start.size());
+            kls.push_back(kl);
+        }
     }
     if (blob.empty()) blob.assign(256, 0);
     void* d = nullptr;
     s = upload_const(ctx, "tc_batch", blob, st, &d);
     if (s != XS_OK) return s;
     char* dc = static_cast<char*>(d);
-    int chunk = kDefaultChunkStages;
-    if (!trs.empty()) {
-        auto it = ctx->tuned_chunk.find(std::make_tuple(trs[trs.size() / 2].n_pad, trs[trs.size() / 2].nx,
-                                                        trs[trs.size() / 2].ny, trs[trs.size() / 2].nz, (int)prec));
-        if (it != ctx->tuned_chunk.end()) chunk = it->second;
-    }
+    const int chunk = kDefaultChunkStages;  // for trajectories without a tuned chunk
     const bool bf16 = prec == XS_PREC_SPLIT_BF16;
     auto enqueue = [&]() -> cudaError_t {
         cudaError_t err = cudaSuccess;
@@ -1627,10 +1720,12 @@ static xs_status batched_impl(xs_context* ctx, const xs_traj* traj, const xs_qgr
             err = launch_phase(t.pos, t.f, j.N, j.T, j.n_pad, hm, popt, reinterpret_cast<AtomRec*>(ws + j.rec_off),
                                ctx->d_err, st);
         }
-        if (err == cudaSuccess && !trs.empty())
-            err = launch_tc_batch(reinterpret_cast<const TcTraj*>(dc + o_tr), reinterpret_cast<const int4*>(dc + o_units),
-                                  reinterpret_cast<const int*>(dc + o_ps), n_pairs, chunk, bf16,
-                                  reinterpret_cast<double*>(ws + o_scratch), ctx->d_err, ctx->timeout_ns, st);
+        for (size_t k = 0; k < kls.size() && err == cudaSuccess; ++k)
+            err = launch_tc_batch(reinterpret_cast<const TcTraj*>(dc + o_tr),
+                                  reinterpret_cast<const int4*>(dc + kls[k].o_units),
+                                  reinterpret_cast<const int*>(dc + kls[k].o_ps), kls[k].n_pairs, chunk, bf16,
+                                  kls[k].kind, reinterpret_cast<double*>(ws + o_scratch), ctx->d_err, ctx->timeout_ns,
+                                  st);
         for (size_t e = 0; e < trs.size() && err == cudaSuccess; ++e) {
             const Job& j = jobs[(size_t)which[e]];
             if (j.half_axis >= 0)

@@ -63,6 +63,13 @@ cudaError_t launch_direct(const AtomRec* rec, int64_t n_pad, int64_t n_frames, c
 // ---- tensor-core split-precision contraction ----------------------------
 // One trajectory of a launch: phase records [n_frames][n_pad] (slot order of
 // the phase kernel), outputs, and its grid; tiles are 128 x 128 pixels.
+// Tile kinds of the pair contraction: kTcTile128 covers 128 n_x x 128 n_y
+// (MMA N = 256, 8 producer warps with runs of 32 n), kTcTile64 covers
+// 128 n_x x 64 n_y (MMA N = 128, 12 producer warps with runs of 16 n).
+constexpr int kTcTile128 = 0;
+constexpr int kTcTile64 = 1;
+__host__ __device__ constexpr inline int tc_tile_y(int kind) { return kind == kTcTile64 ? 64 : 128; }  // n_y per tile
+
 struct TcTraj {
     const uint4* rec;
     float* I;
@@ -72,11 +79,17 @@ struct TcTraj {
     int tiles_x, tiles_y;
     int nx0, nx, ny0, ny, nz0, nz;
     int n_frames;
+    int kind;      // tile kind (all trajectories of one launch share it)
+    int chunk;     // stages per FP32 accumulation chunk; 0: the launch's
 };
 bool tc_supported(const GridDesc& g);
 int64_t tc_atom_multiple();
-int tc_pair_capacity(int num_sms);  // co-resident CTA pairs
-TcTraj tc_traj(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g, float* I, float* amp);
+int tc_pair_capacity(int num_sms, int kind = kTcTile128);  // co-resident CTA pairs
+TcTraj tc_traj(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g, float* I, float* amp,
+               int kind = kTcTile128, int chunk = 0);
+// tile kind for a (contracted) grid when nothing was tuned: 128 x 64 tiles
+// where they need no more tiles than 128 x 128 ones (n_y extent <= 64)
+int tc_default_kind(const GridDesc& g);
 int64_t tc_units(const TcTraj& t);  // frames x planes x tiles
 size_t tc_scratch_bytes(int n_pairs);
 // per-pair unit lists (traj, frame, plane, tile_x | tile_y << 16), longest first
@@ -107,7 +120,7 @@ cudaError_t launch_tc_single(const TcTraj& tr, int n_pairs, const TcSplit& sp, i
 cudaError_t launch_tc_split_finish(const TcTraj& tr, int n_pairs, const TcSplit& sp, void* split_buf,
                                    cudaStream_t st);
 cudaError_t launch_tc_batch(const TcTraj* d_trajs, const int4* d_units, const int* d_pair_start, int n_pairs,
-                            int chunk_stages, bool bf16, double* scratch, int* err, int64_t timeout_ns,
+                            int chunk_stages, bool bf16, int kind, double* scratch, int* err, int64_t timeout_ns,
                             cudaStream_t st);
 
 // ---- g2 -----------------------------------------------------------------
