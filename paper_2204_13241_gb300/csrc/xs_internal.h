@@ -186,7 +186,7 @@ size_t adjoint_workspace_bytes(const GridDesc& g);
 cudaError_t launch_adjoint(const AtomRec* rec, int64_t n_atoms, int64_t n_pad, const GridDesc& g,
                            const Mat3& hinv, const float* amp, const float* dL_dI,
                            void* workspace, float* grad, int* err, int64_t timeout_ns, cudaStream_t st);
-// the contraction over n_y on tensor cores (split BF16): A images of
+// the contraction over n_y on tensor cores (split BF16): H images of
 // adjoint_tc_image_bytes(g) bytes (16-byte aligned) built from H [P]
 size_t adjoint_tc_image_bytes(const GridDesc& g);
 cudaError_t launch_adjoint_tc(const AtomRec* rec, int64_t n_atoms, int64_t n_pad, const GridDesc& g,
