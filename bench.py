@@ -38,13 +38,18 @@ FALLBACK_PEAK = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gb
 # FP32 SIMT rate from the unit counts and the maximum SM clock (152 SMs x 128
 # FP32 lanes x 2 flops x 2.07 GHz); nominal, the measured peaks carry none
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# issue rate in thread-instructions per second (152 SMs x 4 schedulers x 32
+# lanes x 2.07 GHz), the bound of the FP32 direct kernel, which ncu puts at
+# about 53 thread-instructions per atom*pixel*frame
+ISSUE_PEAK_TINST = 152 * 4 * 32 * 2.07e9
+DIRECT_INST_PER_UNIT = 53.0
 
-# DRAM bytes (read + write) of one tc_kernel launch of the 1,000-frame
-# workload, from an ncu capture of that launch (dram__bytes_read.sum +
-# dram__bytes_write.sum, one pass; 64-stage chunks): 4.11 GB + 77.2 MB.  Reported only while
-# k_tc.cu is unchanged; other frame counts scale it by frames (records and
-# outputs are per frame; the split-piece partials are not, a few percent).
-TC_TRAFFIC = {"k_tc_sha256_prefix": "4c877d58ca21e375", "bytes": 4.11e9 + 77.23e6, "frames": 1000}
+# DRAM bytes (read + write) of one tc_kernel launch, from an ncu capture of
+# the 160-frame case of the same workload (dram__bytes_read.sum +
+# dram__bytes_write.sum: 655.70 MB + 14.16 MB), scaled by frames: the
+# records read and the intensities written are per frame, the split pieces'
+# partials (a few MB) are not.  Reported only while k_tc.cu is unchanged.
+TC_TRAFFIC = {"k_tc_sha256_prefix": "f464cc10a5813c7a", "bytes": 655701760 + 14156032, "frames": 160}
 
 
 def _args():
@@ -62,6 +67,8 @@ def _args():
     ap.add_argument("--no-table1", action="store_true")
     ap.add_argument("--no-next", action="store_true", help="skip the ISF, Ewald-slice and species timings")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing on its own workload")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 4,000-atom FP32 and the 3.2-million-atom crystal entries")
     return ap.parse_args()
 
 
@@ -202,6 +209,197 @@ def run_reference(args):
     return 0
 
 
+def _roof_tensor(units, ms, peaks, what):
+    peak = float(peaks[0].get("bf16_tflops_sustained", FALLBACK_PEAK["bf16_tflops_sustained"]))
+    a = 8.0 * units / (ms * 1e-3) / 1e12
+    return {"bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+            "kernel": what, "kernel_ms_per_call": ms, "peak_source": f"{peaks[1]} bf16 sustained",
+            "note": "8 algorithmic flops per atom*pixel*frame (one complex multiply-add)"}
+
+
+def config_entries(xs, ctx, stream, peaks):
+    """Entries for the 4,000-atom workload on the FP32 path (its whole step)
+    and the 3.2-million-atom crystal; returns (entries, what the oracle checks
+    later in the CPU-baseline leg)."""
+    import torch
+    from paper_2204_13241_gb300 import workloads as wl
+
+    out, keep = {}, {}
+
+    def ev_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        ctx.sync_status()
+        return e0.elapsed_time(e1) / reps, r
+
+    def stage_ms(tag, fn, reps):
+        """device time of the `tag` launches per call (library events)"""
+        fn()
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_read("")
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        ms, n = ctx.profile_read(tag)
+        ctx.profile(False)
+        return ms / reps
+
+    # 4,000 atoms, 10 frames, 64^2 plane: intensity (FP32 direct), g2 on
+    # delays 1..9, XSVS on K = 1..10 over unit rings
+    tr0, g0 = wl.config0()
+    p0 = torch.from_numpy(tr0.pos).cuda()
+    f0 = torch.from_numpy(tr0.f).cuda()
+    T0, P0 = tr0.pos.shape[0], g0.n_pixels
+    R0 = wl.rings_for_plane(g0)
+    taus0, Ks0 = list(range(1, 10)), list(range(1, 11))
+    I0 = torch.empty((T0, 1, g0.ny, g0.nx), dtype=torch.float32, device="cuda")
+
+    def step0():
+        xs.intensity(p0, f0, tr0.box, g0, "fp32", out=I0)
+        g, _ = xs.g2(I0.view(T0, -1), taus0)
+        b, _ = xs.xsvs_contrast(I0, g0, tr0.box, Ks0, R0)
+        return g, b
+
+    ms0, (g0_out, b0_out) = ev_ms(step0, 20)
+    d_ms = stage_ms("direct", lambda: xs.intensity(p0, f0, tr0.box, g0, "fp32", out=I0), 20)
+    units0 = float(tr0.n_atoms) * P0 * T0
+    ach = units0 * DIRECT_INST_PER_UNIT / (d_ms * 1e-3)
+    out["c0_fp32_4000_atoms"] = {
+        "workload": "4,000 atoms U[0,40)^3, f = 1, 10 Brownian frames (0.1 A), 64^2 plane; FP32 direct path; "
+                    "step = intensity + g2 (tau 1..9) + XSVS (K 1..10)",
+        "value": units0 / (ms0 * 1e-3), "unit": METRIC, "ms_per_step": ms0, "dtype": "f32",
+        "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": ISSUE_PEAK_TINST / 1e12,
+                     "unit": "T thread-instructions/s", "frac": ach / ISSUE_PEAK_TINST, "kernel": "direct_kernel",
+                     "kernel_ms_per_call": d_ms,
+                     "note": "about 53 thread-instructions per atom*pixel*frame (ncu); peak = 152 SMs x 4 "
+                             "schedulers x 32 lanes x 2.07 GHz"}}
+    keep["c0"] = (I0.view(T0, -1).cpu().numpy(), g0_out.cpu().numpy(), b0_out.cpu().numpy(), taus0, Ks0, R0, tr0, g0)
+    del p0, f0
+
+    # 3.2-million-atom crystal: 32 frames of the 512^2 plane streamed from
+    # pinned host memory (host in, device out), the 128^3 volume on one frame
+    nf4 = 32
+    tr4, g4 = wl.config4(keep=range(nf4))
+    N4 = tr4.n_atoms
+    pos_h = torch.from_numpy(tr4.pos).pin_memory()
+    f_h = torch.from_numpy(tr4.f).pin_memory()
+    I4 = torch.empty((nf4, 1, g4.ny, g4.nx), dtype=torch.float32, device="cuda")
+    ms4, _ = ev_ms(lambda: xs.intensity(pos_h, f_h, tr4.box, g4, "fp16", out=I4), 2)
+    units4 = float(N4) * g4.n_pixels * nf4
+    tc4 = stage_ms("tc", lambda: xs.intensity(pos_h, f_h, tr4.box, g4, "fp16", out=I4), 2)
+    vol = wl.centered_volume(128)
+    p1 = torch.from_numpy(tr4.pos[:1]).cuda()
+    f1 = f_h.cuda()
+    Iv = torch.empty((1, vol.nz, vol.ny, vol.nx), dtype=torch.float32, device="cuda")
+    msv, _ = ev_ms(lambda: xs.intensity(p1, f1, tr4.box, vol, "fp16", out=Iv), 3)
+    tcv = stage_ms("tc", lambda: xs.intensity(p1, f1, tr4.box, vol, "fp16", out=Iv), 3)
+    unitsv = float(N4) * vol.n_pixels
+    # g2 and XSVS at the workload's correlation size: 10,000 frames of the
+    # 512^2 plane (a seeded speckle series with the ring's AR(1) correlation)
+    T4 = 10_000
+    n_rings4 = wl.rings_for_plane(g4)
+    ring_h = xs.ring_index(g4, tr4.box, 1.0, n_rings4)
+    rho = torch.from_numpy((0.3 + 0.65 * ring_h / n_rings4).astype(np.float32))
+    Is = wl.speckle_series(wl.SEED_BASE + 40, T4, rho, "cuda")
+    taus4 = [int(t) for t in wl.log_delays(T4)]
+    Ks4 = [int(k) for k in wl.window_list_125(1000)]
+    ms_g2, (g4_out, _) = ev_ms(lambda: xs.g2(Is, taus4), 2)
+    ms_xs, (b4_out, _) = ev_ms(lambda: xs.xsvs_contrast(Is.view(T4, 1, g4.ny, g4.nx), g4, tr4.box, Ks4, n_rings4), 2)
+    out["c4_crystal_3_2M_atoms"] = {
+        "workload": "FCC a = 4 A, L = 400 A, 20% vacancies (3,200,000 atoms), thermal 0.2 A, Brownian frames "
+                    "(0.02 A); split FP16",
+        "plane_512_streamed": {"frames": nf4, "value": units4 / (ms4 * 1e-3), "unit": METRIC, "ms_per_call": ms4,
+                               "h2d_bytes_per_call": int(tr4.pos.nbytes + tr4.f.nbytes),
+                               "roofline": _roof_tensor(units4, tc4, peaks, "tc_kernel (all launches of one call: "
+                                                        "the frames are streamed in chunks of growing size)")},
+        "volume_128^3": {"frames": 1, "value": unitsv / (msv * 1e-3), "unit": METRIC, "ms_per_call": msv,
+                         "roofline": _roof_tensor(unitsv, tcv, peaks, "tc_kernel")},
+        "correlations_10000_frames_512^2": {"g2_ms": ms_g2, "n_tau": len(taus4), "xsvs_ms": ms_xs,
+                                            "window_lengths": Ks4, "rings": n_rings4,
+                                            "input": "seeded AR(1) speckle series with the workload's shape "
+                                                     "(10,000 x 512^2; the 10,000 crystal frames would be 384 GB "
+                                                     "of positions)"}}
+    rng = np.random.default_rng(4)
+    m4 = g4.miller()
+    pix4 = np.unique(np.concatenate([np.flatnonzero(np.all(m4 == 0, axis=1)), rng.choice(m4.shape[0], 96, replace=False)]))
+    mv = vol.miller()
+    pixv = np.unique(np.concatenate([np.flatnonzero(np.all(mv == 0, axis=1)), rng.choice(mv.shape[0], 96, replace=False)]))
+    pix_c = rng.choice(m4.shape[0], 256, replace=False)
+    keep["c4"] = dict(tr=tr4, g=g4, vol=vol, pix=pix4, pixv=pixv,
+                      I=I4.view(nf4, -1)[[0, nf4 - 1]][:, torch.from_numpy(pix4).cuda()].cpu().numpy(),
+                      Iv=Iv.view(1, -1)[:, torch.from_numpy(pixv).cuda()].cpu().numpy(),
+                      Is=Is[:, torch.from_numpy(pix_c).cuda()].cpu().numpy(), pix_c=pix_c,
+                      g2=g4_out[:, torch.from_numpy(pix_c).cuda()].cpu().numpy(), taus=taus4)
+    cnt_r = np.bincount(ring_h, minlength=n_rings4 + 1)
+    sel_r = [r for r in (1, 50, 181, 300, n_rings4) if cnt_r[r] >= 8]
+    sel = np.flatnonzero(np.isin(ring_h, sel_r))
+    keep["c4"].update(Ir=Is[:, torch.from_numpy(sel).cuda()].cpu().numpy(), ring_sel=ring_h[sel], rings_pick=sel_r,
+                      beta=b4_out.cpu().numpy(), Ks=Ks4, n_rings=n_rings4)
+    del Is, I4, Iv, p1, f1, pos_h
+    torch.cuda.empty_cache()
+    return out, keep
+
+
+def config_accuracy(entries, keep, ref0):
+    """Errors of the entries of config_entries against the FP64 oracle (run in
+    the CPU-baseline leg)."""
+    import oracle
+
+    I0, g0_out, b0_out, taus0, Ks0, R0, tr0, g0 = keep["c0"]
+    m0 = g0.miller()
+    nz0 = np.any(m0 != 0, axis=1)
+    e_I0 = max(float(np.linalg.norm(I0[t, nz0] - ref0[t, nz0]) / np.linalg.norm(ref0[t, nz0])) for t in range(I0.shape[0]))
+    e_pix0 = max(float(np.max(np.abs(I0[t, nz0] - ref0[t, nz0]) / np.maximum(ref0[t, nz0], ref0[t, nz0].mean())))
+                 for t in range(I0.shape[0]))
+    # end to end: the oracle's g2 and contrast of the oracle's intensity
+    gref, _ = oracle.g2(ref0, taus0)
+    e_g2_0 = float(np.linalg.norm(g0_out[:, nz0] - gref[:, nz0]) / np.linalg.norm(gref[:, nz0]))
+    rings0 = oracle.ring_index(tr0.box, m0, 1.0, R0)
+    bref, cref = oracle.xsvs_contrast(ref0, Ks0, rings0, R0)
+    ok = cref >= 8
+    e_b0 = float(np.max(np.abs(b0_out[:, ok] - bref[:, ok]) / np.abs(bref[:, ok])))
+    entries["c0_fp32_4000_atoms"]["accuracy"] = {
+        "e_I": e_I0, "e_pix": e_pix0, "e_g2": e_g2_0, "e_beta": e_b0, "target": 1e-6,
+        "against": "FP64 oracle, every frame and pixel; g2 and beta end to end (oracle g2 and beta of the "
+                   "oracle's intensity)"}
+    k = keep["c4"]
+    tr4 = k["tr"]
+    ref = oracle.intensity(tr4.pos[[0, tr4.pos.shape[0] - 1]], tr4.f, tr4.box, k["g"].miller()[k["pix"]])
+    refv = oracle.intensity(tr4.pos[:1], tr4.f, tr4.box, k["vol"].miller()[k["pixv"]])
+
+    def errs(I, r, m):
+        nz = np.any(m != 0, axis=1)
+        e = max(float(np.linalg.norm(I[t, nz] - r[t, nz]) / np.linalg.norm(r[t, nz])) for t in range(r.shape[0]))
+        ep = max(float(np.max(np.abs(I[t, nz] - r[t, nz]) / np.maximum(r[t, nz], r[t, nz].mean())))
+                 for t in range(r.shape[0]))
+        z = ~nz
+        e0 = float(np.max(np.abs(I[:, z] - r[:, z]) / r[:, z])) if z.any() else 0.0
+        return e, ep, e0
+
+    e4, ep4, e04 = errs(k["I"].astype(np.float64), ref, k["g"].miller()[k["pix"]])
+    ev, epv, e0v = errs(k["Iv"].astype(np.float64), refv, k["vol"].miller()[k["pixv"]])
+    gr, _ = oracle.g2(k["Is"], k["taus"])
+    e_g2 = float(np.max(np.abs(k["g2"] - gr) / np.abs(gr)))
+    bo, co = oracle.xsvs_contrast(k["Ir"], k["Ks"], k["ring_sel"], k["n_rings"])
+    cols = [r - 1 for r in k["rings_pick"]]
+    e_b = float(np.max(np.abs(k["beta"][:, cols] - bo[:, cols]) / np.abs(bo[:, cols])))
+    c4 = entries["c4_crystal_3_2M_atoms"]
+    c4["plane_512_streamed"]["accuracy"] = {"e_I": e4, "e_pix": ep4, "e_q0": e04, "frames": [0, 31],
+                                            "pixels": int(len(k["pix"]))}
+    c4["volume_128^3"]["accuracy"] = {"e_I": ev, "e_pix": epv, "e_q0": e0v, "pixels": int(len(k["pixv"]))}
+    c4["correlations_10000_frames_512^2"]["accuracy"] = {
+        "e_g2_max_rel": e_g2, "g2_pixels": 256, "e_beta_max_rel": e_b, "beta_rings": k["rings_pick"],
+        "against": "oracle g2 and beta of the same series (stage parity)"}
+
+
 def run_ours(args):
     import torch
 
@@ -302,7 +500,7 @@ def run_ours(args):
     achieved = alg_flops / (tc_launch_ms * 1e-3) / 1e12
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": _tc_traffic(T),
-                "traffic_note": "ncu DRAM bytes (read + write) of the 1,000-frame launch; "
+                "traffic_note": "ncu DRAM bytes (read + write) of a 160-frame launch, scaled by frames; "
                                 "algorithmic bytes per launch = T x (N x 16 B records + P x 4 B)",
                 "algorithmic_bytes": float(T) * (N * 16.0 + P * 4.0),
                 "kernel": "tc_kernel (split-FP16 contraction)", "kernel_ms_per_launch": tc_launch_ms,
@@ -576,6 +774,13 @@ def run_ours(args):
         del trajs, outs
         torch.cuda.empty_cache()
 
+    # ---- the 4,000-atom workload on the FP32 path and the 3.2-million-atom
+    # crystal (512^2 plane streamed from host memory, 128^3 volume, g2 and XSVS
+    # at 10,000 frames of 512^2) ------------------------------------------------
+    cfg_keep = {}
+    if not args.no_configs and rank == 0:
+        line["configs"], cfg_keep = config_entries(xs, ctx, stream, _peaks())
+
     # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N = 1) ----
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         import oracle
@@ -630,8 +835,10 @@ def run_ours(args):
                                                "sample": f"frame 0, {sel1.size} pixels (every 32nd)"}
         t0c, g0 = wl.config0()
         t0 = time.perf_counter()
-        oracle.intensity(t0c.pos, t0c.f, t0c.box, g0.miller())
+        ref0 = oracle.intensity(t0c.pos, t0c.f, t0c.box, g0.miller())
         dt0 = time.perf_counter() - t0
+        if cfg_keep:
+            config_accuracy(line["configs"], cfg_keep, ref0)
         line["cpu_baseline"]["config_4000_atoms_full"] = {
             "value": t0c.n_atoms * g0.n_pixels * t0c.pos.shape[0] / dt0, "unit": METRIC, "seconds": dt0,
             "workload": "4,000 atoms, 10 frames, 64^2 plane, all host cores"}
