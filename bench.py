@@ -635,6 +635,7 @@ def run_ours(args):
         ctx.sync_status()
         return e0.elapsed_time(e1) / reps
 
+    keep_tables = {}
     if not args.no_next and rank == 0:
         nf = min(100, T)
         sub = pos_d[:nf].contiguous()
@@ -658,8 +659,22 @@ def run_ours(args):
         _, Fh = xs.isf(amp, list(range(Kmax)), sum_f2)
         t_cf = ms_per_call(lambda: xs.contrast_from_isf(Fh, grid, box, Ks, R))
         pairs = float(P) * sum(T - t for t in taus)
+        # the FP64 table builder (every entry from sincospi of its exact turn
+        # count) against the default seeds and rotations, same 100 frames
+        ctx.set_table_builder(True)
+        try:
+            t_ex = ms_per_call(lambda: xs.intensity(sub, f_d, box, grid, args.precision))
+            I_ex100 = xs.intensity(sub[:1].contiguous(), f_d, box, grid, args.precision).reshape(-1).cpu()
+        finally:
+            ctx.set_table_builder(False)
+        I_rec100 = xs.intensity(sub[:1].contiguous(), f_d, box, grid, args.precision).reshape(-1).cpu()
+        keep_tables.update(exact=I_ex100.numpy(), rec=I_rec100.numpy())
         line["next_rows"] = {
             "frames": nf,
+            "table_builders": {"recurrence_ms_per_call": t_plane, "fp64_sincospi_ms_per_call": t_ex,
+                               "slowdown": t_ex / t_plane,
+                               "what": "default: FP32 seeds and rotations per run of n; option: FP64 sincospi "
+                                       "of every entry's exact turn count"},
             "plane_reference": {"value": plane_units / (t_plane * 1e-3), "unit": METRIC, "ms_per_call": t_plane},
             "species_form_factors": {"value": plane_units / (t_sp * 1e-3), "unit": METRIC, "ms_per_call": t_sp,
                                      "species": 2, "coefficients": "synthetic four-Gaussian sums"},
@@ -818,6 +833,12 @@ def run_ours(args):
         okr = cref >= 8
         bk = beta_k.cpu().numpy()
         e_beta = float(np.max(np.abs(bk[:, okr] - bref[:, okr]) / np.abs(bref[:, okr])))
+        if keep_tables:
+            # frame 0 from both table builders against the same oracle sample
+            tb = line["next_rows"]["table_builders"]
+            for name in ("rec", "exact"):
+                gv = keep_tables[name].astype(np.float64)[sel]
+                tb[f"e_I_frame0_{name}"] = float(np.linalg.norm(gv[nz] - ref[0, nz]) / np.linalg.norm(ref[0, nz]))
         line["accuracy"] = {
             "e_I_frame0": e_I, "e_pix_frame0": e_pix, "max_abs_dI_over_mean_frame0": mean_dev,
             "e_g2": e_g2, "e_g2_max_rel_bright": e_g2_pix, "g2_pixels": int(nzg.sum()),

@@ -410,6 +410,17 @@ XS_API const char* xs_last_error(void);
  * XS_ERR_TIMEOUT, XS_ERR_NUMERIC or XS_OK. */
 XS_API xs_status xs_sync_status(xs_context* ctx, void* cuda_stream);
 
+/* Table builder of the split-precision (tensor-core) paths, a test and
+ * measurement option of this library (Sec. 3.1 fixes only what the tables
+ * hold, exp(i 2 pi n s) per atom and index).  mode 0 (the default): each
+ * producer thread evaluates a seed exp(i 2 pi n0 U / 2^32) and
+ * exp(i 2 pi U / 2^32) of exact 32-bit turn counts U in FP32 and advances
+ * along n by complex multiplication; mode 1: every entry is sincospi of its
+ * exact turn count n U mod 2^32 in FP64, rounded once to FP32 (and the B
+ * side's weight f E_z in FP64), which makes the contraction several times
+ * slower.  The choice holds for later calls on the context. */
+XS_API xs_status xs_set_table_builder(xs_context* ctx, int32_t mode);
+
 /* Debug knob: the bounded waits inside the tensor-core kernel give up after
  * `ns` nanoseconds (default 2e9).  Used by tests to force a timeout on a
  * kernel whose wait can never complete. */

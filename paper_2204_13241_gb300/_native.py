@@ -21,7 +21,7 @@ EXPORTS = ["xs_context_create", "xs_context_destroy", "xs_intensity", "xs_intens
            "xs_sync_status", "xs_set_wait_timeout_ns", "xs_version", "xs_profile_enable", "xs_profile_read",
            "xs_launch_count", "xs_intensity_fp32_static", "xs_isf", "xs_contrast_from_isf", "xs_intensity_species",
            "xs_intensity_points", "xs_ewald_points", "xs_intensity_fft", "xs_xsvs_partial", "xs_xsvs_finalize",
-           "xs_xpcs_batched", "xs_tuned_choice"]
+           "xs_xpcs_batched", "xs_tuned_choice", "xs_set_table_builder"]
 
 
 class XsError(RuntimeError):
@@ -92,6 +92,7 @@ def load() -> ctypes.CDLL:
         "xs_last_error": ([], ctypes.c_char_p),
         "xs_sync_status": ([P, P], st),
         "xs_set_wait_timeout_ns": ([P, I64], st),
+        "xs_set_table_builder": ([P, I32], st),
         "xs_version": ([], ctypes.c_char_p),
         "xs_profile_enable": ([P, I32], st),
         "xs_profile_read": ([P, ctypes.c_char_p, ctypes.POINTER(D), ctypes.POINTER(I64)], st),

@@ -100,6 +100,11 @@ class Context:
     def set_wait_timeout_ns(self, ns: int) -> None:
         nat.check(self.lib.xs_set_wait_timeout_ns(self.handle, int(ns)))
 
+    def set_table_builder(self, exact: bool) -> None:
+        """False: tensor-core tables from FP32 seeds and rotations (default);
+        True: every entry from FP64 sincospi of its exact turn count."""
+        nat.check(self.lib.xs_set_table_builder(self.handle, 1 if exact else 0))
+
     def profile(self, on: bool) -> None:
         """Bracket every launch group with CUDA events on its stream."""
         nat.check(self.lib.xs_profile_enable(self.handle, 1 if on else 0))

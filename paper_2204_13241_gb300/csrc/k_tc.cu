@@ -339,6 +339,22 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
+// The FP64 table builder (a test and measurement option): w exp(i 2 pi P / 2^32)
+// from sincospi of the exact turn count in FP64, rounded once to FP32; w is
+// the B side's weight f E_z (1 on the A side), also in FP64.
+__device__ __forceinline__ float2 cis_exact(uint32_t P, double2 w) {
+    double s, c;
+    sincospi((double)P * 4.656612873077392578125e-10, &s, &c);  // 2^-31
+    return make_float2((float)(c * w.x - s * w.y), (float)(c * w.y + s * w.x));
+}
+
+// entries n and n + 1 of a run as (Re n, Re n+1) and (Im n, Im n+1)
+__device__ __forceinline__ void exact_pair(uint32_t n, uint32_t U, double2 w, float2& R, float2& Im) {
+    const float2 a = cis_exact(n * U, w), b = cis_exact((n + 1u) * U, w);
+    R = make_float2(a.x, b.x);
+    Im = make_float2(a.y, b.y);
+}
+
 // byte offset of the 16-byte chunk holding MN rows [mn, mn+8) of K row k
 __device__ __forceinline__ uint32_t chunk_off(int mn, int k) {
     return (uint32_t)(mn >> 6) * kMNBlockBytes + (uint32_t)(k >> 3) * 1024u + (uint32_t)(k & 7) * 128u +
@@ -470,7 +486,7 @@ __global__ void split_finish_kernel(TcArgs a, int64_t n_pairs) {
     }
 }
 
-template <bool BF16, int KIND>
+template <bool BF16, int KIND, bool EXACT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads, 1) tc_kernel(TcArgs args) {
     using C = Cfg<KIND>;
     using L = Lay<KIND>;
@@ -571,6 +587,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
                 const float2 NZI = make_float2(-z2.y, -z2.y);
                 float2 Ex = make_float2(0.0f, 0.0f);
                 if (extra) Ex = cis_turns((uint32_t)(32 * (int)rank + 32) * U, ctl->tab);
+                double2 wd = make_double2(1.0, 0.0);  // the FP64 builder's weight
                 if (!is_a) {
                     const float f = __uint_as_float(r.w);
                     float2 wv = make_float2(f, 0.0f);
@@ -581,6 +598,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
                     E0 = cmul(E0, wv);
                     E1 = cmul(E1, wv);
                     Ex = cmul(Ex, wv);
+                    if constexpr (EXACT) {
+                        wd = make_double2((double)f, 0.0);
+                        if (nz != 0u) {
+                            double se, ce;
+                            sincospi((double)(nz * r.z) * 4.656612873077392578125e-10, &se, &ce);
+                            wd = make_double2((double)f * ce, (double)f * se);
+                        }
+                    }
+                }
+                if constexpr (EXACT) {
+                    if (extra) Ex = cis_exact((uint32_t)(32 * (int)rank + 32) * U, wd);
                 }
                 float2 R = make_float2(E0.x, E1.x);   // Re of (n, n+1)
                 float2 Im = make_float2(E0.y, E1.y);  // Im of (n, n+1)
@@ -599,11 +627,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
                         uint32_t h[4], l[4];
 #pragma unroll
                         for (int q = 0; q < 2; ++q) {
+                            if constexpr (EXACT) exact_pair(n0 + 4u * g + 2u * q, U, wd, R, Im);
                             split2<BF16>(R, h[2 * q], l[2 * q]);
                             split2<BF16>(Im, h[2 * q + 1], l[2 * q + 1]);
-                            const float2 Rn = __ffma2_rn(R, ZR, __fmul2_rn(Im, NZI));
-                            Im = __ffma2_rn(R, ZI, __fmul2_rn(Im, ZR));
-                            R = Rn;
+                            if constexpr (!EXACT) {
+                                const float2 Rn = __ffma2_rn(R, ZR, __fmul2_rn(Im, NZI));
+                                Im = __ffma2_rn(R, ZI, __fmul2_rn(Im, ZR));
+                                R = Rn;
+                            }
                         }
                         const uint32_t off = chunk_off(2 * (s0 + 4 * g), k);
                         st_shared_v4(hi_base + off, h[0], h[1], h[2], h[3]);
@@ -626,11 +657,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
                         uint32_t h[4], l[4];
 #pragma unroll
                         for (int q = 0; q < 2; ++q) {
+                            if constexpr (EXACT) exact_pair(n0 + 4u * g + 2u * q, U, wd, R, Im);
                             split2<BF16>(R, h[2 * q], l[2 * q]);
                             split2<BF16>(Im, h[2 * q + 1], l[2 * q + 1]);
-                            const float2 Rn = __ffma2_rn(R, ZR, __fmul2_rn(Im, NZI));
-                            Im = __ffma2_rn(R, ZI, __fmul2_rn(Im, ZR));
-                            R = Rn;
+                            if constexpr (!EXACT) {
+                                const float2 Rn = __ffma2_rn(R, ZR, __fmul2_rn(Im, NZI));
+                                Im = __ffma2_rn(R, ZI, __fmul2_rn(Im, ZR));
+                                R = Rn;
+                            }
                         }
                         const uint32_t off = chunk_off(2 * (run0 + 4 * g), k);
                         st_shared_v4(hi_base + off, h[0], h[1], h[2], h[3]);
@@ -877,9 +911,9 @@ static int pair_capacity_of(int num_sms) {
     static int max_pairs = -1;
     if (max_pairs < 0) {
         using L = Lay<KIND>;
-        cudaFuncSetAttribute((const void*)tc_kernel<false, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute((const void*)tc_kernel<false, KIND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)L::kSmemBytes);
-        cudaFuncSetAttribute((const void*)tc_kernel<true, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute((const void*)tc_kernel<true, KIND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)L::kSmemBytes);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(2 * (unsigned)std::max(1, num_sms / 2), 1, 1);
@@ -893,7 +927,8 @@ static int pair_capacity_of(int num_sms) {
         cfg.attrs = &attr;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, (const void*)tc_kernel<false, KIND>, &cfg) != cudaSuccess || n < 1) {
+        if (cudaOccupancyMaxActiveClusters(&n, (const void*)tc_kernel<false, KIND, false>, &cfg) != cudaSuccess ||
+            n < 1) {
             cudaGetLastError();
             n = std::max(1, num_sms / 2);
         }
@@ -909,8 +944,9 @@ int tc_pair_capacity(int num_sms, int kind) {
 int tc_default_kind(const GridDesc& g) { return g.ny <= 64 ? kTcTile64 : kTcTile128; }
 
 TcTraj tc_traj(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g, float* I, float* amp, int kind,
-               int chunk) {
+               int chunk, bool exact) {
     TcTraj t;
+    t.exact = exact ? 1 : 0;
     t.kind = kind == kTcTile64 ? kTcTile64 : kTcTile128;
     t.chunk = chunk;
     t.rec = reinterpret_cast<const uint4*>(rec);
@@ -978,21 +1014,28 @@ void tc_deal_units(const std::vector<TcTraj>& trajs, const std::vector<int4>& al
     pair_start[n_pairs] = (int)units.size();
 }
 
-template <bool BF16, int KIND>
+template <bool BF16, int KIND, bool EXACT>
 static cudaError_t launch_kind(const TcArgs& a, int n_pairs, cudaStream_t st) {
     using L = Lay<KIND>;
-    const void* fn = (const void*)tc_kernel<BF16, KIND>;
+    const void* fn = (const void*)tc_kernel<BF16, KIND, EXACT>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kSmemBytes);
     if (e != cudaSuccess) return e;
     ++tl_kernel_launches;
-    tc_kernel<BF16, KIND><<<2 * n_pairs, L::kThreads, L::kSmemBytes, st>>>(a);
+    tc_kernel<BF16, KIND, EXACT><<<2 * n_pairs, L::kThreads, L::kSmemBytes, st>>>(a);
     return cudaGetLastError();
 }
 
-static cudaError_t launch(const TcArgs& a, int n_pairs, bool bf16, int kind, cudaStream_t st) {
+template <bool EXACT>
+static cudaError_t launch_exact(const TcArgs& a, int n_pairs, bool bf16, int kind, cudaStream_t st) {
     if (kind == kTcTile64)
-        return bf16 ? launch_kind<true, kTcTile64>(a, n_pairs, st) : launch_kind<false, kTcTile64>(a, n_pairs, st);
-    return bf16 ? launch_kind<true, kTcTile128>(a, n_pairs, st) : launch_kind<false, kTcTile128>(a, n_pairs, st);
+        return bf16 ? launch_kind<true, kTcTile64, EXACT>(a, n_pairs, st)
+                    : launch_kind<false, kTcTile64, EXACT>(a, n_pairs, st);
+    return bf16 ? launch_kind<true, kTcTile128, EXACT>(a, n_pairs, st)
+                : launch_kind<false, kTcTile128, EXACT>(a, n_pairs, st);
+}
+
+static cudaError_t launch(const TcArgs& a, int n_pairs, bool bf16, int kind, bool exact, cudaStream_t st) {
+    return exact ? launch_exact<true>(a, n_pairs, bf16, kind, st) : launch_exact<false>(a, n_pairs, bf16, kind, st);
 }
 
 TcSplit tc_split_plan(int64_t units, int n_pairs, int n_stages, int chunk_stages) {
@@ -1052,7 +1095,7 @@ cudaError_t launch_tc_single(const TcTraj& tr, int n_pairs, const TcSplit& sp, i
     }
     const int64_t pieces = sp.full * n_pairs + sp.rem * sp.parts;
     n_pairs = (int)std::min<int64_t>(n_pairs, pieces);
-    return launch(a, n_pairs, bf16, tr.kind, st);
+    return launch(a, n_pairs, bf16, tr.kind, tr.exact != 0, st);
 }
 
 cudaError_t launch_tc_split_finish(const TcTraj& tr, int n_pairs, const TcSplit& sp, void* split_buf,
@@ -1073,8 +1116,8 @@ cudaError_t launch_tc_split_finish(const TcTraj& tr, int n_pairs, const TcSplit&
 }
 
 cudaError_t launch_tc_batch(const TcTraj* d_trajs, const int4* d_units, const int* d_pair_start, int n_pairs,
-                            int chunk_stages, bool bf16, int kind, double* scratch, int* err, int64_t timeout_ns,
-                            cudaStream_t st) {
+                            int chunk_stages, bool bf16, int kind, bool exact, double* scratch, int* err,
+                            int64_t timeout_ns, cudaStream_t st) {
     TcArgs a{};
     a.trajs = d_trajs;
     a.units = d_units;
@@ -1083,7 +1126,7 @@ cudaError_t launch_tc_batch(const TcTraj* d_trajs, const int4* d_units, const in
     a.scratch = scratch;
     a.err = err;
     a.timeout_ns = timeout_ns;
-    return launch(a, n_pairs, bf16, kind, st);
+    return launch(a, n_pairs, bf16, kind, exact, st);
 }
 
 }  // namespace xs

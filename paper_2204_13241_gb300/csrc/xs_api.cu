@@ -124,6 +124,7 @@ struct xs_context {
         int chunk;
     };
     std::map<std::tuple<int, int, int, int, int>, TcChoice> tuned;
+    bool exact_tables = false;  // tensor-core tables from FP64 sincospi per entry
     // small device-side tables, one slot per caller tag, re-uploaded only
     // when their content changes (so repeated calls enqueue no host copies)
     struct ConstSlot {
@@ -330,6 +331,12 @@ xs_status xs_context_destroy(xs_context* ctx) {
     }
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     delete ctx;
+    return XS_OK;
+}
+
+xs_status xs_set_table_builder(xs_context* ctx, int32_t mode) {
+    if (!ctx || (mode != 0 && mode != 1)) return fail(XS_ERR_INVALID_ARG, "table builder mode is 0 or 1");
+    ctx->exact_tables = mode == 1;
     return XS_OK;
 }
 
@@ -561,7 +568,7 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
             if (use_tc) {
                 float* Ih = half_axis >= 0 ? reinterpret_cast<float*>(ws + o_half) : Ic;
                 float* Ah = half_axis >= 0 ? (Ac ? reinterpret_cast<float*>(ws + o_half_amp) : nullptr) : Ac;
-                const TcTraj tr = tc_traj(rec, n_pad, nf, gc, Ih, Ah, tile_kind);
+                const TcTraj tr = tc_traj(rec, n_pad, nf, gc, Ih, Ah, tile_kind, 0, ctx->exact_tables);
                 const TcSplit sp = split_of(nf);
                 XS_CUDA(traced(ctx, "tc", st, [&] {
                     return launch_tc_single(tr, tc_pairs, sp, chunk_stages, prec == XS_PREC_SPLIT_BF16,
@@ -849,7 +856,7 @@ xs_status xs_intensity_points(xs_context* ctx, const xs_traj* traj, const int32_
         std::vector<TcTraj> trs;
         for (const Plane& pl : planes) {
             GridDesc g{pl.x0, pl.x1 - pl.x0 + 1, pl.y0, pl.y1 - pl.y0 + 1, pl.z, 1};
-            TcTraj tr = tc_traj(rec, n_pad, nf, g, nullptr, nullptr);
+            TcTraj tr = tc_traj(rec, n_pad, nf, g, nullptr, nullptr, kTcTile128, 0, ctx->exact_tables);
             // each plane writes its own [nf][box] block of the temporary buffer
             tr.I = tmp + (size_t)nf * pl.off;
             tr.amp = tamp ? tamp + (size_t)nf * pl.off * 2 : nullptr;
@@ -897,7 +904,7 @@ xs_status xs_intensity_points(xs_context* ctx, const xs_traj* traj, const int32_
         XS_CUDA(traced(ctx, "tc", st, [&] {
             return launch_tc_batch(reinterpret_cast<const TcTraj*>(dc + o_tr), reinterpret_cast<const int4*>(dc + o_units),
                                    reinterpret_cast<const int*>(dc + o_ps), n_pairs, kDefaultChunkStages, prec == XS_PREC_SPLIT_BF16,
-                                   kTcTile128,
+                                   kTcTile128, ctx->exact_tables,
                                    reinterpret_cast<double*>(ws + o_part), ctx->d_err, ctx->timeout_ns, st);
         }));
         XS_CUDA(traced(ctx, "points", st, [&] {
@@ -1047,7 +1054,7 @@ xs_status xs_intensity_species(xs_context* ctx, const xs_traj* traj, const int32
             if (use_tc) {
                 const xs_context::TcChoice ch = choice_of(n_pad);
                 const int pairs = tc_pair_capacity(ctx->num_sms, ch.kind);
-                const TcTraj tr = tc_traj(rec, n_pad, nf, g, I_tmp, S_tmp, ch.kind);
+                const TcTraj tr = tc_traj(rec, n_pad, nf, g, I_tmp, S_tmp, ch.kind, 0, ctx->exact_tables);
                 const TcSplit spl = split_of(n_pad, nf);
                 XS_CUDA(traced(ctx, "tc", st, [&] {
                     return launch_tc_single(tr, pairs, spl, ch.chunk, prec == XS_PREC_SPLIT_BF16,
@@ -1655,10 +1662,10 @@ static xs_status batched_impl(xs_context* ctx, const xs_traj* traj, const xs_qgr
         }
         if (j.half_axis >= 0)
             trs.push_back(tc_traj(reinterpret_cast<AtomRec*>(ws + j.rec_off), j.n_pad, j.T, j.v,
-                                  reinterpret_cast<float*>(ws + j.half_off), nullptr, kind, chunk));
+                                  reinterpret_cast<float*>(ws + j.half_off), nullptr, kind, chunk, ctx->exact_tables));
         else
             trs.push_back(tc_traj(reinterpret_cast<AtomRec*>(ws + j.rec_off), j.n_pad, j.T, j.g, I_out[i], nullptr,
-                                  kind, chunk));
+                                  kind, chunk, ctx->exact_tables));
     }
     for (const TcTraj& t : trs) total_units += tc_units(t);
     for (int i : empty)
@@ -1724,8 +1731,8 @@ static xs_status batched_impl(xs_context* ctx, const xs_traj* traj, const xs_qgr
             err = launch_tc_batch(reinterpret_cast<const TcTraj*>(dc + o_tr),
                                   reinterpret_cast<const int4*>(dc + kls[k].o_units),
                                   reinterpret_cast<const int*>(dc + kls[k].o_ps), kls[k].n_pairs, chunk, bf16,
-                                  kls[k].kind, reinterpret_cast<double*>(ws + o_scratch), ctx->d_err, ctx->timeout_ns,
-                                  st);
+                                  kls[k].kind, ctx->exact_tables, reinterpret_cast<double*>(ws + o_scratch),
+                                  ctx->d_err, ctx->timeout_ns, st);
         for (size_t e = 0; e < trs.size() && err == cudaSuccess; ++e) {
             const Job& j = jobs[(size_t)which[e]];
             if (j.half_axis >= 0)

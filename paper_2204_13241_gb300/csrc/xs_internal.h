@@ -81,12 +81,13 @@ struct TcTraj {
     int n_frames;
     int kind;      // tile kind (all trajectories of one launch share it)
     int chunk;     // stages per FP32 accumulation chunk; 0: the launch's
+    int exact;     // 1: tables from FP64 sincospi per entry (test and measurement option)
 };
 bool tc_supported(const GridDesc& g);
 int64_t tc_atom_multiple();
 int tc_pair_capacity(int num_sms, int kind = kTcTile128);  // co-resident CTA pairs
 TcTraj tc_traj(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g, float* I, float* amp,
-               int kind = kTcTile128, int chunk = 0);
+               int kind = kTcTile128, int chunk = 0, bool exact = false);
 // tile kind for a (contracted) grid when nothing was tuned: 128 x 64 tiles
 // where they need no more tiles than 128 x 128 ones (n_y extent <= 64)
 int tc_default_kind(const GridDesc& g);
@@ -120,8 +121,8 @@ cudaError_t launch_tc_single(const TcTraj& tr, int n_pairs, const TcSplit& sp, i
 cudaError_t launch_tc_split_finish(const TcTraj& tr, int n_pairs, const TcSplit& sp, void* split_buf,
                                    cudaStream_t st);
 cudaError_t launch_tc_batch(const TcTraj* d_trajs, const int4* d_units, const int* d_pair_start, int n_pairs,
-                            int chunk_stages, bool bf16, int kind, double* scratch, int* err, int64_t timeout_ns,
-                            cudaStream_t st);
+                            int chunk_stages, bool bf16, int kind, bool exact, double* scratch, int* err,
+                            int64_t timeout_ns, cudaStream_t st);
 
 // ---- g2 -----------------------------------------------------------------
 int g2_segments(int64_t T);
