@@ -67,6 +67,10 @@ def _args():
     ap.add_argument("--no-table1", action="store_true")
     ap.add_argument("--no-next", action="store_true", help="skip the ISF, Ewald-slice and species timings")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing on its own workload")
+    ap.add_argument("--shard", choices=["replicas", "pixels"], default="replicas",
+                    help="with several GPUs: every rank runs its own replica (default, weak scaling), or the "
+                         "ranks split the detector's n_y rows (strong scaling: I and g2 local, XSVS window sums "
+                         "all-reduced)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the 4,000-atom FP32 and the 3.2-million-atom crystal entries")
     return ap.parse_args()
@@ -170,6 +174,27 @@ def job_value(units_per_rank: float, world: int, ms: float) -> float:
     """Whole-job throughput: every rank runs its own replica of the workload
     (weak scaling), so the job processes world x units in the slowest rank's time."""
     return units_per_rank * world / (ms * 1e-3)
+
+
+def shard_rows(n: int, rank: int, world: int) -> tuple[int, int]:
+    """Contiguous split of n rows over the ranks: (first row, rows) of `rank`;
+    the first n % world ranks take one row more."""
+    base, extra = divmod(n, world)
+    start = rank * base + min(rank, extra)
+    return start, base + (1 if rank < extra else 0)
+
+
+def shard_grid(grid, rank: int, world: int):
+    """A rank's slab of a detector plane: its n_y rows, all n_x.  With x
+    fastest in the pixel order, the slab is the contiguous pixel range
+    [offset, offset + count) of the whole plane.  Returns (slab, offset,
+    count)."""
+    from paper_2204_13241_gb300.workloads import QGrid
+
+    if grid.nz != 1:
+        raise ValueError("pixel shards are slabs of a plane")
+    s, c = shard_rows(grid.ny, rank, world)
+    return QGrid(grid.nx0, grid.nx, grid.ny0 + s, c, grid.nz0, 1), s * grid.nx, c * grid.nx
 
 
 def run_reference(args):
@@ -406,6 +431,9 @@ def run_ours(args):
     world, rank, local = _dist()
     if world > 1:
         import torch.distributed as dist
+        # NCCL's initialisation log names the communicator's ranks
+        os.environ.setdefault("NCCL_DEBUG", "INFO")
+        os.environ.setdefault("NCCL_DEBUG_SUBSYS", "INIT")
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     else:
@@ -441,13 +469,29 @@ def run_ours(args):
     box = traj.box
     pos_d = torch.from_numpy(traj.pos).to(f"cuda:{dev}")
     f_d = torch.from_numpy(traj.f).to(f"cuda:{dev}")
-    I = torch.empty((T, 1, grid.ny, grid.nx), dtype=torch.float32, device="cuda")
     ctx = xs.Context.get()
+    sharded = args.shard == "pixels"
+    if sharded:
+        # this rank's n_y rows; every rank knows the whole ring layout, so
+        # only the XSVS window sums are exchanged
+        grid_r, p_off, p_cnt = shard_grid(grid, rank, world)
+        ring_full = xs.ring_index(grid, box, 1.0, R)
+        ring_r = ring_full[p_off:p_off + p_cnt]
+        counts_full = np.bincount(ring_full, minlength=R + 1)[1:].astype(np.int64)
+    else:
+        grid_r, p_off, p_cnt = grid, 0, P
+    I = torch.empty((T, 1, grid_r.ny, grid_r.nx), dtype=torch.float32, device="cuda")
 
     def step(pos, f):
-        xs.intensity(pos, f, box, grid, args.precision, out=I)
+        xs.intensity(pos, f, box, grid_r, args.precision, out=I)
         g, mean = xs.g2(I.view(T, -1), taus)
-        beta, counts = xs.xsvs_contrast(I, grid, box, Ks, R)
+        if not sharded:
+            beta, counts = xs.xsvs_contrast(I, grid, box, Ks, R)
+            return g, mean, beta
+        sums, _ = xs.xsvs_partial(I.view(T, -1), ring_r, R, Ks)
+        if dist is not None:
+            dist.all_reduce(sums)
+        beta = xs.xsvs_finalize(sums, counts_full, T, Ks)
         return g, mean, beta
 
     for _ in range(max(args.warmup, 1)):
@@ -489,8 +533,10 @@ def run_ours(args):
     ctx.sync_status()
     ms = ev0.elapsed_time(ev1) / args.steps
     ms = max_over_ranks(ms)
-    units = float(N) * P * T
-    value = job_value(units, world, ms)
+    units = float(N) * p_cnt * T          # this rank's atom*pixel*frames per step
+    # replicas: every rank's units count; pixel shards: the ranks together do
+    # the plane once per step
+    value = job_value(units, world, ms) if not sharded else float(N) * P * T / (ms * 1e-3)
 
     peaks, peak_src = _peaks()
     tc_launch_ms = tc_ms / max(tc_n, 1)
@@ -510,27 +556,58 @@ def run_ours(args):
                 "share_of_step": tc_ms / max(tc_ms + all_ms, 1e-9)}
 
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong" if sharded else "weak",
             "vs_baseline": None, "dtype": "f16-split (hi+lo), f32 accumulate", "data": "synthetic",
             "config": {"workload": "fcc256k_T1000_plane128", "n_atoms": N, "n_frames": T,
                        "grid": f"{grid.nx}x{grid.ny} (n_z=0)", "precision": f"split_{args.precision}",
                        "n_tau": len(taus), "window_lengths": Ks, "rings": R,
                        "l2": "inputs larger than L2 (3.1 GB positions + 4.1 GB phase records read per step)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": (f"pixel shards x{world} (n_y rows, XSVS sums all-reduced)" if sharded
+                                       else f"replicas x{world}")},
             "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
             "stage_ms_per_step": {k: round(v, 4) for k, v in breakdown.items()}}
+
+    # ---- pixel shards: the same plane on one GPU gives the same g2 and beta
+    if sharded:
+        g_sh, _, b_sh = res
+        I_full = xs.intensity(pos_d, f_d, box, grid, args.precision)
+        g_full, _ = xs.g2(I_full.view(T, -1), taus)
+        b_full, _ = xs.xsvs_contrast(I_full, grid, box, Ks, R)
+        ctx.sync_status()
+        g_ref = g_full[:, p_off:p_off + p_cnt].cpu().numpy()
+        b_ref = b_full.cpu().numpy()
+        okr = counts_full >= 8
+        d_g = float(np.max(np.abs(g_sh.cpu().numpy() - g_ref) / np.abs(g_ref)))
+        d_b = float(np.max(np.abs(np.asarray(b_sh)[:, okr] - b_ref[:, okr]) / np.abs(b_ref[:, okr])))
+        d_g, d_b = max_over_ranks(d_g), max_over_ranks(d_b)
+        line["shard_check"] = {
+            "g2_max_rel_vs_one_gpu": d_g, "beta_max_rel_vs_one_gpu": d_b,
+            "note": "each rank's g2 of its rows and the all-reduced beta against the whole plane computed on "
+                    "the rank's own GPU; a slab's tile layout differs from the plane's, so the FP32 "
+                    "accumulation differs in the last bits"}
+        del I_full
 
     # ---- end to end through the public API with host buffers ------------------
     if not args.no_e2e:
         pos_h = torch.from_numpy(traj.pos).pin_memory()
         f_h = torch.from_numpy(traj.f).pin_memory()
         I_h = torch.empty(I.shape, dtype=torch.float32).pin_memory()
-        g_h = torch.empty((len(taus), P), dtype=torch.float64).pin_memory()
+        g_h = torch.empty((len(taus), p_cnt), dtype=torch.float64).pin_memory()
         b_h = torch.empty((len(Ks), R), dtype=torch.float64).pin_memory()
 
         side = torch.cuda.Stream()
 
         def e2e_step():
+            if sharded:
+                # pixel shards: this rank's rows streamed from host positions;
+                # beta arrives on the host through the finalize
+                g, _, beta = step(pos_h, f_h)
+                I_h.copy_(I, non_blocking=True)
+                g_h.copy_(g, non_blocking=True)
+                b_h.copy_(torch.from_numpy(np.asarray(beta)))
+                torch.cuda.current_stream().synchronize()
+                return
             xs.intensity(pos_h, f_h, box, grid, args.precision, out=I)
             # the intensity goes back to the host on a side stream while g2
             # and the contrast run; the next step waits for it before it
@@ -556,7 +633,10 @@ def run_ours(args):
         ctx.sync_status()
         h2d = traj.pos.nbytes + traj.f.nbytes
         d2h = I_h.numel() * 4 + g_h.numel() * 8 + b_h.numel() * 8
-        line["e2e"] = {"value": job_value(units, world, e_ms), "unit": METRIC, "ms_per_step": e_ms,
+        if sharded:
+            d2h += sum(T // k for k in Ks) * R * 2 * 8   # the all-reduced window sums read by the finalize
+        e_val = job_value(units, world, e_ms) if not sharded else float(N) * P * T / (e_ms * 1e-3)
+        line["e2e"] = {"value": e_val, "unit": METRIC, "ms_per_step": e_ms,
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
         del pos_h
 

@@ -138,3 +138,68 @@ def test_two_gloo_ranks_shard_pixels_for_xsvs_and_finalize_in_the_library():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert all(ok for _, ok in out), out
+
+
+def _bench_shard_rank_main(rank, world, port, q):
+    # the orchestration of `bench.py --shard pixels` with the GPU work replaced
+    # by host sums: slabs of n_y rows, the whole ring layout on every rank,
+    # the window sums all-reduced and finalized by the library
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_2204_13241_gb300 import api as xs
+    from paper_2204_13241_gb300 import workloads as wl
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        grid = wl.centered_plane(24)
+        box = np.eye(3) * 30.0
+        R = wl.rings_for_plane(grid)
+        T, Ks = 30, [1, 2, 5, 10, 30]
+        rng = np.random.default_rng(11)                   # every rank draws the same series
+        I = rng.exponential(size=(T, grid.n_pixels))
+        slab, off, cnt = bench.shard_grid(grid, rank, world)
+        m_full, m_slab = grid.miller(), slab.miller()
+        same_pixels = bool(np.array_equal(m_full[off:off + cnt], m_slab))
+        ring_full = xs.ring_index(grid, box, 1.0, R)
+        ring_r = ring_full[off:off + cnt]
+        counts_full = np.bincount(ring_full, minlength=R + 1)[1:].astype(np.int64)
+        sums, _ = _shard_sums(I[:, off:off + cnt], ring_r, R, Ks)
+        ts = torch.from_numpy(sums)
+        dist.all_reduce(ts)
+        beta = xs.xsvs_finalize(ts.numpy(), counts_full, T, Ks)
+        ref, cref = oracle.xsvs_contrast(I, Ks, oracle.ring_index(box, m_full, 1.0, R), R)
+        ok = bool(same_pixels and np.array_equal(counts_full, cref)
+                  and np.allclose(beta, ref, rtol=1e-12, atol=0, equal_nan=True))
+        q.put((rank, ok, cnt))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_bench_pixel_shards_on_two_gloo_ranks():
+    from paper_2204_13241_gb300 import build as xbuild
+    xbuild.build()
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_bench_shard_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert all(ok for _, ok, _ in out), out
+    assert sum(c for _, _, c in out) == 24 * 24
+
+
+def test_shard_rows_cover_every_row_once():
+    sys.path.insert(0, ROOT)
+    import bench
+    for n in (1, 7, 64, 128, 129):
+        for world in (1, 2, 3, 8):
+            parts = [bench.shard_rows(n, r, world) for r in range(world)]
+            assert sum(c for _, c in parts) == n
+            assert all(parts[i][0] + parts[i][1] == parts[i + 1][0] for i in range(world - 1))
+            assert max(c for _, c in parts) - min(c for _, c in parts) <= 1
