@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libxs.so")
 
 SOURCES = ["xs_api.cu", "xs_static.cu", "k_direct.cu", "k_corr.cu", "k_adjoint.cu", "k_adjoint_tc.cu", "k_tc.cu",
-           "k_species.cu", "k_fft.cu"]
+           "k_species.cu", "k_fft.cu", "k_factored.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

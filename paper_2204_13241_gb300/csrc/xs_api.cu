@@ -407,7 +407,8 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
     if (!ctx || !traj || !I_out) return fail(XS_ERR_INVALID_ARG, "context, trajectory and I_out are required");
     xs_status s = check_grid(grid);
     if (s != XS_OK) return s;
-    if (prec != XS_PREC_FP32_DIRECT && prec != XS_PREC_SPLIT_FP16 && prec != XS_PREC_SPLIT_BF16)
+    if (prec != XS_PREC_FP32_DIRECT && prec != XS_PREC_SPLIT_FP16 && prec != XS_PREC_SPLIT_BF16 &&
+        prec != XS_PREC_FP32_FACTORED)
         return fail(XS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
     if (traj->n_atoms < 0 || traj->n_frames < 0) return fail(XS_ERR_INVALID_ARG, "negative atom or frame count");
     if (traj->n_atoms > (int64_t)1 << 31) return fail(XS_ERR_INVALID_ARG, "more than 2^31 atoms");
@@ -419,7 +420,8 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
     const int64_t P = g.pixels();
     const int64_t T = traj->n_frames;
     if (P == 0 || T == 0) return XS_OK;
-    const bool use_tc = prec != XS_PREC_FP32_DIRECT;
+    const bool use_tc = prec == XS_PREC_SPLIT_FP16 || prec == XS_PREC_SPLIT_BF16;
+    const bool factored = prec == XS_PREC_FP32_FACTORED;
     if (use_tc && !tc_supported(g)) return fail(XS_ERR_UNSUPPORTED, "grid not supported by the tensor-core path");
 
     const bool out_dev = is_device_ptr(I_out) && (!amp_out || is_device_ptr(amp_out));
@@ -470,6 +472,7 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
     }
 
     DirectPlan dplan{};
+    FactoredPlan fplan{};
     int tc_pairs = 0;
     int chunk_stages = kDefaultChunkStages;
     int tile_kind = kTcTile128;
@@ -485,6 +488,8 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
         if (chunk_override > 0) chunk_stages = chunk_override;
         if (kind_override >= 0 && half_axis < 0) tile_kind = kind_override;
         tc_pairs = tc_pair_capacity(ctx->num_sms, tile_kind);
+    } else if (factored) {
+        fplan = plan_factored(n_pad, fchunk, g, ctx->num_sms);
     } else {
         dplan = plan_direct(n_pad, fchunk, g, ctx->num_sms);
     }
@@ -497,7 +502,8 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
         return o;
     };
     const size_t o_rec = carve((size_t)fchunk * rec_per_frame);
-    const size_t o_part = carve(use_tc ? tc_scratch_bytes(tc_pairs) : dplan.partial_bytes);
+    const size_t o_part =
+        carve(use_tc ? tc_scratch_bytes(tc_pairs) : (factored ? fplan.partial_bytes : dplan.partial_bytes));
     auto split_of = [&](int64_t nf) {
         return tc_split_plan(tc_units(tc_traj(nullptr, n_pad, nf, gc, nullptr, nullptr, tile_kind)), tc_pairs,
                              (int)(n_pad / tc_atom_multiple()), chunk_stages);
@@ -580,6 +586,11 @@ static xs_status intensity_impl(xs_context* ctx, const xs_traj* traj, const xs_q
                 if (half_axis >= 0)
                     XS_CUDA(traced(ctx, "friedel", st,
                                    [&] { return launch_friedel(Ih, Ah, nf, gh, g, half_axis, Ic, Ac, st); }));
+            } else if (factored) {
+                const FactoredPlan pc = plan_factored(n_pad, nf, g, ctx->num_sms);
+                if (pc.partial_bytes > fplan.partial_bytes) return fail(XS_ERR_CUDA, "internal: partial plan grew");
+                XS_CUDA(traced(ctx, "factored", st,
+                               [&] { return launch_factored(rec, n_pad, nf, g, pc, ws + o_part, Ic, Ac, st); }));
             } else {
                 DirectPlan pc = plan_direct(n_pad, nf, g, ctx->num_sms);
                 if (pc.partial_bytes > dplan.partial_bytes) return fail(XS_ERR_CUDA, "internal: partial plan grew");
@@ -1088,7 +1099,7 @@ xs_status xs_intensity_species(xs_context* ctx, const xs_traj* traj, const int32
 
 xs_status xs_tune(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, xs_precision prec, void* cuda_stream) {
     if (!ctx || !traj || !grid) return fail(XS_ERR_INVALID_ARG, "bad tune arguments");
-    if (prec == XS_PREC_FP32_DIRECT) return XS_OK;
+    if (prec == XS_PREC_FP32_DIRECT || prec == XS_PREC_FP32_FACTORED) return XS_OK;
     if (traj->pos_on_host) return fail(XS_ERR_INVALID_ARG, "tuning needs device positions");
     xs_status s = check_grid(grid);
     if (s != XS_OK) return s;
@@ -1556,7 +1567,7 @@ static cudaError_t corr_launch(const CorrPrep& cp, const xs_corr_request& r, con
 static xs_status batched_impl(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid, int32_t n_traj,
                               xs_precision prec, float* const* I_out, const xs_corr_request* req, cudaStream_t st) {
     if (!ctx || !traj || !grid || !I_out || n_traj < 1) return fail(XS_ERR_INVALID_ARG, "bad batched arguments");
-    if (prec == XS_PREC_FP32_DIRECT) {
+    if (prec == XS_PREC_FP32_DIRECT || prec == XS_PREC_FP32_FACTORED) {
         for (int32_t i = 0; i < n_traj; ++i) {
             if (traj[i].pos_on_host) return fail(XS_ERR_INVALID_ARG, "batched trajectories need device positions");
             xs_status s = intensity_impl(ctx, &traj[i], &grid[i], prec, I_out[i], nullptr, st, 0);

@@ -60,6 +60,16 @@ cudaError_t launch_direct(const AtomRec* rec, int64_t n_pad, int64_t n_frames, c
                           const DirectPlan& plan, void* partial, float* I, float* amp,
                           cudaStream_t st, const int32_t* pts = nullptr);
 
+// ---- factorised FP32 direct sum -------------------------------------------
+struct FactoredPlan {
+    int splits;            // atom ranges (FP64 partial amplitudes added in order by a second kernel)
+    int64_t atoms_per_split;
+    size_t partial_bytes;  // workspace for the partial amplitudes
+};
+FactoredPlan plan_factored(int64_t n_pad, int64_t n_frames, const GridDesc& g, int num_sms);
+cudaError_t launch_factored(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g,
+                            const FactoredPlan& plan, void* partial, float* I, float* amp, cudaStream_t st);
+
 // ---- tensor-core split-precision contraction ----------------------------
 // One trajectory of a launch: phase records [n_frames][n_pad] (slot order of
 // the phase kernel), outputs, and its grid; tiles are 128 x 128 pixels.

@@ -18,8 +18,8 @@ the FP32 path; the bounds leave a factor of three and seven.
 """
 import numpy as np
 
-NORM_TOL = {"fp32": 1e-6, "fp16": 1e-4, "bf16": 1e-4}
-PIX_TOL = {"fp32": 5e-6, "fp16": 2e-3, "bf16": 2e-3}
+NORM_TOL = {"fp32": 1e-6, "fp32f": 1e-6, "fp16": 1e-4, "bf16": 1e-4}
+PIX_TOL = {"fp32": 5e-6, "fp32f": 5e-6, "fp16": 2e-3, "bf16": 2e-3}
 
 
 def e_I(I, ref, miller):

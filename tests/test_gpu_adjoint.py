@@ -60,7 +60,7 @@ def test_autograd_function_chain_and_translation_invariance(xs):
     f = torch.ones(N, device="cuda")
     target = torch.from_numpy(rng.exponential(float(N), grid.n_pixels).astype(np.float32)).cuda()
     w = torch.from_numpy(_weights(grid, L).astype(np.float32)).cuda()
-    I = xs.IntensityFn.apply(pos, f, np.eye(3) * L, grid, "fp32")
+    I = xs.IntensityFn.apply(pos, f, np.eye(3) * L, grid)   # default: the factorised FP32 forward
     loss = (w * (I - target) ** 2).sum()
     loss.backward()
     g = pos.grad.detach().cpu().numpy()
@@ -74,9 +74,11 @@ def test_autograd_function_chain_and_translation_invariance(xs):
     assert np.linalg.norm(g - ref) / np.linalg.norm(ref) <= 1e-4
 
 
-def test_config3_full_size_against_finite_differences(xs):
+@pytest.mark.parametrize("prec", ["fp32", "fp32f"])
+def test_config3_full_size_against_finite_differences(xs, prec):
     """100,000 atoms, 256^2 plane; 64 random atoms checked against FP64
-    central differences of the loss (exact incremental S updates)."""
+    central differences of the loss (exact incremental S updates), with the
+    forward (I and S) from the plain FP32 kernel or the factorised one."""
     traj, target, grid = wl.config3()
     L = traj.L
     m = grid.miller()
@@ -84,7 +86,7 @@ def test_config3_full_size_against_finite_differences(xs):
     pos = torch.from_numpy(traj.pos[0]).cuda()
     f = torch.from_numpy(traj.f).cuda()
     It = oracle.intensity(target[0], traj.f, traj.box, m)[0]
-    I, amp = xs.intensity(pos, f, traj.box, grid, "fp32", want_amp=True)
+    I, amp = xs.intensity(pos, f, traj.box, grid, prec, want_amp=True)
     G = 2 * torch.from_numpy(w.astype(np.float32)).cuda() * (I.reshape(-1) - torch.from_numpy(It.astype(np.float32)).cuda())
     g = xs.intensity_backward(pos, f, traj.box, grid, amp.reshape(-1, 2).contiguous(), G.contiguous())
     xs.Context.get().sync_status()

@@ -46,14 +46,27 @@ def _case(seed, N, T, L, sigma=0.2, f_mixed=True):
     return pos, f, np.eye(3) * L
 
 
-def test_fp32_direct_config0_full(xs):
+@pytest.mark.parametrize("prec", ["fp32", "fp32f"])
+def test_fp32_direct_config0_full(xs, prec):
     traj, grid = wl.config0()
-    I = _run(xs, traj.pos, traj.f, traj.box, grid, "fp32")
+    I = _run(xs, traj.pos, traj.f, traj.box, grid, prec)
     ref = oracle.intensity(traj.pos, traj.f, traj.box, grid.miller())
-    check_I(I, ref, grid.miller(), "fp32")
+    check_I(I, ref, grid.miller(), prec)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+def test_factored_fp32_at_the_adjoint_workload_size(xs):
+    # 100,000 atoms, 256^2 plane: the forward of the fitting workload, against
+    # the oracle on sampled pixels (q = 0 included)
+    traj, _, grid = wl.config3()
+    I = _run(xs, traj.pos, traj.f, traj.box, grid, "fp32f").reshape(1, -1)
+    m = grid.miller()
+    rng = np.random.default_rng(31)
+    pick = np.unique(np.concatenate([np.flatnonzero(np.all(m == 0, axis=1)), rng.choice(m.shape[0], 2048, replace=False)]))
+    ref = oracle.intensity(traj.pos, traj.f, traj.box, m[pick])
+    check_I(I[:, pick], ref, m[pick], "fp32f")
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32f", "fp16", "bf16"])
 @pytest.mark.parametrize("N,T,grid", [
     (1000, 3, wl.QGrid(-48, 96, -40, 80, 0, 1)),      # ragged atoms and tiles
     (64, 2, wl.QGrid(-64, 128, -64, 128, 1, 1)),      # exact tiles, q_z != 0
@@ -67,7 +80,7 @@ def test_ragged_shapes(xs, prec, N, T, grid):
     check_I(I, ref, grid.miller(), prec)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("prec", ["fp32", "fp32f", "fp16"])
 def test_amplitude_matches_oracle(xs, prec):
     pos, f, box = _case(3, 700, 2, 17.0)
     grid = wl.QGrid(-20, 40, -20, 40, 0, 1)
@@ -79,7 +92,7 @@ def test_amplitude_matches_oracle(xs, prec):
     assert np.allclose(I.reshape(-1), (A[..., 0] ** 2 + A[..., 1] ** 2).reshape(-1), rtol=1e-5)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "fp32f", "fp16", "bf16"])
 def test_triclinic_cell(xs, prec):
     rng = np.random.default_rng(5)
     h = np.array([[12.0, 3.0, -1.5], [0.0, 10.0, 2.5], [1.0, 0.0, 9.0]])
@@ -126,7 +139,7 @@ def test_half_grid_against_oracle(xs, grid):
     check_I(I[:, pick], ref, m[pick], "fp16")
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "fp32f", "fp16", "bf16"])
 def test_edge_cases_single_and_zero_atoms(xs, prec):
     grid = wl.QGrid(-8, 16, -8, 16, 0, 1)
     box = np.eye(3) * 9.0
@@ -185,7 +198,7 @@ def test_nonfinite_position_is_reported(xs):
     xs.Context.get().sync_status()  # cleared
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("prec", ["fp32", "fp32f", "fp16"])
 def test_periodic_images_give_identical_records(xs, prec):
     # box 16 and positions on a 2^-8 grid: shifts by up to 2^10 boxes stay
     # exact in float32, and the turn counts rint(x 2^32 / 16) mod 2^32 of an
