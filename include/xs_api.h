@@ -445,7 +445,7 @@ XS_API xs_status xs_set_wait_timeout_ns(xs_context* ctx, int64_t ns);
  * prefix, windows, finalize: 1-4), "isf" (1), "isf_contrast" (2), "species"
  * (form-factor table, per-species sum, finish: 1 each), "points" (gather,
  * 1), "fft" (spread, three line passes, gather: 4-5), "batched"
- * (graph replay: its kernels), "adjoint" (3).  xs_launch_count returns the
+ * (graph replay: its kernels), "adjoint" (4).  xs_launch_count returns the
  * number of kernels the context has launched since it was created (tracing
  * on or off). */
 XS_API xs_status xs_profile_enable(xs_context* ctx, int32_t on);

@@ -29,7 +29,9 @@ __global__ void h_kernel(const float* __restrict__ amp, const float* __restrict_
 
 static size_t h_bytes(const GridDesc& g) { return ((size_t)g.pixels() * sizeof(float2) + 1023) & ~(size_t)1023; }
 
-size_t adjoint_workspace_bytes(const GridDesc& g) { return h_bytes(g) + adjoint_tc_image_bytes(g); }
+size_t adjoint_workspace_bytes(const GridDesc& g, int64_t n_pad) {
+    return h_bytes(g) + adjoint_tc_image_bytes(g, n_pad);
+}
 
 cudaError_t launch_adjoint(const AtomRec* rec, int64_t n_atoms, int64_t n_pad, const GridDesc& g,
                            const Mat3& hinv, const float* amp, const float* dL_dI, void* workspace,

@@ -32,9 +32,12 @@
 //   * after a row tile, 4 epilogue warps per CTA read their atom's 256
 //     columns (one TMEM lane = one atom), form Im[E_xz X] with E_xz advanced
 //     along n_x by the exact step exp(i 2 pi U_x) (reseeded every 16 rows and
-//     where n_x wraps) and keep the atom's running Im T in registers, while
-//     the MMA fills the other accumulator.
-// Pairs are persistent over the 256-atom tiles.  Every wait is bounded; on
+//     where n_x wraps) and write the atom's sums of the row tile, while the
+//     MMA fills the other accumulator.
+// Pairs are persistent over the units (tile of 256 atoms, row tile), dealt
+// round-robin: cutting the work at row tiles instead of whole atom tiles
+// shortens the last wave; adjoint_finish_kernel adds each atom's row-tile
+// sums in row-tile order and forms the gradient.  Every wait is bounded; on
 // expiry the kernel sets the device error word, all roles leave, the loader
 // waits for its copies in flight and tensor memory is released.
 #include <cuda_bf16.h>
@@ -302,9 +305,8 @@ __global__ void adjoint_image_kernel(const float2* __restrict__ H, GridDesc g, i
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAtThreads, 1)
-adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pad, GridDesc g, Mat3 hinv,
-                  const uint8_t* __restrict__ img, int n_rt, int n_st, int64_t n_tiles, float* __restrict__ grad,
-                  int* err, int64_t timeout_ns) {
+adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_pad, GridDesc g, const uint8_t* __restrict__ img,
+                  int n_rt, int n_st, int64_t n_work, float* __restrict__ partial, int* err, int64_t timeout_ns) {
     extern __shared__ __align__(16) uint8_t at_raw[];
     const uint32_t raw = at_smem_u32(at_raw);
     uint8_t* smem = at_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -347,7 +349,6 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
     at_fence_after();
     const uint32_t tmem = ctl->tmem;
     const int64_t Q = (int64_t)g.nx * g.nz;
-    const int n_units = n_rt * n_st;  // stages per atom tile
 
     if (warp >= kAtProdWarp0) {
         // ------------------------------------------------------------ producers
@@ -359,12 +360,12 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
         int slot = 0;
         uint32_t phase = 0;
         bool stop = false;
-        for (int64_t tile = pair; tile < n_tiles && !stop; tile += n_pairs) {
+        for (int64_t wk = pair; wk < n_work && !stop; wk += n_pairs) {
+            const int64_t tile = wk / n_rt;
             const int64_t j = tile * (2 * kAtAtomsCta) + (int64_t)rank * kAtAtomsCta + a_loc;
             const uint32_t U = j < n_pad ? __ldg(&rec[j].uy) : 0u;
             const float2 zstep = at_cis(U, ctl->tab);
-            for (int u = 0; u < n_units && !stop; ++u) {
-                const int s = u % n_st;
+            for (int s = 0; s < n_st && !stop; ++s) {
                 const int y0 = s * (kAtK / 2) + 16 * h;  // local n_y of this thread's first value
                 float2 E = at_cis((uint32_t)(g.ny0 + y0) * U, ctl->tab);
                 if (!at_wait(&ctl->empty[slot], phase ^ 1u, abort_flag, err, timeout_ns)) {
@@ -403,13 +404,14 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
             uint32_t issued = 0u;  // bit s: a copy into slot s was issued (its latest phase)
             uint32_t last_par = 0u;
             bool stop = false;
-            for (int64_t tile = pair; tile < n_tiles && !stop; tile += n_pairs) {
-                for (int u = 0; u < n_units && !stop; ++u) {
+            for (int64_t wk = pair; wk < n_work && !stop; wk += n_pairs) {
+                const int rt = (int)(wk % n_rt);
+                for (int s = 0; s < n_st && !stop; ++s) {
                     if (!at_wait(&ctl->empty[slot], phase ^ 1u, abort_flag, err, timeout_ns)) {
                         stop = true;
                         break;
                     }
-                    const uint8_t* src = img + ((int64_t)u * 2 + rank) * kAtBBytes;
+                    const uint8_t* src = img + (((int64_t)rt * n_st + s) * 2 + rank) * kAtBBytes;
                     at_arrive_expect_tx(&ctl->copy[slot], kAtBBytes);
                     at_bulk_copy(stage_base + (uint32_t)slot * kAtStage + 2 * kAtAHalf, src, kAtBBytes,
                                  &ctl->copy[slot]);
@@ -435,8 +437,8 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
             uint32_t phase = 0;
             int64_t a_cnt = 0;
             bool ok = true;
-            for (int64_t tile = pair; tile < n_tiles && ok; tile += n_pairs) {
-                for (int rt = 0; rt < n_rt && ok; ++rt, ++a_cnt) {
+            for (int64_t wk = pair; wk < n_work && ok; wk += n_pairs, ++a_cnt) {
+                {
                     const int b = (int)(a_cnt & 1);
                     const uint32_t use = (uint32_t)(a_cnt >> 1);
                     if (!at_wait(&ctl->acc_empty[b], (use & 1u) ^ 1u, abort_flag, err, timeout_ns)) {
@@ -485,8 +487,8 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
             int slot = 0;
             uint32_t phase = 0;
             bool ok = true;
-            for (int64_t tile = pair; tile < n_tiles && ok; tile += n_pairs) {
-                for (int u = 0; u < n_units; ++u) {
+            for (int64_t wk = pair; wk < n_work && ok; wk += n_pairs) {
+                for (int s = 0; s < n_st; ++s) {
                     if (!at_wait(&ctl->fill[slot], phase, abort_flag, err, timeout_ns) ||
                         !at_wait(&ctl->copy[slot], phase, abort_flag, err, timeout_ns)) {
                         ok = false;
@@ -510,74 +512,66 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
         const uint32_t acc_empty_c0 = at_map(at_smem_u32(&ctl->acc_empty[0]), 0);
         int64_t a_cnt = 0;
-        bool ok = true;
-        for (int64_t tile = pair; tile < n_tiles && ok; tile += n_pairs) {
+        for (int64_t wk = pair; wk < n_work; wk += n_pairs, ++a_cnt) {
+            const int64_t tile = wk / n_rt;
+            const int rt = (int)(wk % n_rt);
             const int64_t j = tile * (2 * kAtAtomsCta) + (int64_t)rank * kAtAtomsCta + a_loc;
             AtomRec me;
             me.ux = me.uy = me.uz = 0u;
             me.f = 0.0f;
             if (j < n_pad) me = rec[j];
             const float2 zx = at_cis(me.ux, ctl->tab);
-            float tx = 0.0f, ty = 0.0f, tz = 0.0f;  // Im T of this thread's atom
-            for (int rt = 0; rt < n_rt; ++rt, ++a_cnt) {
-                const int b = (int)(a_cnt & 1);
-                const uint32_t use = (uint32_t)(a_cnt >> 1);
-                uint32_t got = 0;
-                if (lane == 0) got = at_wait(&ctl->acc_full[b], use & 1u, abort_flag, err, timeout_ns, 200000u);
-                got = __shfl_sync(0xffffffffu, got, 0);
-                if (!got) {
-                    ok = false;
-                    break;
-                }
-                at_fence_after();
-                const uint32_t dcol = lane_base + (uint32_t)b * (uint32_t)kAtN;
+            float tx = 0.0f, ty = 0.0f, tz = 0.0f;  // Im T of this thread's atom over the row tile
+            const int b = (int)(a_cnt & 1);
+            const uint32_t use = (uint32_t)(a_cnt >> 1);
+            uint32_t got = 0;
+            if (lane == 0) got = at_wait(&ctl->acc_full[b], use & 1u, abort_flag, err, timeout_ns, 200000u);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) break;
+            at_fence_after();
+            const uint32_t dcol = lane_base + (uint32_t)b * (uint32_t)kAtN;
 #pragma unroll 1
-                for (int gq = 0; gq < kAtQ / 16; ++gq) {
-                    uint32_t rz[16], iz[16], ryv[16], iyv[16];
-                    at_ld16(dcol + 0 * kAtQ + 16 * gq, rz);
-                    at_ld16(dcol + 1 * kAtQ + 16 * gq, iz);
-                    at_ld16(dcol + 2 * kAtQ + 16 * gq, ryv);
-                    at_ld16(dcol + 3 * kAtQ + 16 * gq, iyv);
-                    at_wait_ld(rz);
-                    at_wait_ld(iz);
-                    at_wait_ld(ryv);
-                    at_wait_ld(iyv);
-                    const int64_t q0 = (int64_t)rt * kAtQ + 16 * gq;
-                    int xq = (int)(q0 % g.nx), zq = (int)(q0 / g.nx);
-                    float2 E = at_cis((uint32_t)(g.nx0 + xq) * me.ux + (uint32_t)(g.nz0 + zq) * me.uz, ctl->tab);
+            for (int gq = 0; gq < kAtQ / 16; ++gq) {
+                uint32_t rz[16], iz[16], ryv[16], iyv[16];
+                at_ld16(dcol + 0 * kAtQ + 16 * gq, rz);
+                at_ld16(dcol + 1 * kAtQ + 16 * gq, iz);
+                at_ld16(dcol + 2 * kAtQ + 16 * gq, ryv);
+                at_ld16(dcol + 3 * kAtQ + 16 * gq, iyv);
+                at_wait_ld(rz);
+                at_wait_ld(iz);
+                at_wait_ld(ryv);
+                at_wait_ld(iyv);
+                const int64_t q0 = (int64_t)rt * kAtQ + 16 * gq;
+                int xq = (int)(q0 % g.nx), zq = (int)(q0 / g.nx);
+                float2 E = at_cis((uint32_t)(g.nx0 + xq) * me.ux + (uint32_t)(g.nz0 + zq) * me.uz, ctl->tab);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        if (q0 + i < Q) {
-                            const float nxv = (float)(g.nx0 + xq), nzv = (float)(g.nz0 + zq);
-                            // Im[E X] = Re E Im X + Im E Re X
-                            const float ez = fmaf(E.x, __uint_as_float(iz[i]), E.y * __uint_as_float(rz[i]));
-                            tx = fmaf(nxv, ez, tx);
-                            tz = fmaf(nzv, ez, tz);
-                            ty += fmaf(E.x, __uint_as_float(iyv[i]), E.y * __uint_as_float(ryv[i]));
-                        }
-                        // next row: n_x + 1, or the next n_z plane (reseeded)
-                        if (++xq == g.nx) {
-                            xq = 0;
-                            ++zq;
-                            E = at_cis((uint32_t)g.nx0 * me.ux + (uint32_t)(g.nz0 + zq) * me.uz, ctl->tab);
-                        } else {
-                            E = at_cmul(E, zx);
-                        }
+                for (int i = 0; i < 16; ++i) {
+                    if (q0 + i < Q) {
+                        const float nxv = (float)(g.nx0 + xq), nzv = (float)(g.nz0 + zq);
+                        // Im[E X] = Re E Im X + Im E Re X
+                        const float ez = fmaf(E.x, __uint_as_float(iz[i]), E.y * __uint_as_float(rz[i]));
+                        tx = fmaf(nxv, ez, tx);
+                        tz = fmaf(nzv, ez, tz);
+                        ty += fmaf(E.x, __uint_as_float(iyv[i]), E.y * __uint_as_float(ryv[i]));
+                    }
+                    // next row: n_x + 1, or the next n_z plane (reseeded)
+                    if (++xq == g.nx) {
+                        xq = 0;
+                        ++zq;
+                        E = at_cis((uint32_t)g.nx0 * me.ux + (uint32_t)(g.nz0 + zq) * me.uz, ctl->tab);
+                    } else {
+                        E = at_cmul(E, zx);
                     }
                 }
-                at_fence_before();
-                __syncwarp();
-                if (lane == 0) at_arrive_cluster(acc_empty_c0 + (uint32_t)b * 8u);
             }
-            if (!ok) break;
-            if (j < n_atoms) {
-                const double scale = -4.0 * 3.14159265358979323846 * (double)me.f;
-                const double v[3] = {(double)tx, (double)ty, (double)tz};
-                for (int c = 0; c < 3; ++c) {
-                    const double hv = hinv.a[0 * 3 + c] * v[0] + hinv.a[1 * 3 + c] * v[1] + hinv.a[2 * 3 + c] * v[2];
-                    grad[j * 3 + c] = (float)(scale * hv);
-                }
-            }
+            at_fence_before();
+            __syncwarp();
+            if (lane == 0) at_arrive_cluster(acc_empty_c0 + (uint32_t)b * 8u);
+            // this unit's sums of the atom: [unit][256 atoms][3]
+            float* pw = partial + (wk * (2 * kAtAtomsCta) + (int64_t)rank * kAtAtomsCta + a_loc) * 3;
+            pw[0] = tx;
+            pw[1] = ty;
+            pw[2] = tz;
         }
     }
 
@@ -590,12 +584,39 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int64_t n_pa
                      : "memory");
 }
 
+// one thread per atom: the row tiles' sums in row-tile order, then
+// dL/dr_j = -4 pi f_j h^-T Im T_j
+__global__ void adjoint_finish_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int n_rt, Mat3 hinv,
+                                      const float* __restrict__ partial, float* __restrict__ grad) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n_atoms) return;
+    const int64_t tile = j / (2 * kAtAtomsCta), jl = j % (2 * kAtAtomsCta);
+    float t[3] = {0.0f, 0.0f, 0.0f};
+    for (int rt = 0; rt < n_rt; ++rt) {
+        const float* p = partial + (((tile * n_rt + rt) * (2 * kAtAtomsCta)) + jl) * 3;
+        t[0] += p[0];
+        t[1] += p[1];
+        t[2] += p[2];
+    }
+    const double scale = -4.0 * 3.14159265358979323846 * (double)rec[j].f;
+    for (int c = 0; c < 3; ++c) {
+        const double hv = hinv.a[0 * 3 + c] * t[0] + hinv.a[1 * 3 + c] * t[1] + hinv.a[2 * 3 + c] * t[2];
+        grad[j * 3 + c] = (float)(scale * hv);
+    }
+}
+
 }  // namespace
 
-size_t adjoint_tc_image_bytes(const GridDesc& g) {
+static size_t image_bytes(const GridDesc& g) {
     const int64_t n_rt = ((int64_t)g.nx * g.nz + kAtQ - 1) / kAtQ;
     const int64_t n_st = ((int64_t)g.ny + kAtK / 2 - 1) / (kAtK / 2);
     return (size_t)(n_rt * n_st) * 2 * kAtBBytes;
+}
+
+size_t adjoint_tc_image_bytes(const GridDesc& g, int64_t n_pad) {
+    const int64_t n_rt = ((int64_t)g.nx * g.nz + kAtQ - 1) / kAtQ;
+    const int64_t n_tiles = (n_pad + 2 * kAtAtomsCta - 1) / (2 * kAtAtomsCta);
+    return image_bytes(g) + (size_t)(n_tiles * n_rt) * (2 * kAtAtomsCta) * 3 * sizeof(float);
 }
 
 cudaError_t launch_adjoint_tc(const AtomRec* rec, int64_t n_atoms, int64_t n_pad, const GridDesc& g,
@@ -639,10 +660,18 @@ cudaError_t launch_adjoint_tc(const AtomRec* rec, int64_t n_atoms, int64_t n_pad
         max_pairs = n;
     }
     const int64_t n_tiles = (n_pad + 2 * kAtAtomsCta - 1) / (2 * kAtAtomsCta);
-    const int64_t pairs = std::min<int64_t>(max_pairs, n_tiles);
+    const int64_t n_work = n_tiles * n_rt;  // units (atom tile, row tile)
+    const int64_t pairs = std::min<int64_t>(max_pairs, n_work);
+    float* partial = reinterpret_cast<float*>(img + image_bytes(g));
     ++tl_kernel_launches;
-    adjoint_tc_kernel<<<(unsigned)(2 * pairs), kAtThreads, kAtSmemBytes, st>>>(
-        rec, n_atoms, n_pad, g, hinv, img, (int)n_rt, (int)n_st, n_tiles, grad, err, timeout_ns);
+    adjoint_tc_kernel<<<(unsigned)(2 * pairs), kAtThreads, kAtSmemBytes, st>>>(rec, n_pad, g, img, (int)n_rt,
+                                                                              (int)n_st, n_work, partial, err,
+                                                                              timeout_ns);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ++tl_kernel_launches;
+    adjoint_finish_kernel<<<(unsigned)((n_atoms + 255) / 256), 256, 0, st>>>(rec, n_atoms, (int)n_rt, hinv, partial,
+                                                                             grad);
     return cudaGetLastError();
 }
 

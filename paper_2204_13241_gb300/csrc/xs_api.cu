@@ -1926,7 +1926,7 @@ xs_status xs_intensity_backward(xs_context* ctx, const xs_traj* traj, const xs_q
         return o;
     };
     const size_t o_rec = carve((size_t)n_pad * sizeof(AtomRec));
-    const size_t o_h = carve(adjoint_workspace_bytes(g));
+    const size_t o_h = carve(adjoint_workspace_bytes(g, n_pad));
     s = ensure_ws(ctx, off + 256);
     if (s != XS_OK) return s;
     char* ws = static_cast<char*>(ctx->ws);

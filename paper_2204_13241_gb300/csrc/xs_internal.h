@@ -193,13 +193,14 @@ cudaError_t launch_xsvs(const float* I, int64_t T, int64_t P, const int32_t* d_p
                         cudaStream_t st);
 
 // ---- adjoint --------------------------------------------------------------
-size_t adjoint_workspace_bytes(const GridDesc& g);
+size_t adjoint_workspace_bytes(const GridDesc& g, int64_t n_pad);
 cudaError_t launch_adjoint(const AtomRec* rec, int64_t n_atoms, int64_t n_pad, const GridDesc& g,
                            const Mat3& hinv, const float* amp, const float* dL_dI,
                            void* workspace, float* grad, int* err, int64_t timeout_ns, cudaStream_t st);
-// the contraction over n_y on tensor cores (split BF16): H images of
-// adjoint_tc_image_bytes(g) bytes (16-byte aligned) built from H [P]
-size_t adjoint_tc_image_bytes(const GridDesc& g);
+// the contraction over n_y on tensor cores (split BF16): H images built
+// from H [P] and the per-unit partial sums, adjoint_tc_image_bytes(g, n_pad)
+// bytes (16-byte aligned)
+size_t adjoint_tc_image_bytes(const GridDesc& g, int64_t n_pad);
 cudaError_t launch_adjoint_tc(const AtomRec* rec, int64_t n_atoms, int64_t n_pad, const GridDesc& g,
                               const Mat3& hinv, const float2* H, void* image, float* grad, int* err,
                               int64_t timeout_ns, cudaStream_t st);
