@@ -513,7 +513,7 @@ def run_ours(args):
     time.sleep(0.3)
     ev0.record(stream)
     for _ in range(args.steps):
-        res = step(pos_d, f_d)
+        res = step(pos_d, f_d)  # the last step's g2 and beta are checked against the oracle below
     ev1.record(stream)
     ev1.synchronize()
     clocks = sampler.stop()
@@ -971,6 +971,8 @@ def run_ours(args):
 
 def main():
     args = _args()
+    if args.steps < 1 or args.warmup < 0:
+        raise SystemExit("--steps must be at least 1 and --warmup at least 0")
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

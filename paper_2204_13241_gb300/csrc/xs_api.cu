@@ -1646,7 +1646,6 @@ static xs_status batched_impl(xs_context* ctx, const xs_traj* traj, const xs_qgr
         }
         which.push_back(i);
     }
-    int64_t total_units = 0;
     std::vector<char> blob;
     // correlation requests: host tables into the blob, one shared workspace
     std::vector<CorrPrep> corr(req ? (size_t)n_traj : 0);
@@ -1678,7 +1677,6 @@ static xs_status batched_impl(xs_context* ctx, const xs_traj* traj, const xs_qgr
             trs.push_back(tc_traj(reinterpret_cast<AtomRec*>(ws + j.rec_off), j.n_pad, j.T, j.g, I_out[i], nullptr,
                                   kind, chunk, ctx->exact_tables));
     }
-    for (const TcTraj& t : trs) total_units += tc_units(t);
     for (int i : empty)
         XS_CUDA(cudaMemsetAsync(I_out[i], 0, (size_t)jobs[(size_t)i].T * jobs[(size_t)i].g.pixels() * sizeof(float), st));
     if (trs.empty() && !req) return XS_OK;
