@@ -63,7 +63,9 @@ typedef enum {
     XS_ERR_NO_MEMORY = 3,     /* the allocator returned NULL */
     XS_ERR_CUDA = 4,          /* a CUDA runtime call failed (message has the CUDA error) */
     XS_ERR_TIMEOUT = 5,       /* a kernel's bounded wait expired (device error word) */
-    XS_ERR_NUMERIC = 6        /* a kernel met a non-finite input (device error word) */
+    XS_ERR_NUMERIC = 6,       /* a kernel met a non-finite input (device error word) */
+    XS_ERR_BOUNDS = 7         /* a bounds check of the checked build failed (device error word; the
+                                 access was skipped) */
 } xs_status;
 
 /* Arithmetic of the intensity (Sec. 3.1 direct method; every variant computes

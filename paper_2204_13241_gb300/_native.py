@@ -13,7 +13,7 @@ from . import build as _build
 
 XS_OK = 0
 STATUS_NAMES = {0: "XS_OK", 1: "XS_ERR_INVALID_ARG", 2: "XS_ERR_UNSUPPORTED", 3: "XS_ERR_NO_MEMORY",
-                4: "XS_ERR_CUDA", 5: "XS_ERR_TIMEOUT", 6: "XS_ERR_NUMERIC"}
+                4: "XS_ERR_CUDA", 5: "XS_ERR_TIMEOUT", 6: "XS_ERR_NUMERIC", 7: "XS_ERR_BOUNDS"}
 PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2, "fp32f": 3}
 
 EXPORTS = ["xs_context_create", "xs_context_destroy", "xs_intensity", "xs_intensity_batched", "xs_g2",

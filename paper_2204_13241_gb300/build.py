@@ -3,6 +3,11 @@
 Each .cu file is compiled by nvcc in parallel, then linked into
 paper_2204_13241_gb300/_build/libxs.so with the static CUDA runtime.
 Rebuilds only when a source or header is newer than the library.
+
+With the environment variable XS_BUILD_VARIANT=check the library is the
+checked build: compiled with -DXS_BOUNDS_CHECK into _build_check/, its
+kernels test their shared-memory, tensor-memory, workspace and output
+indexes and report a failed check through the device error word.
 """
 from __future__ import annotations
 
@@ -16,14 +21,15 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(PKG, "_build")
+CHECKED = os.environ.get("XS_BUILD_VARIANT", "") == "check"
+BUILD = os.path.join(PKG, "_build_check" if CHECKED else "_build")
 LIB = os.path.join(BUILD, "libxs.so")
 
 SOURCES = ["xs_api.cu", "xs_static.cu", "k_direct.cu", "k_corr.cu", "k_adjoint.cu", "k_adjoint_tc.cu", "k_tc.cu",
            "k_species.cu", "k_fft.cu", "k_factored.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-         "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
+         "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC] + (["-DXS_BOUNDS_CHECK"] if CHECKED else [])
 
 
 def _nvcc() -> str:

@@ -306,7 +306,10 @@ __global__ void adjoint_image_kernel(const float2* __restrict__ H, GridDesc g, i
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAtThreads, 1)
 adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_pad, GridDesc g, const uint8_t* __restrict__ img,
-                  int n_rt, int n_st, int64_t n_work, float* __restrict__ partial, int* err, int64_t timeout_ns) {
+                  int n_rt, int n_st, int64_t n_work, float* __restrict__ partial, int* err, int64_t timeout_ns,
+                  int64_t img_bytes, int64_t partial_n) {
+    // img_bytes and partial_n (the sizes of `img` and `partial` the host
+    // reserved) are read by the bounds checks of the checked build only
     extern __shared__ __align__(16) uint8_t at_raw[];
     const uint32_t raw = at_smem_u32(at_raw);
     uint8_t* smem = at_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -384,8 +387,10 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_pad, GridDesc g, co
                         E = at_cmul(E, zstep);
                     }
                     const uint32_t ch = (uint32_t)(((4 * h + c) ^ (a_loc & 7)) << 4);
-                    at_st_v4(a_hi + ch, hi[0], hi[1], hi[2], hi[3]);
-                    at_st_v4(a_hi + kAtAHalf + ch, lo[0], lo[1], lo[2], lo[3]);
+                    if (XS_IN_BOUNDS(err, slot < kAtStages && row_off + ch + 16u <= kAtAHalf)) {
+                        at_st_v4(a_hi + ch, hi[0], hi[1], hi[2], hi[3]);
+                        at_st_v4(a_hi + kAtAHalf + ch, lo[0], lo[1], lo[2], lo[3]);
+                    }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
@@ -411,10 +416,15 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_pad, GridDesc g, co
                         stop = true;
                         break;
                     }
-                    const uint8_t* src = img + (((int64_t)rt * n_st + s) * 2 + rank) * kAtBBytes;
-                    at_arrive_expect_tx(&ctl->copy[slot], kAtBBytes);
-                    at_bulk_copy(stage_base + (uint32_t)slot * kAtStage + 2 * kAtAHalf, src, kAtBBytes,
-                                 &ctl->copy[slot]);
+                    const int64_t src_off = (((int64_t)rt * n_st + s) * 2 + rank) * kAtBBytes;
+                    const uint8_t* src = img + src_off;
+                    if (XS_IN_BOUNDS(err, slot < kAtStages && src_off >= 0 && src_off + kAtBBytes <= img_bytes)) {
+                        at_arrive_expect_tx(&ctl->copy[slot], kAtBBytes);
+                        at_bulk_copy(stage_base + (uint32_t)slot * kAtStage + 2 * kAtAHalf, src, kAtBBytes,
+                                     &ctl->copy[slot]);
+                    } else {
+                        at_arrive_expect_tx(&ctl->copy[slot], 0u);  // completes the phase with no copy
+                    }
                     issued |= 1u << slot;
                     last_par = (last_par & ~(1u << slot)) | (phase << slot);
                     if (++slot == kAtStages) {
@@ -458,14 +468,16 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_pad, GridDesc g, co
                         const uint32_t a_lo = a_hi + kAtAHalf;
                         const uint32_t b_hi = a_hi + 2 * kAtAHalf;
                         const uint32_t b_lo = b_hi + kAtBHalf;
+                        if (XS_IN_BOUNDS(err, slot < kAtStages && (uint32_t)(b + 1) * kAtN <= kAtTmemCols)) {
 #pragma unroll
-                        for (int kk = 0; kk < kAtK / 16; ++kk) {
-                            const uint32_t ka = (uint32_t)kk * 32u;    // K-major: 16 BF16 along the row
-                            const uint32_t kb = (uint32_t)kk * 2048u;  // MN-major: two 8-row K atoms
-                            at_mma_pair(d_tmem, at_desc_k(a_hi + ka), at_desc_mn(b_hi + kb), idesc,
-                                        (s > 0 || kk > 0) ? 1u : 0u);
-                            at_mma_pair(d_tmem, at_desc_k(a_hi + ka), at_desc_mn(b_lo + kb), idesc, 1u);
-                            at_mma_pair(d_tmem, at_desc_k(a_lo + ka), at_desc_mn(b_hi + kb), idesc, 1u);
+                            for (int kk = 0; kk < kAtK / 16; ++kk) {
+                                const uint32_t ka = (uint32_t)kk * 32u;    // K-major: 16 BF16 along the row
+                                const uint32_t kb = (uint32_t)kk * 2048u;  // MN-major: two 8-row K atoms
+                                at_mma_pair(d_tmem, at_desc_k(a_hi + ka), at_desc_mn(b_hi + kb), idesc,
+                                            (s > 0 || kk > 0) ? 1u : 0u);
+                                at_mma_pair(d_tmem, at_desc_k(a_hi + ka), at_desc_mn(b_lo + kb), idesc, 1u);
+                                at_mma_pair(d_tmem, at_desc_k(a_lo + ka), at_desc_mn(b_hi + kb), idesc, 1u);
+                            }
                         }
                         at_commit_pair(&ctl->empty[slot], 0x3);
                         if (++slot == kAtStages) {
@@ -533,14 +545,19 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_pad, GridDesc g, co
 #pragma unroll 1
             for (int gq = 0; gq < kAtQ / 16; ++gq) {
                 uint32_t rz[16], iz[16], ryv[16], iyv[16];
-                at_ld16(dcol + 0 * kAtQ + 16 * gq, rz);
-                at_ld16(dcol + 1 * kAtQ + 16 * gq, iz);
-                at_ld16(dcol + 2 * kAtQ + 16 * gq, ryv);
-                at_ld16(dcol + 3 * kAtQ + 16 * gq, iyv);
-                at_wait_ld(rz);
-                at_wait_ld(iz);
-                at_wait_ld(ryv);
-                at_wait_ld(iyv);
+                if (XS_IN_BOUNDS(err, (uint32_t)b * kAtN + 3u * kAtQ + 16u * (gq + 1) <= kAtTmemCols)) {
+                    at_ld16(dcol + 0 * kAtQ + 16 * gq, rz);
+                    at_ld16(dcol + 1 * kAtQ + 16 * gq, iz);
+                    at_ld16(dcol + 2 * kAtQ + 16 * gq, ryv);
+                    at_ld16(dcol + 3 * kAtQ + 16 * gq, iyv);
+                    at_wait_ld(rz);
+                    at_wait_ld(iz);
+                    at_wait_ld(ryv);
+                    at_wait_ld(iyv);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) rz[i] = iz[i] = ryv[i] = iyv[i] = 0u;
+                }
                 const int64_t q0 = (int64_t)rt * kAtQ + 16 * gq;
                 int xq = (int)(q0 % g.nx), zq = (int)(q0 / g.nx);
                 float2 E = at_cis((uint32_t)(g.nx0 + xq) * me.ux + (uint32_t)(g.nz0 + zq) * me.uz, ctl->tab);
@@ -568,10 +585,13 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_pad, GridDesc g, co
             __syncwarp();
             if (lane == 0) at_arrive_cluster(acc_empty_c0 + (uint32_t)b * 8u);
             // this unit's sums of the atom: [unit][256 atoms][3]
-            float* pw = partial + (wk * (2 * kAtAtomsCta) + (int64_t)rank * kAtAtomsCta + a_loc) * 3;
-            pw[0] = tx;
-            pw[1] = ty;
-            pw[2] = tz;
+            const int64_t pi = (wk * (2 * kAtAtomsCta) + (int64_t)rank * kAtAtomsCta + a_loc) * 3;
+            if (XS_IN_BOUNDS(err, pi >= 0 && pi + 3 <= partial_n)) {
+                float* pw = partial + pi;
+                pw[0] = tx;
+                pw[1] = ty;
+                pw[2] = tz;
+            }
         }
     }
 
@@ -587,13 +607,16 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_pad, GridDesc g, co
 // one thread per atom: the row tiles' sums in row-tile order, then
 // dL/dr_j = -4 pi f_j h^-T Im T_j
 __global__ void adjoint_finish_kernel(const AtomRec* __restrict__ rec, int64_t n_atoms, int n_rt, Mat3 hinv,
-                                      const float* __restrict__ partial, float* __restrict__ grad) {
+                                      const float* __restrict__ partial, float* __restrict__ grad, int64_t partial_n,
+                                      int* err) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n_atoms) return;
     const int64_t tile = j / (2 * kAtAtomsCta), jl = j % (2 * kAtAtomsCta);
     float t[3] = {0.0f, 0.0f, 0.0f};
     for (int rt = 0; rt < n_rt; ++rt) {
-        const float* p = partial + (((tile * n_rt + rt) * (2 * kAtAtomsCta)) + jl) * 3;
+        const int64_t pi = (((tile * n_rt + rt) * (2 * kAtAtomsCta)) + jl) * 3;
+        if (!XS_IN_BOUNDS(err, pi + 3 <= partial_n)) continue;
+        const float* p = partial + pi;
         t[0] += p[0];
         t[1] += p[1];
         t[2] += p[2];
@@ -663,15 +686,17 @@ cudaError_t launch_adjoint_tc(const AtomRec* rec, int64_t n_atoms, int64_t n_pad
     const int64_t n_work = n_tiles * n_rt;  // units (atom tile, row tile)
     const int64_t pairs = std::min<int64_t>(max_pairs, n_work);
     float* partial = reinterpret_cast<float*>(img + image_bytes(g));
+    const int64_t img_bytes = (int64_t)image_bytes(g);
+    const int64_t partial_n = (int64_t)((adjoint_tc_image_bytes(g, n_pad) - image_bytes(g)) / sizeof(float));
     ++tl_kernel_launches;
     adjoint_tc_kernel<<<(unsigned)(2 * pairs), kAtThreads, kAtSmemBytes, st>>>(rec, n_pad, g, img, (int)n_rt,
                                                                               (int)n_st, n_work, partial, err,
-                                                                              timeout_ns);
+                                                                              timeout_ns, img_bytes, partial_n);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ++tl_kernel_launches;
     adjoint_finish_kernel<<<(unsigned)((n_atoms + 255) / 256), 256, 0, st>>>(rec, n_atoms, (int)n_rt, hinv, partial,
-                                                                             grad);
+                                                                             grad, partial_n, err);
     return cudaGetLastError();
 }
 

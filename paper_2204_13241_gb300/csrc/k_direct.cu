@@ -90,10 +90,12 @@ phase_kernel(const float* __restrict__ pos, const float* __restrict__ f, int64_t
     const int64_t j = opt.perm_mul == 1 ? k
                                         : (int64_t)(((uint64_t)(k / kPermRun) * (uint64_t)opt.perm_mul) %
                                                     (uint64_t)(n_pad / kPermRun)) * kPermRun + k % kPermRun;
+    if (!XS_IN_BOUNDS(err, j >= 0 && j < n_pad)) return;
     const bool real = j < n_atoms;
     // atom j of this call is atom a of the frames (a subset when an index is given)
     const int64_t a = (opt.index && real) ? (int64_t)opt.index[j] : j;
     const int64_t stride = opt.index ? opt.pos_atoms : n_atoms;
+    if (real && !XS_IN_BOUNDS(err, a >= 0 && a < stride)) return;
     const float fj = real ? f[a] : 0.0f;
     const int64_t t0 = (int64_t)blockIdx.y * kPhaseFrames;
     const int64_t t1 = min(n_frames, t0 + kPhaseFrames);

@@ -53,6 +53,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <queue>
 #include <vector>
 
@@ -136,6 +137,10 @@ struct TcArgs {
     double2* partial;       // split units: [rem][parts][128 x][128 y] partial amplitudes
     int* err;
     int64_t timeout_ns;
+#ifdef XS_BOUNDS_CHECK
+    int64_t scratch_f2;     // float2 entries of `scratch`
+    int64_t partial_n;      // double2 entries of `partial`
+#endif
 };
 
 // ---- PTX wrappers ------------------------------------------------------------
@@ -392,6 +397,11 @@ struct Unit {
     int part;
     int chunk;     // stages per accumulation chunk (0: the launch's)
     int tile_y;    // n_y per tile
+#ifdef XS_BOUNDS_CHECK
+    const uint4* rec_lo;  // the trajectory's records [rec_lo, rec_hi)
+    const uint4* rec_hi;
+    int64_t out_n;        // entries of I the check admits
+#endif
 };
 
 __device__ __forceinline__ Unit make_unit(const TcTraj& tr, int t, int iz, int tx, int ty) {
@@ -417,7 +427,19 @@ __device__ __forceinline__ Unit make_unit(const TcTraj& tr, int t, int iz, int t
     u.split = -1;
     u.part = 0;
     u.chunk = tr.chunk;
+#ifdef XS_BOUNDS_CHECK
+    u.rec_lo = tr.rec;
+    u.rec_hi = tr.rec + (int64_t)tr.n_frames * tr.n_pad;
+    u.out_n = (int64_t)tr.check_frames * tr.nz * tr.ny * tr.nx;
+#endif
     return u;
+}
+
+// record `p` of unit `u`; the checked build tests that it lies in the
+// trajectory's records and reads a zero record in place of one that does not
+__device__ __forceinline__ uint4 load_rec(const Unit& u, const uint4* p, int* err) {
+    if (!XS_IN_BOUNDS(err, p >= u.rec_lo && p < u.rec_hi)) return make_uint4(0u, 0u, 0u, 0u);
+    return __ldg(p);
 }
 
 __device__ __forceinline__ Unit single_unit(const TcTraj& tr, int64_t u) {
@@ -554,7 +576,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
         Unit up{};
         if (my_units > 0) up = get_unit(args, pair, n_pairs, 0);
         uint4 r_next = make_uint4(0, 0, 0, 0);
-        if (my_units > 0) r_next = __ldg(up.rec + (int64_t)up.s0 * kBK + k);
+        if (my_units > 0) r_next = load_rec(up, up.rec + (int64_t)up.s0 * kBK + k, args.err);
         bool stop = false;
         for (int64_t ku = 0; ku < my_units && !stop; ++ku) {
             Unit up_next{};
@@ -572,9 +594,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
             for (int s = up.s0; s < st1; ++s) {
                 const uint4 r = r_next;
                 if (s + 1 < st1)
-                    r_next = __ldg(rec_cur + (int64_t)(s + 1) * kBK);
+                    r_next = load_rec(up, rec_cur + (int64_t)(s + 1) * kBK, args.err);
                 else if (has_next)
-                    r_next = __ldg(up_next.rec + (int64_t)up_next.s0 * kBK + k);
+                    r_next = load_rec(up_next, up_next.rec + (int64_t)up_next.s0 * kBK + k, args.err);
                 // seed E(n0) and z = E(1) of this thread's run, E(n0 + 1) = E(n0) z
                 // and the step z^2 (two table evaluations instead of three
                 // made producer-bound tiles 2-7% faster, at the same error)
@@ -618,7 +640,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
                 }
                 const uint32_t sb = stage_base + (uint32_t)slot * kStageBytes;
                 const uint32_t hi_base = is_a ? sb : sb + 2 * kAHalfBytes;
-                const uint32_t lo_base = hi_base + (is_a ? kAHalfBytes : L::kBHalfBytes);
+                const uint32_t half_bytes = is_a ? kAHalfBytes : L::kBHalfBytes;
+                const uint32_t lo_base = hi_base + half_bytes;
                 if (KIND == kTcTile128 && centred) {
                     uint32_t xh = 0u, xl = 0u;  // X(32 rank + 32) as packed (Re, Im)
                     if (extra) split2<BF16>(Ex, xh, xl);
@@ -637,8 +660,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
                             }
                         }
                         const uint32_t off = chunk_off(2 * (s0 + 4 * g), k);
-                        st_shared_v4(hi_base + off, h[0], h[1], h[2], h[3]);
-                        st_shared_v4(lo_base + off, l[0], l[1], l[2], l[3]);
+                        if (XS_IN_BOUNDS(args.err, slot < kStages && off + 16u <= half_bytes)) {
+                            st_shared_v4(hi_base + off, h[0], h[1], h[2], h[3]);
+                            st_shared_v4(lo_base + off, l[0], l[1], l[2], l[3]);
+                        }
                         if (g == 0 && extra) {
                             // slot 32 takes X(32 rank + 32) in place of X(32 rank)
                             h[0] = __byte_perm(xh, h[0], 0x7610);
@@ -647,8 +672,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
                             l[1] = __byte_perm(xl, l[1], 0x7632);
                         }
                         const uint32_t moff = chunk_off(2 * (32 + s0 + 4 * g), k);
-                        st_shared_v4(hi_base + moff, h[0], h[1], h[2], h[3]);
-                        st_shared_v4(lo_base + moff, l[0], l[1], l[2], l[3]);
+                        if (XS_IN_BOUNDS(args.err, slot < kStages && moff + 16u <= half_bytes)) {
+                            st_shared_v4(hi_base + moff, h[0], h[1], h[2], h[3]);
+                            st_shared_v4(lo_base + moff, l[0], l[1], l[2], l[3]);
+                        }
                     }
                 } else {
 #pragma unroll
@@ -667,8 +694,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
                             }
                         }
                         const uint32_t off = chunk_off(2 * (run0 + 4 * g), k);
-                        st_shared_v4(hi_base + off, h[0], h[1], h[2], h[3]);
-                        st_shared_v4(lo_base + off, l[0], l[1], l[2], l[3]);
+                        if (XS_IN_BOUNDS(args.err, slot < kStages && off + 16u <= half_bytes)) {
+                            st_shared_v4(hi_base + off, h[0], h[1], h[2], h[3]);
+                            st_shared_v4(lo_base + off, l[0], l[1], l[2], l[3]);
+                        }
                     }
                 }
                 fence_async_shared();
@@ -722,13 +751,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
                         const uint32_t a_lo = a_hi + kAHalfBytes;
                         const uint32_t b_hi = a_hi + 2 * kAHalfBytes;
                         const uint32_t b_lo = b_hi + L::kBHalfBytes;
+                        if (XS_IN_BOUNDS(args.err, slot < kStages && (uint32_t)(b + 1) * kBN <= C::kTmemCols)) {
 #pragma unroll
-                        for (int kk = 0; kk < kBK / 16; ++kk) {
-                            const uint32_t ko = (uint32_t)kk * 2048u;  // two 8-row K atoms per K = 16
-                            umma_pair(d_tmem, mn_desc(a_hi + ko), mn_desc(b_hi + ko), idesc,
-                                      (s > s0 || kk > 0) ? 1u : 0u);
-                            umma_pair(d_tmem, mn_desc(a_hi + ko), mn_desc(b_lo + ko), idesc, 1u);
-                            umma_pair(d_tmem, mn_desc(a_lo + ko), mn_desc(b_hi + ko), idesc, 1u);
+                            for (int kk = 0; kk < kBK / 16; ++kk) {
+                                const uint32_t ko = (uint32_t)kk * 2048u;  // two 8-row K atoms per K = 16
+                                umma_pair(d_tmem, mn_desc(a_hi + ko), mn_desc(b_hi + ko), idesc,
+                                          (s > s0 || kk > 0) ? 1u : 0u);
+                                umma_pair(d_tmem, mn_desc(a_hi + ko), mn_desc(b_lo + ko), idesc, 1u);
+                                umma_pair(d_tmem, mn_desc(a_lo + ko), mn_desc(b_hi + ko), idesc, 1u);
+                            }
                         }
                         umma_commit_pair(&ctl->empty[slot], 0x3);
                         if (++slot == kStages) {
@@ -805,15 +836,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
 #pragma unroll 1
                 for (int j = 0; j < kBN / 16; ++j) {
                     uint32_t r[16];
-                    tmem_ld16(dcol + 16 * j, r);
-                    tmem_wait16(r);
+                    if (XS_IN_BOUNDS(args.err, row < 128 && (uint32_t)b * kBN + 16u * (j + 1) <= C::kTmemCols)) {
+                        tmem_ld16(dcol + 16 * j, r);
+                        tmem_wait16(r);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) r[i] = 0u;
+                    }
+                    // scratch rows of this thread for columns 16j .. 16j+15
+                    const bool scr_ok = XS_IN_BOUNDS(
+                        args.err, (int64_t)blockIdx.x * 256 * 128 + row + (int64_t)(16 * j + 15) * 128 < args.scratch_f2);
                     // running total per value as an unevaluated FP32 pair hi + lo,
                     // updated with the error-free sum TwoSum(hi, chunk)
                     float hi[16], lo[16];
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const float c = __uint_as_float(r[i]);
-                        if (first) {
+                        if (first || !scr_ok) {
                             hi[i] = c;
                             lo[i] = 0.0f;
                         } else {
@@ -826,8 +865,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
                         }
                     }
                     if (!last) {
+                        if (scr_ok) {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) scr[(size_t)(16 * j + i) * 128] = make_float2(hi[i], lo[i]);
+                            for (int i = 0; i < 16; ++i) scr[(size_t)(16 * j + i) * 128] = make_float2(hi[i], lo[i]);
+                        }
                         continue;
                     }
                     double v[16];
@@ -872,13 +913,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
                                 const double sim = sy * p_ri + sx * p_ir;
                                 const int iy = up.ty * C::kTileY + yi;
                                 if (part_dst) {
-                                    part_dst[yi] = make_double2(sre, sim);
+                                    if (XS_IN_BOUNDS(args.err, ((int64_t)up.split * args.parts + up.part) * (kTile * kTile) +
+                                                                       (int64_t)xi * kTile + yi <
+                                                                   args.partial_n))
+                                        part_dst[yi] = make_double2(sre, sim);
                                 } else if (iy < up.ny) {
                                     const int64_t o = (((int64_t)up.t * up.nz + up.iz) * up.ny + iy) * up.nx + ix;
-                                    up.I[o] = (float)(sre * sre + sim * sim);
-                                    if (up.amp) {
-                                        up.amp[2 * o] = (float)sre;
-                                        up.amp[2 * o + 1] = (float)sim;
+                                    if (XS_IN_BOUNDS(args.err, o >= 0 && o < up.out_n)) {
+                                        up.I[o] = (float)(sre * sre + sim * sim);
+                                        if (up.amp) {
+                                            up.amp[2 * o] = (float)sre;
+                                            up.amp[2 * o + 1] = (float)sim;
+                                        }
                                     }
                                 }
                             }
@@ -943,6 +989,20 @@ int tc_pair_capacity(int num_sms, int kind) {
 
 int tc_default_kind(const GridDesc& g) { return g.ny <= 64 ? kTcTile64 : kTcTile128; }
 
+#ifdef XS_BOUNDS_CHECK
+// Self-test of the checked build: with XS_CHECK_SHORT_OUTPUT=1 the bounds
+// check of tc_kernel admits one frame of I less than the buffers hold, so the
+// last frame's writes fail the check and are skipped (every access stays
+// inside the real buffers) and the call returns XS_ERR_BOUNDS.
+static bool check_short_output() {
+    static const bool on = [] {
+        const char* v = std::getenv("XS_CHECK_SHORT_OUTPUT");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
+#endif
+
 TcTraj tc_traj(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDesc& g, float* I, float* amp, int kind,
                int chunk, bool exact) {
     TcTraj t;
@@ -963,6 +1023,9 @@ TcTraj tc_traj(const AtomRec* rec, int64_t n_pad, int64_t n_frames, const GridDe
     t.nz0 = g.nz0;
     t.nz = g.nz;
     t.n_frames = (int)n_frames;
+#ifdef XS_BOUNDS_CHECK
+    t.check_frames = (int)n_frames - (check_short_output() ? 1 : 0);
+#endif
     return t;
 }
 
@@ -1093,6 +1156,10 @@ cudaError_t launch_tc_single(const TcTraj& tr, int n_pairs, const TcSplit& sp, i
         if (!split_buf) return cudaErrorInvalidValue;
         a.partial = static_cast<double2*>(split_buf);
     }
+#ifdef XS_BOUNDS_CHECK
+    a.scratch_f2 = (int64_t)(tc_scratch_bytes(n_pairs) / sizeof(float2));
+    a.partial_n = (int64_t)(tc_split_bytes(sp) / sizeof(double2));
+#endif
     const int64_t pieces = sp.full * n_pairs + sp.rem * sp.parts;
     n_pairs = (int)std::min<int64_t>(n_pairs, pieces);
     return launch(a, n_pairs, bf16, tr.kind, tr.exact != 0, st);
@@ -1126,6 +1193,9 @@ cudaError_t launch_tc_batch(const TcTraj* d_trajs, const int4* d_units, const in
     a.scratch = scratch;
     a.err = err;
     a.timeout_ns = timeout_ns;
+#ifdef XS_BOUNDS_CHECK
+    a.scratch_f2 = (int64_t)(tc_scratch_bytes(n_pairs) / sizeof(float2));
+#endif
     return launch(a, n_pairs, bf16, kind, exact, st);
 }
 

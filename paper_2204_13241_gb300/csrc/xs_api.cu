@@ -11,6 +11,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "xs_api.h"
 #include "xs_internal.h"
 
@@ -247,8 +249,15 @@ GridDesc to_desc(const xs_qgrid* g) { return GridDesc{g->nx0, g->nx, g->ny0, g->
 
 // Runs one launch_* call: counts its kernels and, when tracing, brackets it
 // with events on the launching stream.
+// Every launch group runs inside an NVTX range of its name ("phase", "tc",
+// ...), so a timeline tool shows the stages of a call; with no tool attached
+// the header-only NVTX calls return at once.
 template <class F>
 cudaError_t traced(xs_context* ctx, const char* name, cudaStream_t st, F&& launch) {
+    struct NvtxRange {
+        explicit NvtxRange(const char* n) { nvtxRangePushA(n); }
+        ~NvtxRange() { nvtxRangePop(); }
+    } range(name);
     const int64_t before = tl_kernel_launches;
     cudaEvent_t a = nullptr;
     if (ctx->prof_on) {
@@ -394,6 +403,7 @@ xs_status xs_sync_status(xs_context* ctx, void* cuda_stream) {
     XS_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
     if (word & kDevErrTimeout) return fail(XS_ERR_TIMEOUT, "a kernel wait timed out (device error word %d)", word);
     if (word & kDevErrNonFinite) return fail(XS_ERR_NUMERIC, "non-finite form factor, or a position that is non-finite or more than 2^18 cells from the origin (device error word %d)", word);
+    if (word & kDevErrBounds) return fail(XS_ERR_BOUNDS, "a bounds check failed and its access was skipped (device error word %d)", word);
     return XS_OK;
 }
 

@@ -10,6 +10,7 @@ namespace xs {
 enum : int {
     kDevErrTimeout = 1,    // a bounded wait expired
     kDevErrNonFinite = 2,  // a non-finite form factor, or a position non-finite or more than 2^18 cells out
+    kDevErrBounds = 4,     // a bounds check of the checked build failed (the access was skipped)
 };
 
 // 3x3 inverse cell matrix (row-major), passed by value to kernels.
@@ -30,6 +31,20 @@ struct AtomRec {
 __device__ __forceinline__ void set_dev_error(int* err, int bit) {
     if (err) atomicOr(err, bit);
 }
+
+// Bounds checks of the checked build (compiled with -DXS_BOUNDS_CHECK): a
+// failed check sets kDevErrBounds in the device error word and the caller
+// skips the access; no assert, no trap.  In the normal build the condition
+// is not evaluated.
+#ifdef XS_BOUNDS_CHECK
+__device__ __forceinline__ bool xs_in_bounds(int* err, bool ok) {
+    if (!ok) set_dev_error(err, kDevErrBounds);
+    return ok;
+}
+#define XS_IN_BOUNDS(err, cond) ::xs::xs_in_bounds((err), (cond))
+#else
+#define XS_IN_BOUNDS(err, cond) true
+#endif
 
 // Phase factor exp(+i 2 pi P / 2^32) for a 32-bit turn count P.
 __device__ __forceinline__ void phase_to_cs(uint32_t P, float& c, float& s) {

@@ -92,6 +92,9 @@ struct TcTraj {
     int kind;      // tile kind (all trajectories of one launch share it)
     int chunk;     // stages per FP32 accumulation chunk; 0: the launch's
     int exact;     // 1: tables from FP64 sincospi per entry (test and measurement option)
+#ifdef XS_BOUNDS_CHECK
+    int check_frames;  // frames of I and amp the bounds check admits (n_frames; one less in the self-test)
+#endif
 };
 bool tc_supported(const GridDesc& g);
 int64_t tc_atom_multiple();
