@@ -383,9 +383,9 @@ XS_API xs_status xs_ring_index(const xs_qgrid* grid, const xs_box* box, double r
  *   dL_dr_out  device float32 [n_atoms][3]
  * The contraction over n_y runs on tensor cores in split BF16 (FP32
  * accumulation; relative error near 1e-5), the rest in FP32; every grid shape
- * is accepted.  Uses context workspace for H = dL/dI conj(S) and its
- * tensor-core images (8 B per pixel plus 16 KB per 32 (n_x, n_z) rows and 16
- * n_y).
+ * is accepted.  Uses context workspace for the tensor-core images of
+ * H = dL/dI conj(S) (32 B per pixel, with (n_x, n_z) rows rounded up to 64
+ * and n_y to 32) and per-atom partial sums (12 B per atom and 64 rows).
  */
 XS_API xs_status xs_intensity_backward(xs_context* ctx, const xs_traj* traj, const xs_qgrid* grid,
                                 const float* amp, const float* dL_dI, float* dL_dr_out,

@@ -9,42 +9,19 @@
 // with Z(x,z) = sum_y H(x,y,z) E_y and Z_y(x,z) = sum_y n_y H(x,y,z) E_y:
 // two complex contractions over n_y followed by per-atom sums over n_x, n_z.
 //
-// h_kernel forms H; the contractions and the per-atom sums run on tensor
-// cores in k_adjoint_tc.cu.
+// H is formed where it is used, by the kernel that writes the swizzled H image
+// of the tensor-core contraction (k_adjoint_tc.cu); the contractions and the
+// per-atom sums run there too.
 #include "xs_internal.h"
 
 namespace xs {
 
-namespace {
-
-__global__ void h_kernel(const float* __restrict__ amp, const float* __restrict__ G, int64_t P,
-                         float2* __restrict__ H) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-        const float g = G[p];
-        H[p] = make_float2(g * amp[2 * p], -g * amp[2 * p + 1]);
-    }
-}
-
-}  // namespace
-
-static size_t h_bytes(const GridDesc& g) { return ((size_t)g.pixels() * sizeof(float2) + 1023) & ~(size_t)1023; }
-
-size_t adjoint_workspace_bytes(const GridDesc& g, int64_t n_pad) {
-    return h_bytes(g) + adjoint_tc_image_bytes(g, n_pad);
-}
+size_t adjoint_workspace_bytes(const GridDesc& g, int64_t n_pad) { return adjoint_tc_image_bytes(g, n_pad); }
 
 cudaError_t launch_adjoint(const AtomRec* rec, int64_t n_atoms, int64_t n_pad, const GridDesc& g,
                            const Mat3& hinv, const float* amp, const float* dL_dI, void* workspace,
                            float* grad, int* err, int64_t timeout_ns, cudaStream_t st) {
-    const int64_t P = g.pixels();
-    float2* H = static_cast<float2*>(workspace);
-    const int64_t hb = min((P + 255) / 256, (int64_t)4096);
-    ++tl_kernel_launches;
-    h_kernel<<<(unsigned)hb, 256, 0, st>>>(amp, dL_dI, P, H);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_adjoint_tc(rec, n_atoms, n_pad, g, hinv, H, static_cast<char*>(workspace) + h_bytes(g), grad, err,
-                             timeout_ns, st);
+    return launch_adjoint_tc(rec, n_atoms, n_pad, g, hinv, amp, dL_dI, workspace, grad, err, timeout_ns, st);
 }
 
 }  // namespace xs

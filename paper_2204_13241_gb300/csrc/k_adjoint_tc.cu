@@ -1,4 +1,4 @@
-// Tensor-core kernels of the adjoint (k_adjoint.cu forms H and launches them).
+// Tensor-core kernels of the adjoint (the sums they compute are derived in k_adjoint.cu).
 //
 // With H_q = G_q conj(S_q) and rows q = (n_x, n_z) of the grid,
 //   Z(q, j)   = sum_y H(q, y) E_y(y, j),    Z_y(q, j) = sum_y n_y H(q, y) E_y(y, j),
@@ -272,9 +272,10 @@ __host__ __device__ __forceinline__ uint32_t at_chunk_mn(int mn, int k) {
 // The H image: per (row tile rt, stage s, CTA half r) 32 KB = [hi 16 KB | lo
 // 16 KB] of 128 rows (kind 2r + (row >> 6), q = 64 rt + (row & 63)) by 64 k'
 // (n_y = 32 s + k' / 2), MN-major with 128-byte swizzle.  One thread per
-// element (hi and lo).
-__global__ void adjoint_image_kernel(const float2* __restrict__ H, GridDesc g, int n_rt, int n_st,
-                                     uint8_t* __restrict__ img) {
+// element (hi and lo), which forms H_q = G_q conj(S_q) from the amplitude
+// (interleaved re, im) and dL/dI where it reads them.
+__global__ void adjoint_image_kernel(const float* __restrict__ amp, const float* __restrict__ G, GridDesc g,
+                                     int n_rt, int n_st, uint8_t* __restrict__ img) {
     const int64_t n = (int64_t)n_rt * n_st * 2 * 128 * kAtK;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -292,7 +293,9 @@ __global__ void adjoint_image_kernel(const float2* __restrict__ H, GridDesc g, i
     float v = 0.0f;
     if (q < (int64_t)g.nx * g.nz && y < g.ny) {
         const int64_t x = q % g.nx, z = q / g.nx;
-        const float2 h = H[(z * g.ny + y) * g.nx + x];
+        const int64_t pix = (z * g.ny + y) * g.nx + x;
+        const float gq = G[pix];
+        const float2 h = make_float2(gq * amp[2 * pix], -gq * amp[2 * pix + 1]);
         const bool im_row = (kind & 1) != 0;
         v = p == 0 ? (im_row ? h.y : h.x) : (im_row ? h.x : -h.y);
         if (kind >= 2) v *= (float)(g.ny0 + y);
@@ -320,10 +323,24 @@ adjoint_tc_kernel(const AtomRec* __restrict__ rec, int64_t n_pad, GridDesc g, co
     const uint32_t rank = at_rank();  // 0: issues the MMAs of the pair
     const int64_t pair = blockIdx.x >> 1, n_pairs = gridDim.x >> 1;
 
-    for (int i = tid; i < kAtTab; i += kAtThreads) {
+    // exp(i 2 pi k / 256): FP64 sincospi on the first octant (k <= 32) only,
+    // the rest by the exact symmetries exp(i(pi/2 - t)) = i conj(exp(i t)) and
+    // exp(i(t + pi/2)) = i exp(i t).  FP64 runs at a small fraction of the
+    // FP32 rate, and 33 evaluations instead of 256 shorten the kernel's start.
+    constexpr int kOct = kAtTab / 8, kQuad = kAtTab / 4;
+    if (tid <= kOct) {
         double s, c;
-        sincospi((double)i / (kAtTab / 2), &s, &c);
-        ctl->tab[i] = make_float2((float)c, (float)s);
+        sincospi((double)tid / (kAtTab / 2), &s, &c);
+        ctl->tab[tid] = make_float2((float)c, (float)s);
+    }
+    __syncthreads();
+    for (int i = tid; i < kAtTab; i += kAtThreads) {
+        if (i <= kOct) continue;
+        const int q = i / kQuad, r = i % kQuad;
+        float2 v = ctl->tab[r <= kOct ? r : kQuad - r];
+        if (r > kOct) v = make_float2(v.y, v.x);
+        for (int k = 0; k < q; ++k) v = make_float2(-v.y, v.x);
+        ctl->tab[i] = v;
     }
     if (tid == kAtMmaWarp * 32) {
         for (int s = 0; s < kAtStages; ++s) {
@@ -643,7 +660,7 @@ size_t adjoint_tc_image_bytes(const GridDesc& g, int64_t n_pad) {
 }
 
 cudaError_t launch_adjoint_tc(const AtomRec* rec, int64_t n_atoms, int64_t n_pad, const GridDesc& g,
-                              const Mat3& hinv, const float2* H, void* image, float* grad, int* err,
+                              const Mat3& hinv, const float* amp, const float* G, void* image, float* grad, int* err,
                               int64_t timeout_ns, cudaStream_t st) {
     const int64_t n_rt = ((int64_t)g.nx * g.nz + kAtQ - 1) / kAtQ;
     const int64_t n_st = ((int64_t)g.ny + kAtK / 2 - 1) / (kAtK / 2);
@@ -652,7 +669,7 @@ cudaError_t launch_adjoint_tc(const AtomRec* rec, int64_t n_atoms, int64_t n_pad
     uint8_t* img = static_cast<uint8_t*>(image);
     const int64_t n_el = n_rt * n_st * 2 * 128 * kAtK;
     ++tl_kernel_launches;
-    adjoint_image_kernel<<<(unsigned)((n_el + 255) / 256), 256, 0, st>>>(H, g, (int)n_rt, (int)n_st, img);
+    adjoint_image_kernel<<<(unsigned)((n_el + 255) / 256), 256, 0, st>>>(amp, G, g, (int)n_rt, (int)n_st, img);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(adjoint_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAtSmemBytes);

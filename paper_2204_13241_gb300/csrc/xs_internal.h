@@ -200,12 +200,12 @@ size_t adjoint_workspace_bytes(const GridDesc& g, int64_t n_pad);
 cudaError_t launch_adjoint(const AtomRec* rec, int64_t n_atoms, int64_t n_pad, const GridDesc& g,
                            const Mat3& hinv, const float* amp, const float* dL_dI,
                            void* workspace, float* grad, int* err, int64_t timeout_ns, cudaStream_t st);
-// the contraction over n_y on tensor cores (split BF16): H images built
-// from H [P] and the per-unit partial sums, adjoint_tc_image_bytes(g, n_pad)
-// bytes (16-byte aligned)
+// the contraction over n_y on tensor cores (split BF16): the H image, built
+// from amp [P][2] and dL/dI [P], and the per-unit partial sums,
+// adjoint_tc_image_bytes(g, n_pad) bytes (16-byte aligned)
 size_t adjoint_tc_image_bytes(const GridDesc& g, int64_t n_pad);
 cudaError_t launch_adjoint_tc(const AtomRec* rec, int64_t n_atoms, int64_t n_pad, const GridDesc& g,
-                              const Mat3& hinv, const float2* H, void* image, float* grad, int* err,
+                              const Mat3& hinv, const float* amp, const float* G, void* image, float* grad, int* err,
                               int64_t timeout_ns, cudaStream_t st);
 
 }  // namespace xs
