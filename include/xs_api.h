@@ -417,7 +417,8 @@ XS_API xs_status xs_tuned_choice(xs_context* ctx, int64_t n_atoms, const xs_qgri
 XS_API const char* xs_last_error(void);
 
 /* Waits for `cuda_stream`, then reads and clears the device error word:
- * XS_ERR_TIMEOUT, XS_ERR_NUMERIC or XS_OK. */
+ * XS_ERR_TIMEOUT, XS_ERR_NUMERIC, XS_ERR_BOUNDS (checked build only) or
+ * XS_OK. */
 XS_API xs_status xs_sync_status(xs_context* ctx, void* cuda_stream);
 
 /* Table builder of the split-precision (tensor-core) paths, a test and

@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "xs_internal.h"
+#include "xs_phase.cuh"
 
 namespace xs {
 
@@ -34,120 +35,25 @@ constexpr int kDirectThreads = 256;
 constexpr int kDirectPX = 4;     // pixels per thread
 constexpr int kAtomTile = 256;   // atom records staged per shared-memory tile
 
-// hs = 2^32 h^-1 (a power-of-two scaling, exact): rint(hs r) mod 2^32 equals
-// rint(frac(h^-1 r) 2^32) mod 2^32.  Adding M = 1.5 * 2^52 to |v| < 2^51 gives
-// M + rint(v) (ties to even) in one FP64 rounding, and the low 32 bits of that
-// sum's encoding are rint(v) mod 2^32.
-constexpr double kRoundMagic = 6755399441055744.0;      // 1.5 * 2^52
-constexpr double kTurnLimit = 1125899906842624.0;       // 2^50: |v| bound checked
-__device__ __forceinline__ uint32_t turns_of(double v) { return (uint32_t)__double2loint(v + kRoundMagic); }
-
-// The count for an orthorhombic cell in integer arithmetic: x = +-m 2^ex
-// (m the float's 24-bit significand) times c = +-cm 2^ce (cm < 2^53) is the
-// exact product m cm = H 2^32 + L (two 32 x 32 -> 64-bit multiplies, H <
-// 2^45) scaled by 2^-d, d = -(ex + ce).  The turns are bits d.. of m cm,
-// rounded to nearest with ties to even from the bit below (rb) and those
-// under it (sticky), as the FP64 rounding above does.  GB300 issues FP64 at a
-// small fraction of its integer rate, and this was the phase kernel's only
-// FP64 work.
-__device__ __forceinline__ uint32_t turns_int(float x, uint32_t ch, uint32_t cl, int ce, uint32_t cneg) {
-    const uint32_t b = __float_as_uint(x);
-    const uint32_t E = (b >> 23) & 0xffu;
-    const uint32_t m = E ? ((b & 0x7fffffu) | 0x800000u) : (b & 0x7fffffu);
-    const int d = -((E ? (int)E - 150 : -149) + ce);
-    const uint64_t A = (uint64_t)m * cl;
-    const uint64_t H = (uint64_t)m * ch + (A >> 32);
-    const uint32_t L = (uint32_t)A;
-    uint32_t u;
-    if (d > 32 && d <= 77) {  // the usual case: |x c| < 2^45
-        const int e = d - 32;
-        const uint32_t q = (uint32_t)(H >> e);
-        const uint32_t rb = (uint32_t)(H >> (e - 1)) & 1u;
-        const uint32_t st = ((H & ((1ull << (e - 1)) - 1ull)) != 0ull || L != 0u) ? 1u : 0u;
-        u = q + (rb & (st | (q & 1u)));
-    } else if (d > 77) {
-        u = 0u;  // |x c| < 1/2
-    } else if (d > 0) {
-        const uint32_t q = d == 32 ? (uint32_t)H : (((uint32_t)H << (32 - d)) | (L >> d));
-        const uint32_t rb = (L >> (d - 1)) & 1u;
-        const uint32_t st = (L & ((1u << (d - 1)) - 1u)) != 0u ? 1u : 0u;
-        u = q + (rb & (st | (q & 1u)));
-    } else {
-        u = d <= -32 ? 0u : L << -d;
-    }
-    return ((b >> 31) ^ cneg) ? 0u - u : u;
-}
 
 constexpr int kPhaseFrames = 8;  // frames per block of the phase kernel
 
 // grid: x = blocks of 256 slots, y = groups of kPhaseFrames frames; the atom of
 // a slot (one 64-bit modulo) is computed once and reused for every frame
-__global__ void __launch_bounds__(256)
-phase_kernel(const float* __restrict__ pos, const float* __restrict__ f, int64_t n_atoms, int64_t n_frames,
-             int64_t n_pad, Mat3 hs, PhaseOpts opt, AtomRec* __restrict__ rec, int* err) {
+__global__ void __launch_bounds__(256) phase_kernel(PhaseSrc ps, int64_t n_frames, int* err) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= n_pad) return;
-    const int64_t j = opt.perm_mul == 1 ? k
-                                        : (int64_t)(((uint64_t)(k / kPermRun) * (uint64_t)opt.perm_mul) %
-                                                    (uint64_t)(n_pad / kPermRun)) * kPermRun + k % kPermRun;
-    if (!XS_IN_BOUNDS(err, j >= 0 && j < n_pad)) return;
-    const bool real = j < n_atoms;
-    // atom j of this call is atom a of the frames (a subset when an index is given)
-    const int64_t a = (opt.index && real) ? (int64_t)opt.index[j] : j;
-    const int64_t stride = opt.index ? opt.pos_atoms : n_atoms;
-    if (real && !XS_IN_BOUNDS(err, a >= 0 && a < stride)) return;
-    const float fj = real ? f[a] : 0.0f;
+    if (k >= ps.n_pad) return;
+    int64_t a = 0;
+    float fj = 0.0f;
+    const bool real = slot_atom(ps, k, a, fj, err);
     const int64_t t0 = (int64_t)blockIdx.y * kPhaseFrames;
     const int64_t t1 = min(n_frames, t0 + kPhaseFrames);
     for (int64_t t = t0; t < t1; ++t) {
         AtomRec r;
         r.ux = r.uy = r.uz = 0u;
         r.f = 0.0f;
-        if (real) {
-            const int64_t idx = t * stride + a;
-            const float* p = pos + idx * 3;
-            float x, y, z;
-            if (opt.pos8) {
-                // with `pos` 8-byte aligned, the 12-byte position is one aligned
-                // 8-byte load and one 4-byte load: (x, y) + z at an even index,
-                // x + (y, z) at an odd one
-                const int odd = (int)(idx & 1);
-                const float2 v2 = *reinterpret_cast<const float2*>(p + odd);
-                const float v1 = p[odd ? 0 : 2];
-                x = odd ? v1 : v2.x;
-                y = odd ? v2.x : v2.y;
-                z = odd ? v2.y : v1;
-            } else {
-                x = p[0];
-                y = p[1];
-                z = p[2];
-            }
-            // NaN and Inf fail these comparisons too
-            bool ok = isfinite(fj);
-            if (opt.ortho) {
-                ok = ok && fabsf(x) < opt.lim[0] && fabsf(y) < opt.lim[1] && fabsf(z) < opt.lim[2];
-                if (ok) {
-                    r.ux = turns_int(x, opt.ch[0], opt.cl[0], opt.ce[0], opt.cneg[0]);
-                    r.uy = turns_int(y, opt.ch[1], opt.cl[1], opt.ce[1], opt.cneg[1]);
-                    if (opt.need_z) r.uz = turns_int(z, opt.ch[2], opt.cl[2], opt.ce[2], opt.cneg[2]);
-                }
-            } else {
-                const double vx = hs.a[0] * x + hs.a[1] * y + hs.a[2] * z;
-                const double vy = hs.a[3] * x + hs.a[4] * y + hs.a[5] * z;
-                const double vz = hs.a[6] * x + hs.a[7] * y + hs.a[8] * z;
-                ok = ok && fabs(vx) < kTurnLimit && fabs(vy) < kTurnLimit && fabs(vz) < kTurnLimit;
-                if (ok) {
-                    r.ux = turns_of(vx);
-                    r.uy = turns_of(vy);
-                    if (opt.need_z) r.uz = turns_of(vz);
-                }
-            }
-            if (ok)
-                r.f = fj;
-            else
-                set_dev_error(err, kDevErrNonFinite);
-        }
-        rec[t * n_pad + k] = r;
+        if (real) r = rec_of_atom(ps, t, a, fj, err);
+        ps.rec[t * ps.n_pad + k] = r;
     }
 }
 
@@ -265,23 +171,24 @@ __global__ void reduce_kernel(const double2* __restrict__ partial, int splits, i
 
 }  // namespace
 
-cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int64_t n_frames,
-                         int64_t n_pad, const Mat3& hinv, const PhaseOpts& opt, AtomRec* rec, int* err,
-                         cudaStream_t st) {
-    if (n_frames * n_pad == 0) return cudaSuccess;
-    const int64_t gy = (n_frames + kPhaseFrames - 1) / kPhaseFrames;
-    if (gy > 65535) return cudaErrorInvalidConfiguration;
-    Mat3 hs;
-    for (int i = 0; i < 9; ++i) hs.a[i] = hinv.a[i] * 4294967296.0;
-    PhaseOpts o = opt;
-    o.pos8 = ((uintptr_t)pos & 7u) == 0;
+bool make_phase_src(const float* pos, const float* f, int64_t n_atoms, int64_t n_pad, const Mat3& hinv,
+                    const PhaseOpts& opt, AtomRec* rec, PhaseSrc& ps) {
     // atom of slot k = kPermRun ((k / kPermRun) a mod n_pad / kPermRun) + k mod
     // kPermRun; the products stay below 2^64
-    if (o.perm_mul != 1 && (n_pad >= ((int64_t)1 << 32) || n_pad % kPermRun != 0)) return cudaErrorInvalidValue;
+    if (opt.perm_mul != 1 && (n_pad >= ((int64_t)1 << 32) || n_pad % kPermRun != 0)) return false;
+    ps.pos = pos;
+    ps.f = f;
+    ps.n_atoms = n_atoms;
+    ps.n_pad = n_pad;
+    ps.rec = rec;
+    for (int i = 0; i < 9; ++i) ps.hs.a[i] = hinv.a[i] * 4294967296.0;
+    PhaseOpts& o = ps.opt;
+    o = opt;
+    o.pos8 = ((uintptr_t)pos & 7u) == 0;
     // orthorhombic cells: |x| < lim_x keeps |hs_xx x| below 2^50 (the FP32
     // bound is rounded down, so the check is conservative)
     for (int a = 0; a < 3; ++a) {
-        const double d = std::fabs(hs.a[4 * a]);
+        const double d = std::fabs(ps.hs.a[4 * a]);
         o.lim[a] = d > 0.0 ? std::nextafter((float)(1125899906842624.0 / d), 0.0f) : 3.0e38f;
         // d = cm 2^ce with cm < 2^53 an integer (exact: frexp only moves the exponent)
         int e = 0;
@@ -290,11 +197,22 @@ cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int6
         o.ch[a] = (uint32_t)(cm >> 32);
         o.cl[a] = (uint32_t)cm;
         o.ce[a] = e - 53;
-        o.cneg[a] = hs.a[4 * a] < 0.0 ? 1u : 0u;
+        o.cneg[a] = ps.hs.a[4 * a] < 0.0 ? 1u : 0u;
     }
+    return true;
+}
+
+cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int64_t n_frames,
+                         int64_t n_pad, const Mat3& hinv, const PhaseOpts& opt, AtomRec* rec, int* err,
+                         cudaStream_t st) {
+    if (n_frames * n_pad == 0) return cudaSuccess;
+    const int64_t gy = (n_frames + kPhaseFrames - 1) / kPhaseFrames;
+    if (gy > 65535) return cudaErrorInvalidConfiguration;
+    PhaseSrc ps;
+    if (!make_phase_src(pos, f, n_atoms, n_pad, hinv, opt, rec, ps)) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((n_pad + 255) / 256), (unsigned)gy);
     ++tl_kernel_launches;
-    phase_kernel<<<grid, 256, 0, st>>>(pos, f, n_atoms, n_frames, n_pad, hs, o, rec, err);
+    phase_kernel<<<grid, 256, 0, st>>>(ps, n_frames, err);
     return cudaGetLastError();
 }
 

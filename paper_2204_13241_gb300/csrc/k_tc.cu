@@ -530,10 +530,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
     const uint32_t rank = cluster_rank();  // 0: issues the MMAs of the pair
     const int64_t pair = blockIdx.x >> 1, n_pairs = gridDim.x >> 1;
 
-    for (int i = threadIdx.x; i < 256; i += L::kThreads) {
+    // exp(i 2 pi k / 256): FP64 sincospi on the first octant (k <= 32) only,
+    // the rest by the exact symmetries exp(i(pi/2 - t)) = i conj(exp(i t)) and
+    // exp(i(t + pi/2)) = i exp(i t) (FP64 runs at a small fraction of the
+    // FP32 rate); the cluster barrier below orders the table for every warp
+    if (threadIdx.x <= 32) {
         double sn, cs;
-        sincospi((double)i / 128, &sn, &cs);
-        ctl->tab[i] = make_float2((float)cs, (float)sn);
+        sincospi((double)threadIdx.x / 128, &sn, &cs);
+        ctl->tab[threadIdx.x] = make_float2((float)cs, (float)sn);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += L::kThreads) {
+        if (i <= 32) continue;
+        const int q = i >> 6, r = i & 63;
+        float2 v = ctl->tab[r <= 32 ? r : 64 - r];
+        if (r > 32) v = make_float2(v.y, v.x);
+        for (int j = 0; j < q; ++j) v = make_float2(-v.y, v.x);
+        ctl->tab[i] = v;
     }
     if (threadIdx.x == kMmaWarp * 32) {
         for (int s = 0; s < kStages; ++s) {

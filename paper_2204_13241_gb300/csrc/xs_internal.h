@@ -46,6 +46,21 @@ struct PhaseOpts {
 cudaError_t launch_phase(const float* pos, const float* f, int64_t n_atoms, int64_t n_frames,
                          int64_t n_pad, const Mat3& hinv, const PhaseOpts& opt, AtomRec* rec, int* err,
                          cudaStream_t st);
+// What the phase kernel needs to build the record of any (frame, slot):
+// `opt` completed by make_phase_src, hs = 2^32 h^-1.
+struct PhaseSrc {
+    const float* pos = nullptr;  // frame 0 of the records: [frames][stride][3]
+    const float* f = nullptr;
+    int64_t n_atoms = 0;
+    int64_t n_pad = 0;
+    Mat3 hs;
+    PhaseOpts opt;
+    AtomRec* rec = nullptr;      // [frames][n_pad]
+};
+// Completes `opt` for the kernels; false when the permutation's products could
+// overflow (perm_mul != 1 with n_pad >= 2^32 or not a multiple of kPermRun)
+bool make_phase_src(const float* pos, const float* f, int64_t n_atoms, int64_t n_pad, const Mat3& hinv,
+                    const PhaseOpts& opt, AtomRec* rec, PhaseSrc& out);
 
 // ---- plain FP32 direct sum ----------------------------------------------
 struct DirectPlan {
