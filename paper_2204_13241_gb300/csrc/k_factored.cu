@@ -27,7 +27,11 @@ namespace {
 constexpr int kFxTile = 64;     // n_x and n_y per block
 constexpr int kFxAtoms = 32;    // atoms per stage
 constexpr int kFxThreads = 256;
-constexpr size_t kFxSmemBytes = 2 * 2 * kFxAtoms * kFxTile * sizeof(float2);  // E_x and W, two buffers: 64 KB
+constexpr size_t kFxTabBytes = 2 * 2 * kFxAtoms * kFxTile * sizeof(float2);  // E_x and W, two buffers: 64 KB
+// plus the low parts of the running totals, [32 values][256 threads] (32 KB):
+// kept in shared memory, where they are touched once per stage, instead of
+// 32 registers that the inner loop needs
+constexpr size_t kFxSmemBytes = kFxTabBytes + 32 * kFxThreads * sizeof(float);
 
 struct FxArgs {
     const AtomRec* rec;
@@ -47,13 +51,24 @@ __device__ __forceinline__ float2 fx_cis(uint32_t P) {
     return make_float2(c, s);
 }
 
+// Shared-memory layout of a table row (one atom, 64 complex entries = 512 B):
+// four 128-byte lines of 16 entries, each line eight 16-byte chunks of two
+// entries.  Chunk c of line l (l = 4 atom + segment) is stored at position
+// c ^ (l & 7): a table builder's store instruction has its 32 threads on 32
+// lines at the same chunk, which without the swizzle would fall on the same
+// banks (32 wavefronts instead of 4), while the readers' loads of one atom
+// stay within one line (E_x) or two lines at disjoint positions (W).
+__device__ __forceinline__ int fx_slot(int atom, int seg, int chunk) {
+    return atom * kFxTile + seg * 16 + 2 * (chunk ^ ((atom * 4 + seg) & 7));
+}
+
 // TwoSum: hi + lo += c with the rounding error of hi + c carried in lo
-__device__ __forceinline__ void two_sum(float& hi, float& lo, float c) {
+__device__ __forceinline__ void two_sum(float& hi, float* lo, float c) {
     const float s = hi + c;
     const float bb = s - hi;
     const float e = (hi - (s - bb)) + (c - bb);
     hi = s;
-    lo += e;
+    *lo += e;
 }
 
 // grid: x = (frame, plane, tile), y = atom split
@@ -87,11 +102,16 @@ __global__ void __launch_bounds__(kFxThreads, 2) fx_kernel(FxArgs a) {
 
     float sr[4][4], si[4][4];     // this stage's sums
     float hr[4][4], hi_[4][4];    // running totals, high parts
-    float lr[4][4], li[4][4];     // low parts
+    // low parts: value v = 2 (4 x + y) + (0: re, 1: im) of this thread
+    float* s_lo = reinterpret_cast<float*>(reinterpret_cast<char*>(fx_smem) + kFxTabBytes) + tid;
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) hr[x][y] = hi_[x][y] = lr[x][y] = li[x][y] = 0.0f;
+        for (int y = 0; y < 4; ++y) {
+            hr[x][y] = hi_[x][y] = 0.0f;
+            s_lo[(2 * (4 * x + y)) * kFxThreads] = 0.0f;
+            s_lo[(2 * (4 * x + y) + 1) * kFxThreads] = 0.0f;
+        }
 
     int buf = 0;
     for (int64_t k0 = a0; k0 < a1; k0 += kFxAtoms, buf ^= 1) {
@@ -116,7 +136,8 @@ __global__ void __launch_bounds__(kFxThreads, 2) fx_kernel(FxArgs a) {
                 }
             }
             const float2 z = fx_cis(U);
-            float2* dst = is_x ? &s_ex[buf][b_atom][16 * b_seg] : &s_w[buf][b_atom][16 * (b_seg - 4)];
+            float2* row = is_x ? &s_ex[buf][0][0] : &s_w[buf][0][0];
+            const int seg = b_seg & 3;
 #pragma unroll
             for (int run = 0; run < 4; ++run) {
                 const float2 e0 = fx_cis((n0 + 4u * (uint32_t)run) * U);
@@ -133,8 +154,8 @@ __global__ void __launch_bounds__(kFxThreads, 2) fx_kernel(FxArgs a) {
                 e = make_float2(fmaf(e.x, z.x, -e.y * z.y), fmaf(e.x, z.y, e.y * z.x));
                 v23.z = e.x;
                 v23.w = e.y;
-                *reinterpret_cast<float4*>(dst + 4 * run) = v01;
-                *reinterpret_cast<float4*>(dst + 4 * run + 2) = v23;
+                *reinterpret_cast<float4*>(row + fx_slot(b_atom, seg, 2 * run)) = v01;
+                *reinterpret_cast<float4*>(row + fx_slot(b_atom, seg, 2 * run + 1)) = v23;
             }
         }
         __syncthreads();  // the tables of this stage are complete; the other buffer's readers are done
@@ -144,10 +165,13 @@ __global__ void __launch_bounds__(kFxThreads, 2) fx_kernel(FxArgs a) {
             for (int y = 0; y < 4; ++y) sr[x][y] = si[x][y] = 0.0f;
 #pragma unroll 4
         for (int k = 0; k < kFxAtoms; ++k) {
-            const float4 e01 = *reinterpret_cast<const float4*>(&s_ex[buf][k][4 * xg]);
-            const float4 e23 = *reinterpret_cast<const float4*>(&s_ex[buf][k][4 * xg + 2]);
-            const float4 w01 = *reinterpret_cast<const float4*>(&s_w[buf][k][4 * yg]);
-            const float4 w23 = *reinterpret_cast<const float4*>(&s_w[buf][k][4 * yg + 2]);
+            // entries 4 xg .. 4 xg + 3: chunks 2 (xg & 3), +1 of line segment xg >> 2
+            const float2* ex = &s_ex[buf][0][0];
+            const float2* wy = &s_w[buf][0][0];
+            const float4 e01 = *reinterpret_cast<const float4*>(ex + fx_slot(k, xg >> 2, 2 * (xg & 3)));
+            const float4 e23 = *reinterpret_cast<const float4*>(ex + fx_slot(k, xg >> 2, 2 * (xg & 3) + 1));
+            const float4 w01 = *reinterpret_cast<const float4*>(wy + fx_slot(k, yg >> 2, 2 * (yg & 3)));
+            const float4 w23 = *reinterpret_cast<const float4*>(wy + fx_slot(k, yg >> 2, 2 * (yg & 3) + 1));
             const float ex_r[4] = {e01.x, e01.z, e23.x, e23.z}, ex_i[4] = {e01.y, e01.w, e23.y, e23.w};
             const float w_r[4] = {w01.x, w01.z, w23.x, w23.z}, w_i[4] = {w01.y, w01.w, w23.y, w23.w};
 #pragma unroll
@@ -162,8 +186,8 @@ __global__ void __launch_bounds__(kFxThreads, 2) fx_kernel(FxArgs a) {
         for (int x = 0; x < 4; ++x)
 #pragma unroll
             for (int y = 0; y < 4; ++y) {
-                two_sum(hr[x][y], lr[x][y], sr[x][y]);
-                two_sum(hi_[x][y], li[x][y], si[x][y]);
+                two_sum(hr[x][y], &s_lo[(2 * (4 * x + y)) * kFxThreads], sr[x][y]);
+                two_sum(hi_[x][y], &s_lo[(2 * (4 * x + y) + 1) * kFxThreads], si[x][y]);
             }
     }
 
@@ -176,8 +200,8 @@ __global__ void __launch_bounds__(kFxThreads, 2) fx_kernel(FxArgs a) {
         for (int y = 0; y < 4; ++y) {
             const int iy = y0 + 4 * yg + y;
             if (iy >= g.ny) continue;
-            const double re = (double)hr[x][y] + (double)lr[x][y];
-            const double im = (double)hi_[x][y] + (double)li[x][y];
+            const double re = (double)hr[x][y] + (double)s_lo[(2 * (4 * x + y)) * kFxThreads];
+            const double im = (double)hi_[x][y] + (double)s_lo[(2 * (4 * x + y) + 1) * kFxThreads];
             const int64_t p = ((int64_t)iz * g.ny + iy) * g.nx + ix;
             if (gridDim.y > 1) {
                 a.partial[((int64_t)split * a.n_frames + t) * P + p] = make_double2(re, im);
