@@ -442,6 +442,15 @@ __device__ __forceinline__ uint4 load_rec(const Unit& u, const uint4* p, int* er
     return __ldg(p);
 }
 
+// A tile with at most kHalf valid n_x rows (a grid at most 64 wide, or the
+// last tile of one): each CTA of the pair takes kHalf / 2 of them, and the A
+// runs past those are not built.  The rows left unbuilt hold whatever the
+// stage held; their products only reach accumulator rows the epilogue drops.
+// Not for centred tiles, which have their own row order.
+__device__ __forceinline__ bool unit_narrow(const Unit& u, bool centred) {
+    return !centred && u.nx - u.tx * kTile <= kHalf;
+}
+
 __device__ __forceinline__ Unit single_unit(const TcTraj& tr, int64_t u) {
     const int tx = (int)(u % tr.tiles_x);
     int64_t r = u / tr.tiles_x;
@@ -599,9 +608,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
             const uint4* rec_cur = up.rec + k;
             const bool centred = KIND == kTcTile128 && up.centred;
             const bool extra = centred && (ri & 1) == 0;  // also builds X(32 rank + 32)
+            const bool narrow = unit_narrow(up, centred);
+            const bool idle = is_a && narrow && run0 >= kHalf / 2;  // an A run past the narrow rows
             const uint32_t n0 =
                 centred ? (uint32_t)(32 * (int)rank + s0)
-                        : (is_a ? (uint32_t)(up.nx0 + up.tx * kTile + kHalf * (int)rank + run0)
+                        : (is_a ? (uint32_t)(up.nx0 + up.tx * kTile + (narrow ? kHalf / 2 : kHalf) * (int)rank + run0)
                                 : (uint32_t)(up.ny0 + up.ty * C::kTileY + (C::kTileY / 2) * (int)rank + run0));
             const uint32_t nz = (uint32_t)(up.nz0 + up.iz);
             for (int s = up.s0; s < st1; ++s) {
@@ -610,6 +621,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
                     r_next = load_rec(up, rec_cur + (int64_t)(s + 1) * kBK, args.err);
                 else if (has_next)
                     r_next = load_rec(up_next, up_next.rec + (int64_t)up_next.s0 * kBK + k, args.err);
+                if (idle) {
+                    // nothing to build: take the slot and pass it on
+                    if (!wait_bar(&ctl->empty[slot], phase ^ 1u, abort_flag, args.err, args.timeout_ns, 20000u)) {
+                        stop = true;
+                        break;
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_local(rank == 0 ? &ctl->full[slot] : &ctl->fill[slot]);
+                    if (++slot == kStages) {
+                        slot = 0;
+                        phase ^= 1u;
+                    }
+                    continue;
+                }
                 // seed E(n0) and z = E(1) of this thread's run, E(n0 + 1) = E(n0) z
                 // and the step z^2 (two table evaluations instead of three
                 // made producer-bound tiles 2-7% faster, at the same error)
@@ -830,7 +855,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
             const int cs = up.chunk > 0 ? up.chunk : args.chunk_stages;
             const int n_chunks = (up.s1 - up.s0 + cs - 1) / cs;
             const bool centred = KIND == kTcTile128 && up.centred;
-            const int xi = centred ? xi_c : kHalf * (int)rank + x_slot;
+            // narrow tiles: rows x_slot < kHalf / 2 hold n_x (kHalf / 2) rank +
+            // x_slot, the others were not built (-1: nothing written)
+            const int xi = centred ? xi_c
+                                   : (unit_narrow(up, centred) ? (x_slot < kHalf / 2 ? (kHalf / 2) * (int)rank + x_slot : -1)
+                                                               : kHalf * (int)rank + x_slot);
             const double sx = centred ? (double)sx_c : 1.0;  // sign of the stored Im x rows
             for (int c = 0; c < n_chunks; ++c, ++a_cnt) {
                 const int b = (int)(a_cnt & 1);
@@ -901,11 +930,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lay<KIND>::kThreads,
                     }
                     const int ix = up.tx * kTile + xi;
                     // a piece of a split unit keeps its partial amplitude of every pixel
-                    double2* part_dst = up.split >= 0 ? args.partial +
-                                                            ((size_t)up.split * args.parts + up.part) * (kTile * kTile) +
-                                                            (size_t)xi * kTile
-                                                      : nullptr;
-                    if (part_dst || ix < up.nx) {
+                    double2* part_dst = up.split >= 0 && xi >= 0
+                                            ? args.partial +
+                                                  ((size_t)up.split * args.parts + up.part) * (kTile * kTile) +
+                                                  (size_t)xi * kTile
+                                            : nullptr;
+                    if (xi >= 0 && (part_dst || ix < up.nx)) {
 #pragma unroll
                         for (int hh = 0; hh < 2; ++hh) {
 #pragma unroll
