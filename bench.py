@@ -46,10 +46,10 @@ DIRECT_INST_PER_UNIT = 53.0
 
 # DRAM bytes (read + write) of one tc_kernel launch, from an ncu capture of
 # the 160-frame case of the same workload (dram__bytes_read.sum +
-# dram__bytes_write.sum: 656.03 MB + 14.47 MB), scaled by frames: the
+# dram__bytes_write.sum: 656.34 MB + 14.66 MB), scaled by frames: the
 # records read and the intensities written are per frame, the split pieces'
 # partials (a few MB) are not.  Reported only while k_tc.cu is unchanged.
-TC_TRAFFIC = {"k_tc_sha256_prefix": "0541fb23cfb2348e", "bytes": 656028416 + 14472704, "frames": 160}
+TC_TRAFFIC = {"k_tc_sha256_prefix": "245a3523b1588130", "bytes": 656344576 + 14661632, "frames": 160}
 
 
 def _args():

@@ -100,3 +100,21 @@ def test_batched_with_both_kinds_matches_single_calls(xs):
         assert e_I(got, ref_s, m)[0] <= 1e-4 and e_pix(got, ref_s, m) <= 2e-3
         ref = oracle.intensity(pos[T - 1:T], f, box, m)
         check_I(got[T - 1:T], ref, m, "bf16", what=str(grid))
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("N,T,grid", [
+    (3000, 3, wl.QGrid(-30, 60, -70, 140, 0, 1)),     # 60 n_x: narrow 128 x 128 tiles, two y tiles
+    (3000, 2, wl.QGrid(-100, 180, -40, 100, 0, 1)),   # the second x tile holds 52 rows
+    (16384, 1, wl.QGrid(-25, 50, -64, 128, 0, 1)),    # one narrow unit split along the atoms
+    (2000, 2, wl.QGrid(-12, 33, -20, 40, 1, 2)),      # 128 x 64 kind, 33 rows, q_z != 0
+])
+def test_narrow_tiles_against_oracle(xs, N, T, grid, prec):
+    # tiles with at most 64 valid n_x rows build only those rows, 32 per CTA
+    pos, f, box = _case(N + grid.nx, N, T, 26.0)
+    p, fd = torch.from_numpy(pos).cuda(), torch.from_numpy(f).cuda()
+    I, A = xs.intensity(p, fd, box, grid, prec, want_amp=True)
+    xs.Context.get().sync_status()
+    m = grid.miller()
+    S = oracle.amplitude(pos, f, box, m)
+    check_I(I.reshape(T, -1).cpu().numpy(), np.abs(S) ** 2, m, prec)
