@@ -1,8 +1,9 @@
 // Correlation stages on the intensity series I[t][p]:
 //   g2 (Sec. 2.3, Eq. g2_def) and the XSVS contrast (Eqs. inte_Iq, bq_Iq).
 //
-// g2_series_kernel (series of up to kG2sMaxT frames): a block copies the whole
-//   series of 32 consecutive pixels into shared memory once (128-byte rows),
+// g2_series_kernel (series of up to 3,200 frames): a block copies the whole
+//   series of W consecutive pixels into shared memory once (W = 32 up to
+//   1,600 frames, 16 up to 3,200, so that they fit in 200 KB),
 //   then each thread sums one pixel's products for a group of up to 4 delays
 //   and the first group also the pixel's mean, all read from shared memory.
 //   Products are summed in plain FP32 over 8 frames (a relative error of at
@@ -145,13 +146,21 @@ g2_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __re
     }
 }
 
-// one thread per (delay, pixel): segments added in order
-constexpr int kG2sPix = 32;       // pixels per block: one 128-byte row per frame
-constexpr int kG2sGroup = 4;      // delays per thread
+constexpr int kG2sMaxPix = 32;     // pixels per block at most: one 128-byte row per frame
 constexpr int kG2sThreads = 512;
-constexpr int64_t kG2sMaxT = 1600;  // 32 x 1,600 x 4 B = 200 KB of shared memory
+constexpr int64_t kG2sMaxBytes = 200 * 1024;  // shared memory for the series of a block's pixels
+constexpr int kG2sSub = 8;         // frames per plain FP32 sum before the compensated update
 
-constexpr int kG2sSub = 8;        // frames per plain FP32 sum before the compensated update
+// pixels per block for a series of T frames: 32, or 16 where 32 pixels'
+// series do not fit in kG2sMaxBytes; 0 (the segment kernel) beyond.  Rows of
+// 16 pixels are two full 32-byte sectors; narrower rows made the loads a
+// gather of one partial sector per frame and row, and the 10,000-frame
+// 512^2 series took 183 ms instead of 150 ms with 4 pixels per block.
+int g2s_width(int64_t T) {
+    for (int w = kG2sMaxPix; w >= 16; w >>= 1)
+        if ((int64_t)w * T * (int64_t)sizeof(float) <= kG2sMaxBytes) return w;
+    return 0;
+}
 
 // Kahan update: (acc, comp) += v
 __device__ __forceinline__ void kahan_add(float& acc, float& comp, float v) {
@@ -161,43 +170,46 @@ __device__ __forceinline__ void kahan_add(float& acc, float& comp, float v) {
     acc = s;
 }
 
-// frames [t, t + n) of one pixel's series (column `col` of s_x) for up to
-// kG2sGroup delays: the n products per delay are summed in plain FP32 (at
-// most 8 terms), then added to the compensated totals.  CHECK: frames whose
-// partner t + tau lies past the series, and unused delay slots, are skipped.
-template <bool CHECK>
-__device__ __forceinline__ void g2s_sub(const float* col, int t, int n, int T, const int* tau, const int* off, int nk,
-                                        float* acc, float* comp, bool want_mean, float& macc, float& mcomp) {
-    float sk[kG2sGroup], sm = 0.0f;
+// frames [t, t + n) of one pixel's series (column `col` of s_x, rows of W
+// floats) for up to D delays: the n products per delay are summed in plain
+// FP32 (at most 8 terms), then added to the compensated totals.  CHECK:
+// frames whose partner t + tau lies past the series, and unused delay slots,
+// are skipped.
+template <int D, bool CHECK>
+__device__ __forceinline__ void g2s_sub(const float* col, int W, int t, int n, int T, const int* tau, const int* off,
+                                        int nk, float* acc, float* comp, bool want_mean, float& macc, float& mcomp) {
+    float sk[D], sm = 0.0f;
 #pragma unroll
-    for (int k = 0; k < kG2sGroup; ++k) sk[k] = 0.0f;
+    for (int k = 0; k < D; ++k) sk[k] = 0.0f;
 #pragma unroll
     for (int u = 0; u < kG2sSub; ++u) {
         if (CHECK && u >= n) break;
-        const float* r = col + (t + u) * kG2sPix;
+        const float* r = col + (t + u) * W;
         const float x = r[0];
         sm += x;
 #pragma unroll
-        for (int k = 0; k < kG2sGroup; ++k)
+        for (int k = 0; k < D; ++k)
             if (!CHECK || (k < nk && t + u + tau[k] < T)) sk[k] = fmaf(x, r[off[k]], sk[k]);
     }
 #pragma unroll
-    for (int k = 0; k < kG2sGroup; ++k) kahan_add(acc[k], comp[k], sk[k]);
+    for (int k = 0; k < D; ++k) kahan_add(acc[k], comp[k], sk[k]);
     if (want_mean) kahan_add(macc, mcomp, sm);
 }
 
+// W pixels per block (g2s_width), D delays per thread
+template <int D>
 __global__ void __launch_bounds__(kG2sThreads, 1)
 g2_series_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_t* __restrict__ taus, int n_tau,
-                 double* __restrict__ g2, double* __restrict__ mean_out) {
-    extern __shared__ float s_x[];  // [T][kG2sPix]
-    __shared__ double s_mean[kG2sPix];
-    const int64_t p0 = (int64_t)blockIdx.x * kG2sPix;
-    const int np = (int)min((int64_t)kG2sPix, P - p0);
+                 int W, double* __restrict__ g2, double* __restrict__ mean_out) {
+    extern __shared__ float s_x[];  // [T][W]
+    __shared__ double s_mean[kG2sMaxPix];
+    const int64_t p0 = (int64_t)blockIdx.x * W;
+    const int np = (int)min((int64_t)W, P - p0);
     // asynchronous 4-byte copies, all in flight at once (a loop of loads and
     // stores would wait for each load); pixels past P are filled with zeros
-    for (int64_t e = threadIdx.x; e < T * kG2sPix; e += kG2sThreads) {
-        const int64_t t = e / kG2sPix;
-        const int i = (int)(e - t * kG2sPix);
+    for (int64_t e = threadIdx.x; e < T * W; e += blockDim.x) {
+        const int64_t t = e / W;
+        const int i = (int)(e - t * W);
         const float* src = I + t * P + p0 + (i < np ? i : 0);
         const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s_x + e);
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(i < np ? 4 : 0)
@@ -205,23 +217,23 @@ g2_series_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_
     }
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
     __syncthreads();
-    const int n_groups = (n_tau + kG2sGroup - 1) / kG2sGroup;
+    const int n_groups = (n_tau + D - 1) / D;
     const int Ti = (int)T;
-    for (int item = threadIdx.x; item < kG2sPix * n_groups; item += kG2sThreads) {
-        const int i = item % kG2sPix, grp = item / kG2sPix;
-        const int k0 = grp * kG2sGroup, nk = min(kG2sGroup, n_tau - k0);
-        int tau[kG2sGroup], off[kG2sGroup];  // off: offset of x(t + tau_k) from x(t) in s_x
+    for (int item = threadIdx.x; item < W * n_groups; item += blockDim.x) {
+        const int i = item % W, grp = item / W;
+        const int k0 = grp * D, nk = min(D, n_tau - k0);
+        int tau[D], off[D];  // off: offset of x(t + tau_k) from x(t) in s_x
         int tau_max = 0;
 #pragma unroll
-        for (int k = 0; k < kG2sGroup; ++k) {
+        for (int k = 0; k < D; ++k) {
             tau[k] = k < nk ? taus[k0 + k] : 0;
-            off[k] = tau[k] * kG2sPix;
+            off[k] = tau[k] * W;
             tau_max = max(tau_max, tau[k]);
         }
-        float acc[kG2sGroup], comp[kG2sGroup];
-        double dacc[kG2sGroup];
+        float acc[D], comp[D];
+        double dacc[D];
 #pragma unroll
-        for (int k = 0; k < kG2sGroup; ++k) {
+        for (int k = 0; k < D; ++k) {
             acc[k] = comp[k] = 0.0f;
             dacc[k] = 0.0;
         }
@@ -234,11 +246,12 @@ g2_series_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_
             const int tf = max(t0, min(t1, Ti - tau_max));
             int t = t0;
             for (; t + kG2sSub <= tf; t += kG2sSub)
-                g2s_sub<false>(col, t, kG2sSub, Ti, tau, off, nk, acc, comp, want_mean, macc, mcomp);
+                g2s_sub<D, false>(col, W, t, kG2sSub, Ti, tau, off, nk, acc, comp, want_mean, macc, mcomp);
             for (; t < t1; t += kG2sSub)
-                g2s_sub<true>(col, t, min(kG2sSub, t1 - t), Ti, tau, off, nk, acc, comp, want_mean, macc, mcomp);
+                g2s_sub<D, true>(col, W, t, min(kG2sSub, t1 - t), Ti, tau, off, nk, acc, comp, want_mean, macc,
+                                 mcomp);
 #pragma unroll
-            for (int k = 0; k < kG2sGroup; ++k) {
+            for (int k = 0; k < D; ++k) {
                 dacc[k] += (double)acc[k] - (double)comp[k];
                 acc[k] = comp[k] = 0.0f;
             }
@@ -254,13 +267,13 @@ g2_series_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_
         // the numerator's average for now; divided by the squared mean below
         if (i < np) {
 #pragma unroll
-            for (int k = 0; k < kG2sGroup; ++k)
+            for (int k = 0; k < D; ++k)
                 if (k < nk) g2[(int64_t)(k0 + k) * P + p] = dacc[k] / (double)(T - taus[k0 + k]);
         }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < n_tau * kG2sPix; e += kG2sThreads) {
-        const int k = e / kG2sPix, i = e % kG2sPix;
+    for (int e = threadIdx.x; e < n_tau * W; e += blockDim.x) {
+        const int k = e / W, i = e % W;
         if (i >= np) continue;
         const double m = s_mean[i];
         double* gp = g2 + (int64_t)k * P + p0 + i;
@@ -268,6 +281,20 @@ g2_series_kernel(const float* __restrict__ I, int64_t T, int64_t P, const int32_
     }
 }
 
+template <int D>
+cudaError_t launch_g2_series(const float* I, int64_t T, int64_t P, const int32_t* d_taus, int n_tau, int W,
+                             double* g2, double* mean, cudaStream_t st) {
+    const size_t smem = (size_t)T * W * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(g2_series_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int items = W * ((n_tau + D - 1) / D);
+    const int threads = std::min(kG2sThreads, (items + 31) / 32 * 32);
+    ++tl_kernel_launches;
+    g2_series_kernel<D><<<(unsigned)((P + W - 1) / W), threads, smem, st>>>(I, T, P, d_taus, n_tau, W, g2, mean);
+    return cudaGetLastError();
+}
+
+// one thread per (delay, pixel): segments added in order
 __global__ void g2_finish_kernel(const double* __restrict__ part, const double* __restrict__ mpart, int n_seg,
                                  int64_t T, int64_t P, const int32_t* __restrict__ taus, int n_tau,
                                  double* __restrict__ g2, double* __restrict__ mean_out) {
@@ -618,22 +645,19 @@ int g2_segments(int64_t T) {
 }
 
 size_t g2_workspace_bytes(int64_t T, int64_t P, int n_tau) {
-    if (T <= kG2sMaxT) return 0;  // g2_series_kernel writes g2 directly
+    if (g2s_width(T) > 0) return 0;  // g2_series_kernel writes g2 directly
     return (size_t)g2_segments(T) * (size_t)(n_tau + 1) * (size_t)P * sizeof(double);
 }
 
 cudaError_t launch_g2(const float* I, int64_t T, int64_t P, const int32_t* d_taus, int n_tau,
                       double* g2, double* mean, void* ws, cudaStream_t st) {
     if (P == 0 || n_tau == 0) return cudaSuccess;
-    if (T <= kG2sMaxT) {
-        const size_t smem = (size_t)T * kG2sPix * sizeof(float);
-        cudaError_t e = cudaFuncSetAttribute(g2_series_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        ++tl_kernel_launches;
-        g2_series_kernel<<<(unsigned)((P + kG2sPix - 1) / kG2sPix), kG2sThreads, smem, st>>>(I, T, P, d_taus, n_tau,
-                                                                                           g2, mean);
-        return cudaGetLastError();
-    }
+    // the series kernel where 16 or 32 pixels' series fit in shared memory;
+    // 2 delays per thread on 16 pixels keep about 512 (pixel, delay group)
+    // items per block
+    const int W = g2s_width(T);
+    if (W == 32) return launch_g2_series<4>(I, T, P, d_taus, n_tau, W, g2, mean, st);
+    if (W == 16) return launch_g2_series<2>(I, T, P, d_taus, n_tau, W, g2, mean, st);
     const int n_seg = g2_segments(T);
     const int64_t blocks = (T + kFlush - 1) / kFlush;
     const int64_t seg_len = (blocks + n_seg - 1) / n_seg * kFlush;

@@ -30,10 +30,13 @@ def xs():
     (577, 200, [0, 1, 3, 64, 576]),
     (1100, 300, [1, 2, 3, 17, 1099]),
     (40000, 64, [0, 1, 7, 4095, 4096, 39999]),  # several 4,096-frame FP32 blocks per segment
-    # the longest series kept whole in shared memory, and one frame more
-    # (the segment kernel): both sides of the switch
+    # the longest series kept whole for 32 pixels per block, and one frame
+    # more (16 pixels per block)
     (1600, 70, [0, 1, 255, 256, 799, 1599]),
     (1601, 33, [0, 2, 256, 1600]),
+    # 16 pixels per block up to 3,200 frames, then the segment kernel
+    (3200, 40, [0, 1, 9, 1000, 3199]),
+    (3201, 17, [0, 5, 3200]),
 ])
 def test_g2_stage_parity(xs, T, P, taus):
     rng = np.random.default_rng(T + P)
