@@ -100,7 +100,10 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+    """nvidia-smi samples (every 50 ms) of SM clock, power and throttle
+    reasons.  The sampler starts shortly before the timed region, so its first
+    samples can see an idle GPU: the summary keeps the samples drawing at least
+    half the largest power seen (the GPU under load), all of them if none."""
 
     FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
@@ -116,7 +119,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", self.gpu_id], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-lms", "50", "-i", self.gpu_id], stdout=self.fh, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
 
@@ -132,24 +135,30 @@ class ClockSampler:
         self.fh.seek(0)
         rows = [ln.strip().split(",") for ln in self.fh.read().splitlines() if ln.strip()]
         os.unlink(self.fh.name)
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        parsed = []
         for r in rows:
             r = [x.strip() for x in r]
             if len(r) < 8:
                 continue
             try:
-                sm.append(float(r[0]))
-                mx.append(float(r[1]))
+                sm_v, mx_v = float(r[0]), float(r[1])
             except ValueError:
                 continue
-            for name, v in zip(names, r[4:8]):
-                if v.lower().startswith("active"):
-                    reasons.add(name)
-        if not sm:
+            try:
+                pw = float(r[2])
+            except ValueError:
+                pw = float("nan")
+            active = {name for name, v in zip(names, r[4:8]) if v.lower().startswith("active")}
+            parsed.append((sm_v, mx_v, pw, active))
+        if not parsed:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        powers = [p[2] for p in parsed if p[2] == p[2]]
+        loaded = [p for p in parsed if powers and p[2] == p[2] and p[2] >= 0.5 * max(powers)] or parsed
+        reasons = set().union(*(p[3] for p in loaded))
+        return {"sm_mhz": statistics.median(p[0] for p in loaded), "sm_max_mhz": max(p[1] for p in parsed),
+                "reasons": sorted(reasons), "samples": len(loaded), "samples_total": len(parsed),
+                "power_w_median": statistics.median(p[2] for p in loaded) if powers else None}
 
 
 def _dist():
