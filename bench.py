@@ -632,7 +632,22 @@ def run_ours(args):
             b_h.copy_(beta, non_blocking=True)
             stream.wait_stream(side)
 
-        e2e_step()
+        # the host link's copy rate on this machine (pinned, 256 MB, best of 3),
+        # outside the timed region: the e2e figure is bound by it where it
+        # is slow
+        link = torch.empty(1 << 26, dtype=torch.float32).pin_memory()
+        link_d = torch.empty(1 << 26, dtype=torch.float32, device=dev)
+        link_gbs = 0.0
+        for _ in range(3):
+            l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0.record(stream)
+            link_d.copy_(link, non_blocking=True)
+            l1.record(stream)
+            l1.synchronize()
+            link_gbs = max(link_gbs, link.numel() * 4 / (l0.elapsed_time(l1) * 1e-3) / 1e9)
+        del link, link_d
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
@@ -646,7 +661,8 @@ def run_ours(args):
             d2h += sum(T // k for k in Ks) * R * 2 * 8   # the all-reduced window sums read by the finalize
         e_val = job_value(units, world, e_ms) if not sharded else float(N) * P * T / (e_ms * 1e-3)
         line["e2e"] = {"value": e_val, "unit": METRIC, "ms_per_step": e_ms,
-                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "host_to_device_gbs": link_gbs}
         del pos_h
 
     # ---- plain FP32 direct-sum kernel on the same workload (first 32 frames) ---
