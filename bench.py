@@ -649,9 +649,15 @@ def run_ours(args):
         for _ in range(max(1, args.warmup)):
             e2e_step()
         barrier()
+        # each step timed on its own as well (synchronised at its end), so a
+        # step stalled by the host shows in the spread beside the mean
         t0 = time.perf_counter()
+        step_ms = []
         for _ in range(args.steps):
+            ts = time.perf_counter()
             e2e_step()
+            torch.cuda.synchronize()
+            step_ms.append((time.perf_counter() - ts) * 1e3)
         barrier()
         e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
         ctx.sync_status()
@@ -662,7 +668,8 @@ def run_ours(args):
         e_val = job_value(units, world, e_ms) if not sharded else float(N) * P * T / (e_ms * 1e-3)
         line["e2e"] = {"value": e_val, "unit": METRIC, "ms_per_step": e_ms,
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                       "host_to_device_gbs": link_gbs}
+                       "host_to_device_gbs": link_gbs,
+                       "step_ms_min_median_max": [min(step_ms), statistics.median(step_ms), max(step_ms)]}
         del pos_h
 
     # ---- plain FP32 direct-sum kernel on the same workload (first 32 frames) ---
