@@ -102,12 +102,13 @@ def _peaks():
 class ClockSampler:
     """nvidia-smi samples (every 50 ms) of SM clock, power and throttle
     reasons.  The sampler starts shortly before the timed region, so its first
-    samples can see an idle GPU: the summary keeps the samples drawing at least
-    half the largest power seen (the GPU under load), all of them if none."""
+    samples can see an idle GPU: the summary leaves out the samples whose
+    gpu_idle reason is active (all of them are kept if none is left)."""
 
     FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
-              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap",
+              "clocks_event_reasons.gpu_idle"]
 
     def __init__(self, gpu_id: str):
         self.gpu_id = gpu_id
@@ -150,11 +151,12 @@ class ClockSampler:
             except ValueError:
                 pw = float("nan")
             active = {name for name, v in zip(names, r[4:8]) if v.lower().startswith("active")}
-            parsed.append((sm_v, mx_v, pw, active))
+            idle = len(r) > 8 and r[8].lower().startswith("active")
+            parsed.append((sm_v, mx_v, pw, active, idle))
         if not parsed:
             return None
         powers = [p[2] for p in parsed if p[2] == p[2]]
-        loaded = [p for p in parsed if powers and p[2] == p[2] and p[2] >= 0.5 * max(powers)] or parsed
+        loaded = [p for p in parsed if not p[4]] or parsed
         reasons = set().union(*(p[3] for p in loaded))
         return {"sm_mhz": statistics.median(p[0] for p in loaded), "sm_max_mhz": max(p[1] for p in parsed),
                 "reasons": sorted(reasons), "samples": len(loaded), "samples_total": len(parsed),

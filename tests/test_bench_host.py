@@ -1,6 +1,7 @@
 """Host logic of bench.py that needs no GPU: the clock sampler's summary of
-nvidia-smi rows (median SM clock and throttle reasons over the samples taken
-under load, so that idle samples before the timed region do not count)."""
+nvidia-smi rows (median SM clock and throttle reasons over the samples whose
+gpu_idle reason is not active, so that idle samples before the timed region
+do not count)."""
 import os
 import sys
 import tempfile
@@ -27,14 +28,14 @@ def _summary(rows):
     return cs.stop()
 
 
-IDLE = "2070, 2070, 180.5, 0x0, Not Active, Not Active, Not Active, Not Active"
+IDLE = "2070, 2070, 180.5, 0x1, Not Active, Not Active, Not Active, Not Active, Active"
 
 
 def test_idle_samples_before_the_load_are_left_out():
     s = _summary([IDLE, IDLE,
-                  "1650, 2070, 1390.2, 0x4, Not Active, Not Active, Not Active, Active",
-                  "1710, 2070, 1385.0, 0x4, Not Active, Not Active, Not Active, Active",
-                  "1690, 2070, 1388.0, 0x4, Not Active, Not Active, Not Active, Active"])
+                  "1650, 2070, 1390.2, 0x4, Not Active, Not Active, Not Active, Active, Not Active",
+                  "1710, 2070, 1385.0, 0x4, Not Active, Not Active, Not Active, Active, Not Active",
+                  "1690, 2070, 1388.0, 0x4, Not Active, Not Active, Not Active, Active, Not Active"])
     assert s["samples"] == 3 and s["samples_total"] == 5
     assert s["sm_mhz"] == 1690.0
     assert s["sm_max_mhz"] == 2070.0
@@ -42,10 +43,15 @@ def test_idle_samples_before_the_load_are_left_out():
 
 
 def test_throttle_reasons_of_loaded_samples_are_reported():
-    s = _summary(["1500, 2070, 1300.0, 0x20, Not Active, Active, Not Active, Not Active",
-                  "1600, 2070, 1310.0, 0x4, Not Active, Not Active, Not Active, Active"])
+    s = _summary(["1500, 2070, 1300.0, 0x20, Not Active, Active, Not Active, Not Active, Not Active",
+                  "1600, 2070, 1310.0, 0x4, Not Active, Not Active, Not Active, Active, Not Active"])
     assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
     assert s["sm_mhz"] == 1550.0
+
+
+def test_all_idle_keeps_every_sample():
+    s = _summary([IDLE, IDLE])
+    assert s["samples"] == 2 and s["sm_mhz"] == 2070.0
 
 
 def test_rows_without_power_keep_every_sample_and_bad_rows_are_skipped():
