@@ -18,6 +18,7 @@ workload on the host cores (rank 0 only).
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -102,10 +103,11 @@ def _peaks():
 class ClockSampler:
     """nvidia-smi samples (every 50 ms) of SM clock, power and throttle
     reasons.  The sampler starts shortly before the timed region, so its first
-    samples can see an idle GPU: the summary leaves out the samples whose
-    gpu_idle reason is active (all of them are kept if none is left)."""
+    samples can see an idle GPU: given the region's start and end (host wall
+    clock), the summary keeps the samples stamped inside it, and it leaves out
+    samples whose gpu_idle reason is active (all are kept if none is left)."""
 
-    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+    FIELDS = ["timestamp", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
               "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap",
               "clocks_event_reasons.gpu_idle"]
@@ -124,7 +126,7 @@ class ClockSampler:
         except OSError:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0: float | None = None, t1: float | None = None):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -140,23 +142,30 @@ class ClockSampler:
         parsed = []
         for r in rows:
             r = [x.strip() for x in r]
-            if len(r) < 8:
+            if len(r) < 9:
                 continue
             try:
-                sm_v, mx_v = float(r[0]), float(r[1])
+                sm_v, mx_v = float(r[1]), float(r[2])
             except ValueError:
                 continue
             try:
-                pw = float(r[2])
+                pw = float(r[3])
             except ValueError:
                 pw = float("nan")
-            active = {name for name, v in zip(names, r[4:8]) if v.lower().startswith("active")}
-            idle = len(r) > 8 and r[8].lower().startswith("active")
-            parsed.append((sm_v, mx_v, pw, active, idle))
+            try:
+                stamp = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                stamp = None
+            active = {name for name, v in zip(names, r[5:9]) if v.lower().startswith("active")}
+            idle = len(r) > 9 and r[9].lower().startswith("active")
+            parsed.append((sm_v, mx_v, pw, active, idle, stamp))
         if not parsed:
             return None
         powers = [p[2] for p in parsed if p[2] == p[2]]
-        loaded = [p for p in parsed if not p[4]] or parsed
+        inside = parsed
+        if t0 is not None and t1 is not None:
+            inside = [p for p in parsed if p[5] is not None and t0 <= p[5] <= t1] or parsed
+        loaded = [p for p in inside if not p[4]] or inside
         reasons = set().union(*(p[3] for p in loaded))
         return {"sm_mhz": statistics.median(p[0] for p in loaded), "sm_max_mhz": max(p[1] for p in parsed),
                 "reasons": sorted(reasons), "samples": len(loaded), "samples_total": len(parsed),
@@ -522,12 +531,14 @@ def run_ours(args):
     barrier()
     sampler.start()
     time.sleep(0.3)
+    wall0 = time.time()
     ev0.record(stream)
     for _ in range(args.steps):
         res = step(pos_d, f_d)  # the last step's g2 and beta are checked against the oracle below
     ev1.record(stream)
     ev1.synchronize()
-    clocks = sampler.stop()
+    wall1 = time.time()
+    clocks = sampler.stop(wall0, wall1)
     barrier()
     I_step = I.clone()  # the timed step's intensity, for the accuracy check
     launches = ctx.launch_count() - launches0
