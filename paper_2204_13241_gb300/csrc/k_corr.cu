@@ -5,7 +5,8 @@
 //   series of W consecutive pixels into shared memory once (W = 32 up to
 //   1,600 frames, 16 up to 3,200, so that they fit in 200 KB),
 //   then each thread sums one pixel's products for a group of up to 4 delays
-//   and the first group also the pixel's mean, all read from shared memory.
+//   (2 on 16 pixels) and the first group also the pixel's mean, all read from
+//   shared memory.
 //   Products are summed in plain FP32 over 8 frames (a relative error of at
 //   most 7 eps for these positive terms), those sums with compensated FP32
 //   over 256-frame blocks, the block sums in FP64.  Each operand is read from
