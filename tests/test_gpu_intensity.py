@@ -165,6 +165,42 @@ def test_host_streamed_positions_match_device(xs):
     assert np.array_equal(host_out.numpy(), dev)
 
 
+def _host_run(xs, pos, f, box, grid, shift, pinned):
+    pbuf = torch.empty(pos.size + shift, dtype=torch.float32)
+    fbuf = torch.empty(f.size + 3 - shift, dtype=torch.float32)
+    if pinned:
+        pbuf, fbuf = pbuf.pin_memory(), fbuf.pin_memory()
+    hp = pbuf[shift:].view(pos.shape)
+    hf = fbuf[3 - shift:]
+    hp.copy_(torch.from_numpy(pos))
+    hf.copy_(torch.from_numpy(f))
+    assert hp.is_pinned() == pinned
+    out = torch.empty((pos.shape[0], 1, grid.ny, grid.nx), dtype=torch.float32, device="cuda")
+    xs.intensity(hp, hf, box, grid, "fp16", out=out)
+    xs.Context.get().sync_status()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("shift", [0, 1, 2, 3])
+def test_host_positions_at_any_alignment_pinned_or_pageable(xs, shift):
+    # host positions and form factors, page-locked or pageable, starting at
+    # any float offset, give the same bits; 40,000 atoms over 300 frames make
+    # two chunks, whose launches split the work differently from one launch
+    # over all frames, so the device-resident result is met within the
+    # tolerance instead
+    pos, f, box = _case(17, 40000, 300, 70.0)
+    grid = wl.QGrid(-16, 32, -16, 32, 0, 1)
+    ref = _host_run(xs, pos, f, box, grid, 0, False)
+    got = _host_run(xs, pos, f, box, grid, shift, True)
+    assert np.array_equal(got, ref)
+    if shift:
+        assert np.array_equal(_host_run(xs, pos, f, box, grid, shift, False), ref)
+    dev = _run(xs, pos, f, box, grid, "fp16")
+    m = grid.miller()
+    err, err0 = e_I(got.reshape(300, -1), dev.reshape(300, -1).astype(np.float64), m)
+    assert err <= 1e-4 and err0 <= 1e-4, (err, err0)
+
+
 def test_host_streaming_over_several_chunks(xs):
     # 64,000 atoms are 768 kB per frame: host positions are streamed in chunks
     # that start near 64 MB (87 frames) and double, so 200 frames take two
