@@ -59,7 +59,7 @@ extern "C" {
 typedef enum {
     XS_OK = 0,
     XS_ERR_INVALID_ARG = 1,   /* null pointer, size <= 0, singular cell, tau/K out of range */
-    XS_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+    XS_ERR_UNSUPPORTED = 2,   /* valid request this library does not implement */
     XS_ERR_NO_MEMORY = 3,     /* the allocator returned NULL */
     XS_ERR_CUDA = 4,          /* a CUDA runtime call failed (message has the CUDA error) */
     XS_ERR_TIMEOUT = 5,       /* a kernel's bounded wait expired (device error word) */
